@@ -1,0 +1,420 @@
+"""Population annealing for the 2D Ising model: the oracle's step logic.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+The algorithm follows Sec. 2.1 of the paper (Machta's variant with unit
+weights): start from R independent replicas at beta0 = 0; for each new
+inverse temperature resample the population with the nearest-integer rule of
+Eq. resampling-factors, run theta Metropolis sweeps per replica, and measure
+the population averages of Eq. observables. The free energy follows
+Eq. free-energy with Z_beta0 = 2^N, the entropy Eq. entropy. Sec. 2.3 gives
+the adaptive step (histogram overlap alpha), Sec. 2.4 the multi-histogram
+estimate of the density of states (Eq. MHReq1).
+
+Readings where the paper is silent (each listed in the design notes):
+
+* Energy level k = (E + 2N)/4 in [0, N]; magnetisation level m = (M + N)/2.
+* No sweeps at beta0: the random start is already in equilibrium there
+  (Sec. 2.1); row 0 is emitted with ln Q_0 = 0.
+* Fixed schedule: n = round((beta_f - beta0)/dbeta) steps with
+  beta_i = beta0 + i*dbeta (a product, so no drift), step size dbeta in Q.
+* Q is evaluated relative to the lowest occupied level kmin:
+  S = sum_k H[k] t[k - kmin] with t[d] = exp(-(4 dbeta) d), summed as a fixed
+  pairwise tree over the histogram padded with zeros to a power of two (the
+  paper asks for a deterministic order, Sec. 3 "Resampling and
+  measurements"); ln Q_i = ln S - ln R_{i-1} - dbeta * E_min, and
+  tau_hat_k = R t[k - kmin] / S, equal to (R/R_{i-1}) tau_i of Sec. 2.1.
+* Extra copy iff u < frac(tau_hat) with u = x 2^-32: as integers,
+  x < U = ceil(frac * 2^32).
+* Metropolis acceptance for dE = 4, 8: x < ceil(exp(-4 beta) 2^32),
+  x < ceil(exp(-8 beta) 2^32); colour 0 is swept before colour 1.
+* Population capacity R_cap = ceil(1.05 R) + 1024 unless set; a step that
+  produces more replicas fails with "capacity", zero replicas with "extinct".
+* Adaptive step: if alpha(beta_f - beta) >= alpha*, jump to beta_f;
+  otherwise bisect [0, beta_f - beta] for 60 iterations keeping the lower end
+  where alpha >= alpha*. alpha sums levels in ascending order.
+* MHR includes row 0 (an exact beta = 0 sample) in the histogram sum.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import core
+
+
+class OracleError(RuntimeError):
+    """Raised with .kind in {"capacity", "extinct", "stalled"}."""
+
+    def __init__(self, kind: str, msg: str):
+        super().__init__(msg)
+        self.kind = kind
+
+
+def _ptr(a: np.ndarray, ctype):
+    import ctypes
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+# ------------------------------------------------------------- C-core wrappers
+def philox4x32_10(ctr, key) -> tuple[int, int, int, int]:
+    """Philox4x32-10 of one 128-bit counter (4 words) and 64-bit key (2 words)."""
+    import ctypes
+    c = (ctypes.c_uint32 * 4)(*[int(v) & 0xFFFFFFFF for v in ctr])
+    k = (ctypes.c_uint32 * 2)(*[int(v) & 0xFFFFFFFF for v in key])
+    o = (ctypes.c_uint32 * 4)()
+    core().oracle_philox4x32_10(c, k, o)
+    return tuple(int(v) for v in o)
+
+
+def philox_many(ctr: np.ndarray, seed: int) -> np.ndarray:
+    import ctypes
+    ctr = np.ascontiguousarray(ctr, dtype=np.uint32).reshape(-1, 4)
+    out = np.empty_like(ctr)
+    core().oracle_philox_many(ctr.shape[0], _ptr(ctr, ctypes.c_uint32), seed, _ptr(out, ctypes.c_uint32))
+    return out
+
+
+def init_spins(L: int, slots: np.ndarray, seed: int) -> np.ndarray:
+    import ctypes
+    slots = np.ascontiguousarray(slots, dtype=np.int64)
+    s = np.empty((slots.size, L, L), dtype=np.int8)
+    core().oracle_init(L, slots.size, _ptr(slots, ctypes.c_int64), seed, _ptr(s, ctypes.c_int8))
+    return s
+
+
+def sweep(s: np.ndarray, slots: np.ndarray, seed: int, u0: int, theta: int, T4: int, T8: int) -> None:
+    """theta sweeps in place on s[r] (replica slot slots[r])."""
+    import ctypes
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    slots = np.ascontiguousarray(slots, dtype=np.int64)
+    L = s.shape[1]
+    core().oracle_sweep(L, slots.size, _ptr(slots, ctypes.c_int64), seed, u0, theta, T4, T8,
+                        _ptr(s, ctypes.c_int8))
+
+
+def measure(s: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    import ctypes
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    n = s.shape[0]
+    E = np.empty(n, dtype=np.int64)
+    M = np.empty(n, dtype=np.int64)
+    core().oracle_measure(s.shape[1], n, _ptr(s, ctypes.c_int8), _ptr(E, ctypes.c_int64),
+                          _ptr(M, ctypes.c_int64))
+    return E, M
+
+
+def resample_words(seed: int, step: int, n: int) -> np.ndarray:
+    import ctypes
+    out = np.empty(n, dtype=np.uint32)
+    core().oracle_resample_words(seed, step, n, _ptr(out, ctypes.c_uint32))
+    return out
+
+
+# ------------------------------------------------------------- scalar pieces
+def metropolis_threshold(beta: float, dE: int) -> int:
+    """ceil(exp(-beta dE) * 2^32): x < T accepts with probability exp(-beta dE)."""
+    return int(math.ceil(math.ldexp(math.exp(-float(dE) * beta), 32)))
+
+
+def pad_size(N: int) -> int:
+    """Smallest power of two >= N + 1 (the number of energy levels)."""
+    P = 1
+    while P < N + 1:
+        P *= 2
+    return P
+
+
+def pairwise_sum(a: np.ndarray) -> float:
+    """Fixed binary tree: sum(a) = sum(left half) + sum(right half), len(a) a
+    power of two. Computed level by level: neighbours are added in pairs."""
+    a = np.asarray(a, dtype=np.float64)
+    n = a.size
+    assert n >= 1 and n & (n - 1) == 0
+    while a.size > 1:
+        a = a[0::2] + a[1::2]
+    return float(a[0])
+
+
+def level_weights(delta: float, ndiff: int) -> np.ndarray:
+    """t[d] = exp(-(4 delta) d) for d = 0..ndiff-1 (libm exp, one call each)."""
+    f = 4.0 * delta
+    return np.array([math.exp(-(f * float(d))) for d in range(ndiff)], dtype=np.float64)
+
+
+def normaliser_S(H: np.ndarray, kmin: int, kmax: int, t: np.ndarray, N: int) -> float:
+    """S = sum_k H[k] t[k - kmin] by the fixed pairwise tree (Eq. Q up to the
+    factor exp(-dbeta E_min) / R_{i-1})."""
+    T = np.zeros(pad_size(N), dtype=np.float64)
+    T[kmin:kmax + 1] = H[kmin:kmax + 1].astype(np.float64) * t[: kmax - kmin + 1]
+    return pairwise_sum(T)
+
+
+def copy_tables(R: int, t: np.ndarray, S: float):
+    """tau_hat = R t / S; F = floor(tau_hat); U = ceil(frac(tau_hat) 2^32)."""
+    tau = (float(R) * t) / S
+    F = np.floor(tau)
+    frac = tau - F
+    U = np.ceil(frac * 4294967296.0)
+    return tau, F.astype(np.int64), U.astype(np.int64)
+
+
+def overlap_alpha(H: np.ndarray, kmin: int, kmax: int, R: int, R_prev: int, delta: float, N: int) -> float:
+    """Histogram overlap of Sec. 2.3: (1/R_{i-1}) sum_j min(1, tau_hat_j),
+    evaluated over levels in ascending order."""
+    t = level_weights(delta, kmax - kmin + 1)
+    S = normaliser_S(H, kmin, kmax, t, N)
+    acc = 0.0
+    for k in range(kmin, kmax + 1):
+        acc += float(H[k]) * min(1.0, (float(R) * float(t[k - kmin])) / S)
+    return acc / float(R_prev)
+
+
+def choose_delta(H, kmin, kmax, R, R_prev, beta, beta_f, target, N):
+    """Adaptive step (Sec. 2.3): largest delta found by 60 bisection steps
+    with alpha(delta) >= target; the whole remaining interval if it passes."""
+    dmax = beta_f - beta
+    if overlap_alpha(H, kmin, kmax, R, R_prev, dmax, N) >= target:
+        return dmax, True
+    lo, hi = 0.0, dmax
+    for _ in range(60):
+        mid = 0.5 * (lo + hi)
+        if overlap_alpha(H, kmin, kmax, R, R_prev, mid, N) >= target:
+            lo = mid
+        else:
+            hi = mid
+    return lo, False
+
+
+# ------------------------------------------------------------- the run
+@dataclass
+class StepRecord:
+    step: int
+    beta: float
+    delta: float
+    R: int                  # population after this step's resampling
+    R_prev: int
+    kmin_prev: int = 0      # lowest occupied level of the previous population
+    S: float = 0.0
+    lnQ: float = 0.0
+    T4: int = 0
+    T8: int = 0
+    H_E: np.ndarray | None = None   # histogram of this step's population
+    H_M: np.ndarray | None = None
+    counts: np.ndarray | None = None  # r_j of the previous population
+    families: int = 0
+    sums: tuple = ()                # (sum E, sum E^2, sum |M|, sum M^2, sum M^4) as ints
+
+
+@dataclass
+class Row:
+    beta: float
+    e: float
+    C: float
+    abs_m: float
+    m2: float
+    m4: float
+    betaF_per_N: float
+    S_per_N: float
+    lnQ: float
+    R: int
+    families: int
+
+    def as_tuple(self):
+        return (self.beta, self.e, self.C, self.abs_m, self.m2, self.m4,
+                self.betaF_per_N, self.S_per_N, self.lnQ, self.R, self.families)
+
+
+def moment_sums(E: np.ndarray, M: np.ndarray):
+    """Exact integer population sums (Python ints, no overflow)."""
+    Ei = [int(v) for v in E]
+    Mi = [int(v) for v in M]
+    return (sum(Ei), sum(v * v for v in Ei), sum(abs(v) for v in Mi),
+            sum(v * v for v in Mi), sum(v ** 4 for v in Mi))
+
+
+def make_row(beta: float, N: int, R: int, sums, sum_lnQ: float, lnQ: float, families: int) -> Row:
+    """Eq. observables, Eq. free-energy (Z_beta0 = 2^N) and Eq. entropy.
+    C uses the exact integer numerator R sum E^2 - (sum E)^2, which equals
+    beta^2 N (mean(e^2) - mean(e)^2) without cancellation."""
+    sE, sE2, sAM, sM2, sM4 = sums
+    fR, fN = float(R), float(N)
+    e = float(sE) / (fR * fN)
+    C = beta * beta * float(R * sE2 - sE * sE) / (fR * fR * fN)
+    abs_m = float(sAM) / (fR * fN)
+    m2 = float(sM2) / (fR * fN * fN)
+    m4 = float(sM4) / (fR * fN * fN * fN * fN)
+    betaF = -(fN * math.log(2.0) + sum_lnQ) / fN
+    return Row(beta, e, C, abs_m, m2, m4, betaF, beta * e - betaF, lnQ, R, families)
+
+
+class PopulationAnnealing:
+    """One PA run of the 2D Ising model, step by step (Sec. 2.1)."""
+
+    def __init__(self, L: int, R: int, theta: int, beta_f: float = 1.0, dbeta: float = 0.01,
+                 seed: int = 1, beta0: float = 0.0, overlap: float = 0.85,
+                 capacity: int = 0, record_hist: bool = True):
+        if L < 4 or L % 2:
+            raise ValueError("L must be even and >= 4")
+        if beta0 != 0.0:
+            raise ValueError("beta0 must be 0 (Z_beta0 = 2^N is known only there)")
+        if R < 1 or theta < 1 or not (beta_f > beta0):
+            raise ValueError("bad R, theta or beta_f")
+        self.L, self.N, self.R, self.theta = L, L * L, int(R), int(theta)
+        self.seed = int(seed)
+        self.beta_f = float(beta_f)
+        self.dbeta = float(dbeta)
+        self.adaptive = not (self.dbeta > 0.0)
+        self.overlap = float(overlap)
+        # default capacity ceil(1.05 R) + 1024 holds R_i = R +- O(sqrt R)
+        self.R_cap = int(capacity) if capacity > 0 else int(math.ceil(self.R * 1.05)) + 1024
+        self.n_fixed = int(math.floor((self.beta_f - beta0) / self.dbeta + 0.5)) if not self.adaptive else None
+        self.record_hist = record_hist
+        self.step_index = 0
+        self.beta = 0.0
+        self.done = False
+        self.partial = False
+        # step 0: random configurations at beta0 = 0, measured, no sweeps
+        slots = np.arange(self.R, dtype=np.int64)
+        self.pop = init_spins(L, slots, self.seed)
+        self.E, self.M = measure(self.pop)
+        self.fam = np.arange(self.R, dtype=np.int64)
+        self.sum_lnQ = 0.0
+        self.Hsum = np.zeros(self.N + 1, dtype=np.int64)
+        self.records: list[StepRecord] = []
+        self.rows: list[Row] = []
+        self._measure_and_record(StepRecord(step=0, beta=0.0, delta=0.0, R=self.R, R_prev=self.R))
+
+    # -- helpers
+    def levels(self) -> np.ndarray:
+        return (self.E + 2 * self.N) // 4
+
+    def mlevels(self) -> np.ndarray:
+        return (self.M + self.N) // 2
+
+    def _measure_and_record(self, rec: StepRecord):
+        N = self.N
+        H_E = np.bincount(self.levels(), minlength=N + 1).astype(np.int64)
+        H_M = np.bincount(self.mlevels(), minlength=N + 1).astype(np.int64)
+        self.Hsum += H_E
+        rec.families = int(np.unique(self.fam).size)
+        rec.sums = moment_sums(self.E, self.M)
+        if self.record_hist:
+            rec.H_E, rec.H_M = H_E, H_M
+        self.sum_lnQ += rec.lnQ
+        self.records.append(rec)
+        self.rows.append(make_row(rec.beta, N, rec.R, rec.sums, self.sum_lnQ, rec.lnQ, rec.families))
+
+    def n_steps_left(self):
+        return None if self.adaptive else self.n_fixed - self.step_index
+
+    # -- one temperature step (Sec. 2.1 steps 2-4)
+    def step(self, sample: np.ndarray | None = None):
+        """Advance one inverse-temperature step. With `sample` (new-slot
+        indices) only those replicas are swept and measured; the run then
+        stops (used for full-size spot checks). Returns the record."""
+        if self.done or self.partial:
+            raise RuntimeError("run finished")
+        N, R = self.N, self.R
+        i = self.step_index + 1
+        R_prev = self.E.size
+        lv = self.levels()
+        H = np.bincount(lv, minlength=N + 1).astype(np.int64)
+        occ = np.nonzero(H)[0]
+        kmin, kmax = int(occ[0]), int(occ[-1])
+        if self.adaptive:
+            delta, final = choose_delta(H, kmin, kmax, R, R_prev, self.beta, self.beta_f, self.overlap, N)
+            if delta <= 0.0:
+                raise OracleError("stalled", "adaptive step found no positive delta")
+            beta_new = self.beta_f if final else self.beta + delta
+        else:
+            delta = self.dbeta
+            beta_new = 0.0 + i * self.dbeta
+            final = i == self.n_fixed
+        # Eq. Q with the E_min shift, and the copy numbers of Eq. resampling-factors
+        t = level_weights(delta, kmax - kmin + 1)
+        S = normaliser_S(H, kmin, kmax, t, N)
+        _, F, U = copy_tables(R, t, S)
+        x = resample_words(self.seed, i, R_prev).astype(np.int64)
+        d = lv - kmin
+        r = F[d] + (x < U[d]).astype(np.int64)
+        R_new = int(r.sum())
+        if R_new > self.R_cap:
+            raise OracleError("capacity", f"R_{i} = {R_new} exceeds capacity {self.R_cap}")
+        if R_new == 0:
+            raise OracleError("extinct", f"population died out at step {i}")
+        parent = np.repeat(np.arange(R_prev, dtype=np.int64), r)
+        E_min = -2 * N + 4 * kmin
+        lnQ = (math.log(S) - math.log(float(R_prev))) - delta * float(E_min)
+        T4 = metropolis_threshold(beta_new, 4)
+        T8 = metropolis_threshold(beta_new, 8)
+        rec = StepRecord(step=i, beta=beta_new, delta=delta, R=R_new, R_prev=R_prev, kmin_prev=kmin,
+                         S=S, lnQ=lnQ, T4=T4, T8=T8, counts=r if self.record_hist else None)
+        rec.parent = parent
+        u0 = (i - 1) * self.theta
+        if sample is not None:
+            sample = np.asarray(sample, dtype=np.int64)
+            sub = np.ascontiguousarray(self.pop[parent[sample]])
+            sweep(sub, sample, self.seed, u0, self.theta, T4, T8)
+            rec.sample = sample
+            rec.sample_pop = sub
+            rec.sample_E, rec.sample_M = measure(sub)
+            rec.sample_fam = self.fam[parent[sample]]
+            self.partial = True
+            self.records.append(rec)
+            return rec
+        self.pop = np.ascontiguousarray(self.pop[parent])
+        self.fam = self.fam[parent]
+        sweep(self.pop, np.arange(R_new, dtype=np.int64), self.seed, u0, self.theta, T4, T8)
+        self.E, self.M = measure(self.pop)
+        self.step_index = i
+        self.beta = beta_new
+        self.done = bool(final)
+        self._measure_and_record(rec)
+        return rec
+
+    def run(self):
+        while not self.done:
+            self.step()
+        return self.rows
+
+    # -- multi-histogram reweighting (Sec. 2.4, Eq. MHReq1)
+    def ln_dos(self) -> tuple[np.ndarray, np.ndarray]:
+        """ln Omega(E_k) for every level with Hsum[k] > 0 (others -inf):
+        ln Omega_k = ln Hsum_k - LSE_i(ln R_i + beta_i F_i - beta_i E_k),
+        beta_i F_i = -(N ln 2 + sum_{l<=i} ln Q_l)."""
+        N = self.N
+        E_k = (-2 * N + 4 * np.arange(N + 1)).astype(np.float64)
+        betas = np.array([r.beta for r in self.rows])
+        lnR = np.log(np.array([float(r.R) for r in self.rows]))
+        bF = np.array([r.betaF_per_N for r in self.rows]) * N
+        out = np.full(N + 1, -np.inf)
+        for k in range(N + 1):
+            if self.Hsum[k] > 0:
+                a = lnR + bF - betas * E_k[k]
+                m = a.max()
+                out[k] = math.log(float(self.Hsum[k])) - (m + math.log(float(np.exp(a - m).sum())))
+        return E_k, out
+
+    def mhr(self, betas) -> list[dict]:
+        """Reweighted e, C, beta F / N and S / N at each beta from ln Omega."""
+        N = self.N
+        E_k, lno = self.ln_dos()
+        ok = np.isfinite(lno)
+        E, lo = E_k[ok], lno[ok]
+        out = []
+        for b in betas:
+            a = lo - b * E
+            m = a.max()
+            w = np.exp(a - m)
+            Z = w.sum()
+            lnZ = m + math.log(float(Z))
+            e1 = float((w * E).sum() / Z)
+            e2 = float((w * E * E).sum() / Z)
+            e = e1 / N
+            bF = -lnZ / N
+            out.append({"beta": float(b), "e": e, "C": b * b * (e2 - e1 * e1) / N,
+                        "betaF_per_N": bF, "S_per_N": b * e - bF, "lnZ": lnZ})
+        return out

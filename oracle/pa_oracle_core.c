@@ -1,0 +1,174 @@
+/*
+ * Population-annealing ORACLE, C part: the per-site Monte Carlo loops.
+ *
+ * TEST INFRASTRUCTURE ONLY. This file is the slow, plain CPU statement of what
+ * the GPU engine computes. Only the tests, __graft_entry__.smoke() and the
+ * CPU-baseline leg of bench.py may load it. It shares no code, header, table
+ * or constant generator with the CUDA engine under paper_1703_03676_gb300/.
+ *
+ * Model (Sec. 3, Eq. hamiltonian): H = -sum_<ij> s_i s_j on a periodic L x L
+ * lattice, J = 1. Spins are stored in the natural layout s[y*L + x] as int8
+ * +1/-1, one replica after the other.
+ *
+ * Random numbers (Sec. 3, "Spin updates"): the paper draws one uniform per
+ * spin-flip attempt from the counter-based Philox4x32-10 generator of Salmon,
+ * Moraes, Dror and Shaw (SC'11). Philox is written here from that
+ * publication's definition: ten rounds of two 32x32->64 multiplications with
+ * M0 = 0xD2511F53 and M1 = 0xCD9E8D57, the high halves XORed with the other
+ * counter words and the round key, and a Weyl key schedule with increments
+ * 0x9E3779B9 and 0xBB67AE85.
+ *
+ * Counter layout ("stream map"). The paper seeds per thread from grid and
+ * block indices, which would tie the result to the launch shape; here the
+ * counter is a function of logical indices only, so any implementation that
+ * visits the same (replica, site, sweep) gets the same number:
+ *   key = (seed & 0xffffffff, seed >> 32)
+ *   INIT     (tag 0): g = c*N/2 + b,  ctr = (g>>2, k, 0, 0),       x = out[g&3]
+ *   SWEEP    (tag 1): ctr = (b>>2, k, 2u + c, 1),                   x = out[b&3]
+ *   RESAMPLE (tag 2): ctr = (j>>2, i, 0, 2),                        x = out[j&3]
+ * where c = (x+y)&1 is the checkerboard colour of site (x, y),
+ * b = y*(L/2) + (x>>1) its index within the colour, k the replica slot,
+ * u the global sweep number, i the temperature step and j the old slot.
+ */
+#include <stdint.h>
+#include <stddef.h>
+
+#define PHILOX_M0 0xD2511F53u
+#define PHILOX_M1 0xCD9E8D57u
+#define PHILOX_W0 0x9E3779B9u
+#define PHILOX_W1 0xBB67AE85u
+
+/* Philox4x32-10 bijection of a 128-bit counter under a 64-bit key. */
+void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; round++) {
+        uint64_t p0 = (uint64_t)PHILOX_M0 * (uint64_t)x0;
+        uint64_t p1 = (uint64_t)PHILOX_M1 * (uint64_t)x2;
+        uint32_t y0 = (uint32_t)(p1 >> 32) ^ x1 ^ k0;
+        uint32_t y1 = (uint32_t)p1;
+        uint32_t y2 = (uint32_t)(p0 >> 32) ^ x3 ^ k1;
+        uint32_t y3 = (uint32_t)p0;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+        k0 += PHILOX_W0;
+        k1 += PHILOX_W1;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* One 32-bit word of a tagged stream: lane l of Philox(ctr = (c0, c1, c2, tag)). */
+static uint32_t stream_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
+                            uint32_t tag, unsigned lane)
+{
+    uint32_t ctr[4] = {c0, c1, c2, tag};
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    oracle_philox4x32_10(ctr, key, out);
+    return out[lane & 3u];
+}
+
+/*
+ * Initial configurations at beta0 = 0 (Sec. 2.1, step 1): independent spins,
+ * +1 with probability 1/2. Spin = +1 iff the INIT word is < 2^31.
+ * slot[r] is the replica index k of the r-th replica in `s`.
+ */
+void oracle_init(int L, int64_t n, const int64_t *slot, uint64_t seed, int8_t *s)
+{
+    const int N = L * L, half = L / 2;
+    for (int64_t r = 0; r < n; r++) {
+        int8_t *S = s + (size_t)r * N;
+        uint32_t k = (uint32_t)slot[r];
+        for (int y = 0; y < L; y++)
+            for (int x = 0; x < L; x++) {
+                uint32_t c = (uint32_t)((x + y) & 1);
+                uint32_t b = (uint32_t)(y * half + (x >> 1));
+                uint32_t g = c * (uint32_t)(N / 2) + b;
+                uint32_t w = stream_word(seed, g >> 2, k, 0u, 0u, g & 3u);
+                S[y * L + x] = (w < 0x80000000u) ? 1 : -1;
+            }
+    }
+}
+
+/*
+ * theta Metropolis sweeps at one inverse temperature (Sec. 2.1 step 3,
+ * Sec. 3 "Spin updates"). Each sweep updates colour 0 first, then colour 1
+ * (checkerboard decomposition, Fig. 1): all sites of one colour are
+ * independent, so visiting them in raster order is one valid order.
+ *
+ * A flip changes the energy by dE = 2 s_i sum_nb s_j = 4 n - 8, where n is
+ * the number of the four neighbours aligned with s_i. Metropolis accepts with
+ * probability min(1, exp(-beta dE)): always for n <= 2, exp(-4 beta) for
+ * n = 3, exp(-8 beta) for n = 4. With x the SWEEP word, a flip with n = 3 is
+ * accepted iff x < T4, with n = 4 iff x < T8, where T = ceil(p * 2^32)
+ * (computed by the caller) makes Pr[x < T] = p up to 2^-32.
+ * Sweep number u runs from u0 to u0 + theta - 1.
+ */
+void oracle_sweep(int L, int64_t n, const int64_t *slot, uint64_t seed, int64_t u0,
+                  int theta, uint64_t T4, uint64_t T8, int8_t *s)
+{
+    const int N = L * L, half = L / 2;
+    for (int64_t r = 0; r < n; r++) {
+        int8_t *S = s + (size_t)r * N;
+        uint32_t k = (uint32_t)slot[r];
+        for (int sw = 0; sw < theta; sw++) {
+            uint32_t u = (uint32_t)(u0 + sw);
+            for (int c = 0; c < 2; c++) {
+                for (int y = 0; y < L; y++)
+                    for (int x = 0; x < L; x++) {
+                        if (((x + y) & 1) != c)
+                            continue;
+                        int si = S[y * L + x];
+                        int aligned = (S[y * L + (x + 1) % L] == si) +
+                                      (S[y * L + (x + L - 1) % L] == si) +
+                                      (S[((y + 1) % L) * L + x] == si) +
+                                      (S[((y + L - 1) % L) * L + x] == si);
+                        int flip;
+                        if (aligned <= 2) {
+                            flip = 1;  /* dE <= 0 */
+                        } else {
+                            uint32_t b = (uint32_t)(y * half + (x >> 1));
+                            uint32_t w = stream_word(seed, b >> 2, k, 2u * u + (uint32_t)c, 1u, b & 3u);
+                            uint64_t T = (aligned == 3) ? T4 : T8;
+                            flip = ((uint64_t)w < T);
+                        }
+                        if (flip)
+                            S[y * L + x] = (int8_t)(-si);
+                    }
+            }
+        }
+    }
+}
+
+/* Configurational energy E = -sum over bonds s_i s_j and magnetisation M. */
+void oracle_measure(int L, int64_t n, const int8_t *s, int64_t *E, int64_t *M)
+{
+    const int N = L * L;
+    for (int64_t r = 0; r < n; r++) {
+        const int8_t *S = s + (size_t)r * N;
+        int64_t e = 0, m = 0;
+        for (int y = 0; y < L; y++)
+            for (int x = 0; x < L; x++) {
+                int si = S[y * L + x];
+                e -= si * (S[y * L + (x + 1) % L] + S[((y + 1) % L) * L + x]);
+                m += si;
+            }
+        E[r] = e;
+        M[r] = m;
+    }
+}
+
+/* The resampling uniform word of each old slot j = 0..n-1 at step i. */
+void oracle_resample_words(uint64_t seed, int64_t step, int64_t n, uint32_t *out)
+{
+    for (int64_t j = 0; j < n; j++)
+        out[j] = stream_word(seed, (uint32_t)(j >> 2), (uint32_t)step, 0u, 2u, (unsigned)(j & 3));
+}
+
+/* Raw Philox block for tests: out[4*r .. 4*r+3] = Philox(ctr[4*r..], key). */
+void oracle_philox_many(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t *out)
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+    for (int64_t r = 0; r < n; r++)
+        oracle_philox4x32_10(ctr + 4 * r, key, out + 4 * r);
+}

@@ -1,0 +1,89 @@
+"""Pins for the oracle's adaptive inverse-temperature steps (Sec. 2.3) and
+its multi-histogram reweighting (Sec. 2.4, Eq. MHReq1).
+
+Independent facts: 0 <= alpha <= 1 with alpha = 1 at a zero step when
+R_{i-1} <= R; the realised overlap of every non-final step sits at the target
+(the bisection's invariant); the density of states sums to 2^N (Z at
+beta = 0); the reweighted ln Z, e and C agree with Kaufman; the 4 x 4 density
+of states agrees with exact enumeration.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from oracle.exact_ising import BruteForce, kaufman_lnZ, kaufman_observables
+from oracle.pa_oracle import PopulationAnnealing, overlap_alpha
+
+
+@pytest.fixture(scope="module")
+def run8():
+    pa = PopulationAnnealing(8, 2000, 10, beta_f=1.0, dbeta=0.0, seed=7, overlap=0.85)
+    pa.run()
+    return pa
+
+
+def test_alpha_bounds():
+    N = 64
+    H = np.zeros(N + 1, dtype=np.int64)
+    H[5:20] = np.arange(1, 16)
+    R = int(H.sum())
+    assert overlap_alpha(H, 5, 19, R, R, 0.0, N) == pytest.approx(1.0, abs=1e-15)
+    prev = 1.0
+    for d in [0.01, 0.05, 0.2, 1.0, 5.0]:
+        a = overlap_alpha(H, 5, 19, R, R, d, N)
+        assert 0.0 <= a <= prev + 1e-15
+        prev = a
+
+
+def test_realised_overlap_at_target(run8):
+    pa = run8
+    assert pa.rows[-1].beta == 1.0
+    n = len(pa.records)
+    assert 10 < n < 60
+    for i in range(1, n):
+        prev, rec = pa.records[i - 1], pa.records[i]
+        occ = np.nonzero(prev.H_E)[0]
+        a = overlap_alpha(prev.H_E, occ[0], occ[-1], pa.R, prev.R, rec.delta, pa.N)
+        assert a >= 0.85
+        if i < n - 1:
+            assert a - 0.85 < 1e-9, (i, a)
+        assert rec.beta == pytest.approx(pa.records[i - 1].beta + rec.delta, abs=1e-15) or i == n - 1
+
+
+def test_adaptive_observables_vs_kaufman(run8):
+    for r in run8.rows[1:]:
+        ex = kaufman_observables(8, r.beta)
+        assert r.e == pytest.approx(ex["e"], abs=0.03)
+        assert r.betaF_per_N == pytest.approx(ex["betaF_per_N"], abs=5e-3)
+
+
+def test_mhr_normalisation_and_lnZ(run8):
+    E, lno = run8.ln_dos()
+    ok = np.isfinite(lno)
+    m = lno[ok].max()
+    ln_total = m + math.log(float(np.exp(lno[ok] - m).sum()))
+    # Z(beta = 0) = sum_E Omega(E) = 2^N; ground states and their mirror are
+    # rarely sampled at N = 64, so allow a small deficit
+    assert ln_total == pytest.approx(64 * math.log(2.0), abs=0.05)
+    for b in [0.2, 0.44, 0.7, 1.0]:
+        row = run8.mhr([b])[0]
+        assert row["lnZ"] == pytest.approx(kaufman_lnZ(8, b), abs=0.15)
+        ex = kaufman_observables(8, b)
+        assert row["e"] == pytest.approx(ex["e"], abs=0.01)
+        assert row["C"] == pytest.approx(ex["C"], abs=0.05)
+
+
+def test_mhr_dos_4x4_vs_enumeration():
+    pa = PopulationAnnealing(4, 4000, 10, beta_f=1.0, dbeta=0.0, seed=9)
+    pa.run()
+    E, lno = pa.ln_dos()
+    dos = BruteForce(4).energy_dos()
+    checked = 0
+    for k in range(17):
+        e = -32 + 4 * k
+        # E > 4 is visited only near beta = 0 (few samples): compare the rest
+        if e in dos and e <= 4 and dos[e] >= 400 and np.isfinite(lno[k]):
+            assert math.exp(lno[k]) == pytest.approx(dos[e], rel=0.08), e
+            checked += 1
+    assert checked >= 5
