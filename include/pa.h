@@ -1,0 +1,180 @@
+/*
+ * pa.h -- C ABI of the GB300 population-annealing engine for the 2D
+ * ferromagnetic Ising model (Barash, Weigel, Borovsky, Janke, Shchur,
+ * "GPU accelerated population annealing algorithm", arXiv:1703.03676).
+ *
+ * One pa_ctx is one PA run (Sec. 2.1): R replicas of a periodic L x L Ising
+ * lattice (Eq. hamiltonian, J = 1) start from random spins at beta0 = 0 and
+ * are annealed to beta_f. Every temperature step resamples the population
+ * with the nearest-integer copy numbers of Eq. resampling-factors (normaliser
+ * Eq. Q), runs theta checkerboard Metropolis sweeps per replica (Sec. 3,
+ * "Spin updates", Fig. 1) and measures the population (Eq. observables,
+ * Eq. free-energy, Eq. entropy). Steps are fixed (beta_i = i * dbeta) or
+ * adaptive (Sec. 2.3); multi-histogram reweighting follows Sec. 2.4.
+ *
+ * Conventions shared by every entry point:
+ *  - All pointers named host_* or typed as host arrays are host memory owned
+ *    by the caller; the context owns all device memory it allocates.
+ *  - No call aborts, traps or prints. Every call returns a pa_status; a
+ *    failed call leaves the context valid for pa_destroy and for reading the
+ *    rows completed before the failure.
+ *  - Results are a pure function of pa_config: they do not depend on the
+ *    stream, on CUDA-graph use, on the thread-group shape or on batching.
+ *  - Work is enqueued on the stream given to pa_create (NULL: a stream the
+ *    context creates). Calls that return data synchronise that stream.
+ */
+#ifndef PA_GB300_H
+#define PA_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pa_ctx pa_ctx;
+
+typedef enum {
+    PA_OK = 0,
+    PA_DONE = 1,          /* pa_step: beta_f already reached, nothing done      */
+    PA_EINVAL = -1,       /* invalid argument or configuration                  */
+    PA_ENOMEM = -2,       /* device or host allocation failed                   */
+    PA_ECAPACITY = -3,    /* R_i exceeded the population capacity               */
+    PA_EEXTINCT = -4,     /* R_i == 0                                           */
+    PA_ETIMEOUT = -5,     /* a bounded device wait ran out                      */
+    PA_ECUDA = -6,        /* a CUDA runtime call failed                         */
+    PA_ESTATE = -7,       /* call not valid in the context's current state      */
+    PA_ESTALLED = -8      /* adaptive step found no positive step size          */
+} pa_status;
+
+typedef enum { PA_SPIN_INT8 = 0, PA_SPIN_BITS32 = 1 } pa_spin_format;
+
+typedef enum { PA_HIST_E = 0, PA_HIST_M = 1, PA_HIST_ESUM = 2 } pa_hist_kind;
+
+/* Run parameters (Sec. 3 "Further optimization and parameters": R, theta,
+ * beta0, beta_f, the seed; plus the step rule of Sec. 2.1 / 2.3). */
+typedef struct {
+    int32_t L;              /* lattice edge, even, 4 <= L <= 1024. PA_SPIN_BITS32
+                               needs L in {8, 16, 32} or L % 64 == 0              */
+    int32_t theta;          /* Metropolis sweeps per temperature step, >= 1       */
+    int64_t R;              /* target population size, >= 1                      */
+    double beta0;           /* must be 0 (Z_beta0 = 2^N, Eq. free-energy)         */
+    double beta_f;          /* final inverse temperature, 0 < beta_f <= 50        */
+    double dbeta;           /* > 0: fixed step; <= 0: adaptive step (Sec. 2.3)    */
+    double overlap;         /* adaptive target alpha*, 0 < alpha* < 1             */
+    uint64_t seed;          /* Philox4x32-10 key (low word, high word)            */
+    int32_t spin_format;    /* pa_spin_format                                     */
+    int32_t record_histograms; /* != 0: keep H_E and H_M of every step            */
+    int64_t capacity;       /* population buffer size; 0 -> ceil(1.05 R) + 1024   */
+    int32_t group_threads;  /* threads per replica in the sweep; 0 -> autotune    */
+    int32_t use_graph;      /* != 0: pa_run captures the fixed schedule as one
+                               CUDA graph                                       */
+    int32_t profile;        /* != 0: time every kernel phase with CUDA events     */
+    int32_t reserved[3];    /* must be 0                                          */
+} pa_config;
+
+/* One output row (Sec. 3 "Further optimization and parameters": beta, e, C,
+ * m, m^2, m^4, beta F / N, S / N, R, ln Q), plus the number of distinct
+ * families (initial replicas that still have descendants). */
+typedef struct {
+    double beta, e, C, abs_m, m2, m4, betaF_per_N, S_per_N, lnQ;
+    int64_t R;
+    int64_t families;
+} pa_obs;
+
+/* Per-step bookkeeping for tests: what the resampling of step `step` used. */
+typedef struct {
+    double beta;            /* beta_i                                             */
+    double delta;           /* beta step used in Q and tau_hat                    */
+    double S;               /* sum_k H_{i-1}[k] exp(-4 delta (k - kmin)), pairwise */
+    int64_t R;              /* R_i                                                */
+    int64_t R_prev;         /* R_{i-1}                                            */
+    int32_t kmin_prev;      /* lowest occupied energy level of population i-1     */
+    int32_t kmin, kmax;     /* occupied level range of population i               */
+    int32_t pad;
+    uint64_t T4, T8;        /* Metropolis thresholds ceil(exp(-4/8 beta_i) 2^32)  */
+    int64_t families;
+} pa_step_info;
+
+/* Create a run and generate its beta0 population (row 0). `cuda_stream` is
+ * a cudaStream_t borrowed for the context's lifetime, or NULL.
+ * Errors: PA_EINVAL (bad config), PA_ENOMEM, PA_ECUDA. */
+pa_status pa_create(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
+
+/* One temperature step (Sec. 2.1 steps 2-4). Fixed steps only enqueue work;
+ * adaptive steps synchronise once to read the previous histogram.
+ * Returns PA_DONE if beta_f was already reached. Device-side failures
+ * (capacity, extinction) are reported by this call or the next one that
+ * synchronises. */
+pa_status pa_step(pa_ctx *ctx);
+
+/* Steps until beta_f and synchronises. With use_graph the remaining fixed
+ * schedule runs as one CUDA-graph launch. */
+pa_status pa_run(pa_ctx *ctx);
+
+/* Wait for enqueued work and report any device-side failure. */
+pa_status pa_sync(pa_ctx *ctx);
+
+/* Number of completed rows (row 0 is beta0). Synchronises. */
+pa_status pa_num_rows(pa_ctx *ctx, int64_t *n_rows);
+
+/* Copy up to `cap` rows into host `rows`; *n_rows gets the number copied. */
+pa_status pa_observables(pa_ctx *ctx, pa_obs *rows, int64_t cap, int64_t *n_rows);
+
+/* Step bookkeeping of completed step `step` (0 <= step < rows). */
+pa_status pa_step_info_get(pa_ctx *ctx, int64_t step, pa_step_info *out);
+
+/* Histogram over levels 0..N (N = L*L) into host `out` (cap >= N + 1):
+ * PA_HIST_E: energy levels k = (E + 2N)/4 of step `step`;
+ * PA_HIST_M: magnetisation levels m = (M + N)/2 of step `step`;
+ * PA_HIST_ESUM: sum of the energy histograms of steps 0..last (Sec. 2.4;
+ * `step` ignored). Per-step kinds need record_histograms, else PA_ESTATE
+ * (the latest step is always available). */
+pa_status pa_histogram(pa_ctx *ctx, int64_t step, int32_t kind, int64_t *out, int64_t cap);
+
+/* Current population in natural layout: host_out[r*L*L + y*L + x] = +1 / -1
+ * for replica slot r < *n (cap is in replicas). */
+pa_status pa_population(pa_ctx *ctx, int8_t *host_out, int64_t cap, int64_t *n);
+
+/* Current per-replica energies, magnetisations and family ids. */
+pa_status pa_replicas(pa_ctx *ctx, int32_t *E, int32_t *M, int64_t *family, int64_t cap, int64_t *n);
+
+/* Multi-histogram reweighting (Sec. 2.4, Eq. MHReq1) over all completed
+ * rows, evaluated at n inverse temperatures: out[t] gets beta, e, C,
+ * beta F / N and S / N; the magnetisation fields are NaN. */
+pa_status pa_mhr(pa_ctx *ctx, const double *betas, int64_t n, pa_obs *out);
+
+/* ln Omega(E_k) for k = 0..N from Eq. MHReq1 (-inf where never visited). */
+pa_status pa_ln_dos(pa_ctx *ctx, double *out, int64_t cap);
+
+/* Accumulated device time in ms of each kernel phase (needs profile != 0):
+ * [0] tables (Q and copy tables), [1] counts, [2] scan, [3] parent scatter,
+ * [4] sweep, [5] stats, [6] init; launches[p] gets the launch count. */
+pa_status pa_phase_times(pa_ctx *ctx, double ms[7], int64_t launches[7]);
+
+/* The sweep launch shape chosen for this run (threads per replica, CTA size,
+ * persistent CTAs). */
+pa_status pa_launch_shape(pa_ctx *ctx, int32_t *group_threads, int32_t *block_threads, int32_t *grid_blocks);
+
+/* Device bytes a run with this configuration allocates (admission). */
+size_t pa_footprint_bytes(const pa_config *cfg);
+
+/* Default-initialise a config (every field zero except capacity rules). */
+void pa_config_default(pa_config *cfg);
+
+void pa_destroy(pa_ctx *ctx);
+const char *pa_strerror(pa_status s);
+
+/* ---- kernel-level entry points (device pointers, for tests) ----------- */
+
+/* Philox4x32-10 on the device: out[4r..4r+3] = Philox(ctr[4r..4r+3], key =
+ * (seed lo, seed hi)) for r < n. `dev_ctr` and `dev_out` are device
+ * pointers of 4n uint32 each. Synchronous on `cuda_stream`. */
+pa_status pa_philox_device(const uint32_t *dev_ctr, int64_t n, uint64_t seed, uint32_t *dev_out,
+                           void *cuda_stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PA_GB300_H */

@@ -1,0 +1,292 @@
+"""GB300 population-annealing engine for the 2D Ising model (arXiv:1703.03676).
+
+Thin ctypes binding of the C ABI in include/pa.h. Every step of the method
+runs in the CUDA kernels of ``csrc/``; this module only marshals arguments.
+There is no CPU fallback: without the compiled library or a GPU the calls
+raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = ["PAConfig", "PARun", "PAError", "lib", "philox_device", "footprint_bytes",
+           "SPIN_INT8", "SPIN_BITS32", "OBS_FIELDS"]
+
+SPIN_INT8, SPIN_BITS32 = 0, 1
+HIST_E, HIST_M, HIST_ESUM = 0, 1, 2
+
+_STATUS = {0: "ok", 1: "done", -1: "invalid argument", -2: "out of memory", -3: "capacity",
+           -4: "extinct", -5: "timeout", -6: "cuda error", -7: "invalid state", -8: "stalled"}
+
+
+class PAError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        super().__init__(f"{where}: {_STATUS.get(status, status)} ({status})")
+        self.status = status
+        self.kind = _STATUS.get(status, str(status))
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("theta", ctypes.c_int32), ("R", ctypes.c_int64),
+                ("beta0", ctypes.c_double), ("beta_f", ctypes.c_double), ("dbeta", ctypes.c_double),
+                ("overlap", ctypes.c_double), ("seed", ctypes.c_uint64), ("spin_format", ctypes.c_int32),
+                ("record_histograms", ctypes.c_int32), ("capacity", ctypes.c_int64),
+                ("group_threads", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 3)]
+
+
+class _Obs(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("e", ctypes.c_double), ("C", ctypes.c_double),
+                ("abs_m", ctypes.c_double), ("m2", ctypes.c_double), ("m4", ctypes.c_double),
+                ("betaF_per_N", ctypes.c_double), ("S_per_N", ctypes.c_double), ("lnQ", ctypes.c_double),
+                ("R", ctypes.c_int64), ("families", ctypes.c_int64)]
+
+
+class _StepInfo(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("delta", ctypes.c_double), ("S", ctypes.c_double),
+                ("R", ctypes.c_int64), ("R_prev", ctypes.c_int64), ("kmin_prev", ctypes.c_int32),
+                ("kmin", ctypes.c_int32), ("kmax", ctypes.c_int32), ("pad", ctypes.c_int32),
+                ("T4", ctypes.c_uint64), ("T8", ctypes.c_uint64), ("families", ctypes.c_int64)]
+
+
+OBS_FIELDS = [f for f, _ in _Obs._fields_]
+_OBS_DTYPE = np.dtype([(f, np.float64) for f in OBS_FIELDS[:9]] + [("R", np.int64), ("families", np.int64)])
+
+_lib = None
+
+# (name, restype, argtypes) of every exported symbol of include/pa.h
+_P = ctypes.c_void_p
+_I64P = ctypes.POINTER(ctypes.c_int64)
+SIGNATURES = [
+    ("pa_create", ctypes.c_int, [ctypes.POINTER(_Config), _P, ctypes.POINTER(_P)]),
+    ("pa_step", ctypes.c_int, [_P]),
+    ("pa_run", ctypes.c_int, [_P]),
+    ("pa_sync", ctypes.c_int, [_P]),
+    ("pa_num_rows", ctypes.c_int, [_P, _I64P]),
+    ("pa_observables", ctypes.c_int, [_P, ctypes.POINTER(_Obs), ctypes.c_int64, _I64P]),
+    ("pa_step_info_get", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(_StepInfo)]),
+    ("pa_histogram", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _I64P, ctypes.c_int64]),
+    ("pa_population", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int8), ctypes.c_int64, _I64P]),
+    ("pa_replicas", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _I64P,
+                                   ctypes.c_int64, _I64P]),
+    ("pa_mhr", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.POINTER(_Obs)]),
+    ("pa_ln_dos", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
+    ("pa_phase_times", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I64P]),
+    ("pa_launch_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
+                                       ctypes.POINTER(ctypes.c_int32)]),
+    ("pa_footprint_bytes", ctypes.c_size_t, [ctypes.POINTER(_Config)]),
+    ("pa_config_default", None, [ctypes.POINTER(_Config)]),
+    ("pa_destroy", None, [_P]),
+    ("pa_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("pa_philox_device", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_uint64, _P, _P]),
+]
+
+
+def lib() -> ctypes.CDLL:
+    """The engine library, built for sm_103a on first use."""
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libpa_gb300.so is missing and could not be built")
+        L = ctypes.CDLL(path)
+        for name, res, args in SIGNATURES:
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(st: int, where: str, ok=(0,)):
+    if st not in ok:
+        raise PAError(st, where)
+    return st
+
+
+def _stream_handle(stream):
+    if stream is None:
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("a CUDA device is required")
+        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return ctypes.c_void_p(stream)
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+@dataclass
+class PAConfig:
+    """Run parameters (see include/pa.h, pa_config)."""
+    L: int = 16
+    R: int = 1000
+    theta: int = 10
+    beta_f: float = 1.0
+    dbeta: float = 0.01          # <= 0: adaptive steps
+    overlap: float = 0.85
+    seed: int = 1
+    spin_format: int = SPIN_BITS32
+    record_histograms: bool = False
+    capacity: int = 0
+    group_threads: int = 0
+    use_graph: bool = True
+    profile: bool = False
+
+    def _c(self) -> _Config:
+        c = _Config()
+        c.L, c.theta, c.R = self.L, self.theta, self.R
+        c.beta0, c.beta_f, c.dbeta, c.overlap = 0.0, self.beta_f, self.dbeta, self.overlap
+        c.seed = self.seed & 0xFFFFFFFFFFFFFFFF
+        c.spin_format = self.spin_format
+        c.record_histograms = int(bool(self.record_histograms))
+        c.capacity = self.capacity
+        c.group_threads = self.group_threads
+        c.use_graph = int(bool(self.use_graph))
+        c.profile = int(bool(self.profile))
+        return c
+
+
+def footprint_bytes(cfg: PAConfig) -> int:
+    c = cfg._c()
+    return int(lib().pa_footprint_bytes(ctypes.byref(c)))
+
+
+class PARun:
+    """One population-annealing run on the GPU (a pa_ctx)."""
+
+    def __init__(self, cfg: PAConfig, stream=None):
+        self.cfg = cfg
+        self._lib = lib()
+        self._h = ctypes.c_void_p()
+        c = cfg._c()
+        _check(self._lib.pa_create(ctypes.byref(c), _stream_handle(stream), ctypes.byref(self._h)), "pa_create")
+        self.N = cfg.L * cfg.L
+
+    # -- lifecycle
+    def close(self):
+        if self._h:
+            self._lib.pa_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- stepping
+    def step(self) -> bool:
+        """One temperature step; False once beta_f was already reached."""
+        st = self._lib.pa_step(self._h)
+        _check(st, "pa_step", ok=(0, 1))
+        return st == 0
+
+    def run(self):
+        _check(self._lib.pa_run(self._h), "pa_run")
+        return self
+
+    def sync(self):
+        _check(self._lib.pa_sync(self._h), "pa_sync")
+
+    # -- results
+    def num_rows(self) -> int:
+        n = ctypes.c_int64()
+        _check(self._lib.pa_num_rows(self._h, ctypes.byref(n)), "pa_num_rows")
+        return n.value
+
+    def rows(self) -> np.ndarray:
+        """Observables per step as a structured array (fields OBS_FIELDS)."""
+        n = self.num_rows()
+        buf = (_Obs * max(n, 1))()
+        got = ctypes.c_int64()
+        _check(self._lib.pa_observables(self._h, buf, n, ctypes.byref(got)), "pa_observables")
+        out = np.zeros(got.value, dtype=_OBS_DTYPE)
+        for i in range(got.value):
+            for f in OBS_FIELDS:
+                out[f][i] = getattr(buf[i], f)
+        return out
+
+    def step_info(self, step: int) -> dict:
+        s = _StepInfo()
+        _check(self._lib.pa_step_info_get(self._h, step, ctypes.byref(s)), "pa_step_info_get")
+        return {f: getattr(s, f) for f, _ in _StepInfo._fields_ if f != "pad"}
+
+    def histogram(self, step: int, kind: int = HIST_E) -> np.ndarray:
+        out = np.zeros(self.N + 1, dtype=np.int64)
+        _check(self._lib.pa_histogram(self._h, step, kind, out.ctypes.data_as(_I64P), out.size), "pa_histogram")
+        return out
+
+    def population(self) -> np.ndarray:
+        """Current population as int8 +1/-1 of shape (R_i, L, L)."""
+        n = self.num_rows()
+        R = self.step_info(n - 1)["R"]
+        out = np.zeros((R, self.cfg.L, self.cfg.L), dtype=np.int8)
+        got = ctypes.c_int64()
+        _check(self._lib.pa_population(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), R,
+                                       ctypes.byref(got)), "pa_population")
+        return out[: got.value]
+
+    def replicas(self):
+        """(E, M, family) of the current population."""
+        n = self.num_rows()
+        R = self.step_info(n - 1)["R"]
+        E = np.zeros(R, dtype=np.int32)
+        M = np.zeros(R, dtype=np.int32)
+        F = np.zeros(R, dtype=np.int64)
+        got = ctypes.c_int64()
+        _check(self._lib.pa_replicas(self._h, E.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)),
+                                     M.ctypes.data_as(ctypes.POINTER(ctypes.c_int32)), F.ctypes.data_as(_I64P),
+                                     R, ctypes.byref(got)), "pa_replicas")
+        return E[: got.value], M[: got.value], F[: got.value]
+
+    def ln_dos(self) -> np.ndarray:
+        out = np.zeros(self.N + 1, dtype=np.float64)
+        _check(self._lib.pa_ln_dos(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size),
+               "pa_ln_dos")
+        return out
+
+    def mhr(self, betas) -> np.ndarray:
+        b = np.ascontiguousarray(betas, dtype=np.float64)
+        buf = (_Obs * max(b.size, 1))()
+        _check(self._lib.pa_mhr(self._h, b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), b.size, buf), "pa_mhr")
+        out = np.zeros(b.size, dtype=_OBS_DTYPE)
+        for i in range(b.size):
+            for f in OBS_FIELDS:
+                out[f][i] = getattr(buf[i], f)
+        return out
+
+    def phase_times(self):
+        ms = (ctypes.c_double * 7)()
+        n = (ctypes.c_int64 * 7)()
+        _check(self._lib.pa_phase_times(self._h, ms, n), "pa_phase_times")
+        names = ["tables", "counts", "scan", "parent", "sweep", "stats", "init"]
+        return {k: (ms[i], n[i]) for i, k in enumerate(names)}
+
+    def launch_shape(self):
+        g, b, n = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.pa_launch_shape(self._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(n)),
+               "pa_launch_shape")
+        return {"group_threads": g.value, "block_threads": b.value, "grid_blocks": n.value}
+
+
+def philox_device(ctr, seed: int, stream=None):
+    """Philox4x32-10 on the GPU: ctr is a CUDA int32/uint32 tensor of shape
+    (n, 4); returns a tensor of the same shape with the outputs."""
+    import torch
+    assert ctr.is_cuda and ctr.dtype in (torch.int32, torch.uint32) and ctr.is_contiguous()
+    out = torch.empty_like(ctr)
+    _check(lib().pa_philox_device(ctypes.c_void_p(ctr.data_ptr()), ctr.numel() // 4, seed & 0xFFFFFFFFFFFFFFFF,
+                                  ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "pa_philox_device")
+    return out

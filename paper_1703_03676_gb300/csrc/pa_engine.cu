@@ -1,0 +1,908 @@
+// Host side of the population-annealing engine and the C ABI of include/pa.h.
+//
+// The host owns what is sequential and FP64 (Sec. 2.1-2.4): the inverse
+// temperature schedule, the Metropolis thresholds ceil(exp(-4 beta) 2^32) and
+// ceil(exp(-8 beta) 2^32), the level weights t[d] = exp(-4 delta d), the
+// adaptive bisection on the histogram overlap (Sec. 2.3), ln Q, the
+// free energy and entropy (Eq. free-energy, Eq. entropy), the observables
+// (Eq. observables) from exact integer moment sums, and the multi-histogram
+// estimate of the density of states (Eq. MHReq1). Every other step of the
+// method runs in the kernels of pa_kernels.cu.
+//
+// This file must be compiled with -ffp-contract=off so that the FP64 tables
+// are evaluated exactly as written (no fused multiply-add).
+#include "../../include/pa.h"
+#include "pa_internal.cuh"
+
+#include <algorithm>
+#include <cmath>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+using pa::RunDev;
+using pa::StepDev;
+
+namespace {
+
+constexpr long long kMaxAdaptiveSteps = 1 << 16;
+constexpr long long kMaxRecordedHistSteps = 4096;
+
+inline __int128 i128_of(const unsigned long long* p)
+{
+    return (__int128)(((unsigned __int128)p[1] << 64) | p[0]);
+}
+
+// smallest power of two >= n
+inline long long pad_pow2(long long n)
+{
+    long long p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+// Pairwise tree (sum = left half + right half) over T[k] = H[k] w[k - kmin]
+// for k in [kmin, kmax], zero elsewhere, on [lo, lo + n) with n a power of
+// two. Subtrees outside [kmin, kmax] are exactly +0.0.
+double tree_sum(const std::vector<long long>& H, const std::vector<double>& w, int kmin, int kmax, long long lo,
+                long long n)
+{
+    if (lo + n <= kmin || lo > kmax) return 0.0;
+    if (n == 1) return (double)H[(size_t)lo] * w[(size_t)(lo - kmin)];
+    const double a = tree_sum(H, w, kmin, kmax, lo, n / 2);
+    const double b = tree_sum(H, w, kmin, kmax, lo + n / 2, n / 2);
+    return a + b;
+}
+
+// level weights exp(-(4 delta) d), d = 0..nd-1 (libm exp, one call each)
+void level_weights(double delta, int nd, std::vector<double>& w)
+{
+    w.resize((size_t)nd);
+    const double f = 4.0 * delta;
+    for (int d = 0; d < nd; d++) w[(size_t)d] = std::exp(-(f * (double)d));
+}
+
+uint64_t threshold(double beta, double dE)
+{
+    return (uint64_t)std::ceil(std::ldexp(std::exp(-dE * beta), 32));
+}
+
+}  // namespace
+
+struct pa_ctx {
+    pa_config cfg{};
+    RunDev h{};
+    pa::Launch ln{};
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int N = 0;
+    bool adaptive = false;
+    long long n_fixed = 0;        // fixed schedule: number of steps
+    long long max_steps = 0;      // record capacity (steps 0..max_steps)
+    long long hist_steps = 0;     // steps with recorded histograms
+    long long enq_step = 0;       // last step enqueued (0 = init)
+    long long done_rows = 0;      // rows whose records are on the host
+    bool done = false;            // beta_f reached
+    pa_status failed = PA_OK;     // sticky device failure
+    std::vector<double> betas;    // beta_i for i = 0..enq_step
+    std::vector<double> deltas;   // step size used by step i (0 for i = 0)
+    std::vector<uint64_t> T4, T8;
+    std::vector<StepDev> recs;    // host copies of rec[0..done_rows)
+    std::vector<void*> allocs;
+    void* h_stage = nullptr;      // pinned staging for adaptive uploads
+    size_t h_stage_bytes = 0;
+    cudaGraphExec_t graph = nullptr;
+    // profiling
+    std::vector<cudaEvent_t> ev;  // pairs per phase launch
+    std::vector<int> ev_phase;
+    double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    long long phase_n[7] = {0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+pa_status from_cuda(cudaError_t e)
+{
+    if (e == cudaSuccess) return PA_OK;
+    if (e == cudaErrorMemoryAllocation) return PA_ENOMEM;
+    return PA_ECUDA;
+}
+
+#define PA_CUDA(call)                                  \
+    do {                                               \
+        cudaError_t e_ = (call);                       \
+        if (e_ != cudaSuccess) return from_cuda(e_);   \
+    } while (0)
+
+bool bits_L_ok(int L)
+{
+    return L == 8 || L == 16 || L == 32 || L == 64 || L == 128 || L == 256 || L == 512;
+}
+
+pa_status validate(const pa_config& c)
+{
+    if (c.L < 4 || c.L > 1024 || (c.L & 1)) return PA_EINVAL;
+    if (c.theta < 1 || c.R < 1 || c.R > (1ll << 31)) return PA_EINVAL;
+    if (c.beta0 != 0.0) return PA_EINVAL;
+    if (!(c.beta_f > 0.0) || !(c.beta_f <= 50.0)) return PA_EINVAL;
+    if (c.spin_format != PA_SPIN_INT8 && c.spin_format != PA_SPIN_BITS32) return PA_EINVAL;
+    if (c.spin_format == PA_SPIN_BITS32 && !bits_L_ok(c.L)) return PA_EINVAL;
+    if (!(c.dbeta > 0.0)) {
+        if (!(c.overlap > 0.0 && c.overlap < 1.0)) return PA_EINVAL;
+    } else {
+        const double n = std::floor(c.beta_f / c.dbeta + 0.5);
+        if (n < 1 || n > 1e7) return PA_EINVAL;
+    }
+    if (c.capacity < 0 || (c.capacity > 0 && c.capacity < c.R)) return PA_EINVAL;
+    if (c.group_threads < 0 || c.group_threads > 32 || (c.group_threads & (c.group_threads - 1))) return PA_EINVAL;
+    if (c.reserved[0] || c.reserved[1] || c.reserved[2]) return PA_EINVAL;
+    return PA_OK;
+}
+
+long long capacity_of(const pa_config& c)
+{
+    return c.capacity > 0 ? c.capacity : (long long)std::ceil((double)c.R * 1.05) + 1024;
+}
+
+int words_of(const pa_config& c)
+{
+    const long long N = (long long)c.L * c.L;
+    if (c.spin_format == PA_SPIN_BITS32) return (int)(N / 32);
+    return (int)(((N + 15) / 16) * 4);  // bytes padded to 16, in words
+}
+
+// threads per replica: enough to fill the device, a power of two dividing
+// the plane's words (bit-packed) or the Philox blocks per plane (bytes)
+int auto_group(const pa_config& c)
+{
+    const long long N = (long long)c.L * c.L;
+    if (c.spin_format == PA_SPIN_BITS32) {
+        const long long wp = N / 64;
+        int g = 32;
+        while (g > 1 && wp % g) g >>= 1;
+        return g;
+    }
+    const long long qp = (N / 2 + 3) / 4;
+    int g = 1;
+    while (g < 32 && g * 2 <= qp) g <<= 1;
+    return g;
+}
+
+struct Sizes {
+    long long cap, ntiles, steps, hist_steps;
+    int N, words;
+};
+
+Sizes sizes_of(const pa_config& c)
+{
+    Sizes s{};
+    s.N = c.L * c.L;
+    s.cap = capacity_of(c);
+    s.ntiles = (s.cap + pa::kTile - 1) / pa::kTile;
+    s.words = words_of(c);
+    if (c.dbeta > 0.0) s.steps = (long long)std::floor(c.beta_f / c.dbeta + 0.5);
+    else s.steps = kMaxAdaptiveSteps;
+    s.hist_steps = c.record_histograms ? std::min(s.steps + 1, kMaxRecordedHistSteps) : 0;
+    return s;
+}
+
+size_t footprint(const pa_config& c)
+{
+    const Sizes s = sizes_of(c);
+    const size_t N1 = (size_t)s.N + 1;
+    size_t b = 0;
+    b += 2 * (size_t)s.cap * s.words * 4;           // pop
+    b += 2 * (size_t)s.cap * 4 * 3;                 // elev, mlev, fam
+    b += (size_t)s.cap * 4 * 3;                     // parent, cnt, loc
+    b += 2 * (size_t)s.ntiles * 4;                  // tile sums / offsets
+    b += 2 * 2 * N1 * 4;                            // H
+    b += N1 * 8 * 3 + N1 * 4;                       // Hsum, tw, U, F
+    b += 2 * (size_t)(s.steps + 1) * 4;             // thresholds
+    b += (size_t)(s.steps + 1) * sizeof(StepDev);   // records
+    b += (size_t)s.hist_steps * 2 * N1 * 4;         // recorded histograms
+    b += 64;                                        // status + work
+    return b;
+}
+
+template <class T>
+pa_status dev_alloc(pa_ctx* c, T** p, size_t count)
+{
+    void* q = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return e == cudaErrorMemoryAllocation ? PA_ENOMEM : PA_ECUDA;
+    }
+    c->allocs.push_back(q);
+    *p = (T*)q;
+    return PA_OK;
+}
+
+#define PA_TRY(x)                        \
+    do {                                 \
+        pa_status s_ = (x);              \
+        if (s_ != PA_OK) return s_;      \
+    } while (0)
+
+// ---------------------------------------------------------------- profiling
+pa_status prof_begin(pa_ctx* c, int phase, cudaEvent_t* out)
+{
+    *out = nullptr;
+    if (!c->cfg.profile) return PA_OK;
+    cudaEvent_t a;
+    PA_CUDA(cudaEventCreate(&a));
+    PA_CUDA(cudaEventRecord(a, c->stream));
+    c->ev.push_back(a);
+    c->ev_phase.push_back(phase);
+    *out = a;
+    return PA_OK;
+}
+
+pa_status prof_end(pa_ctx* c)
+{
+    if (!c->cfg.profile) return PA_OK;
+    cudaEvent_t b;
+    PA_CUDA(cudaEventCreate(&b));
+    PA_CUDA(cudaEventRecord(b, c->stream));
+    c->ev.push_back(b);
+    c->ev_phase.push_back(-1);
+    return PA_OK;
+}
+
+pa_status prof_collect(pa_ctx* c)
+{
+    for (size_t i = 0; i + 1 < c->ev.size(); i += 2) {
+        float ms = 0.f;
+        PA_CUDA(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+        const int ph = c->ev_phase[i];
+        c->phase_ms[ph] += ms;
+        c->phase_n[ph] += 1;
+    }
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+    c->ev_phase.clear();
+    return PA_OK;
+}
+
+#define PA_PHASE(ctx, ph, launch)                      \
+    do {                                               \
+        cudaEvent_t ev_;                               \
+        PA_TRY(prof_begin(ctx, ph, &ev_));             \
+        PA_CUDA(launch);                               \
+        PA_TRY(prof_end(ctx));                         \
+    } while (0)
+
+// ---------------------------------------------------------------- steps
+pa_status enqueue_kernels(pa_ctx* c, int step)
+{
+    const RunDev& h = c->h;
+    PA_PHASE(c, 0, pa::launch_tables(nullptr, h, step, c->stream));
+    PA_PHASE(c, 1, pa::launch_counts(nullptr, h, c->ln, step, c->stream));
+    PA_PHASE(c, 2, pa::launch_scan(nullptr, h, step, c->stream));
+    PA_PHASE(c, 3, pa::launch_parent(nullptr, h, c->ln, step, c->stream));
+    PA_PHASE(c, 4, pa::launch_sweep(nullptr, h, c->ln, step, c->stream));
+    PA_PHASE(c, 5, pa::launch_stats(nullptr, h, step, c->stream));
+    return PA_OK;
+}
+
+// Pull records rec[done_rows .. enq_step] to the host (synchronises).
+pa_status pull_records(pa_ctx* c)
+{
+    PA_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->cfg.profile) PA_TRY(prof_collect(c));
+    int st = 0;
+    PA_CUDA(cudaMemcpy(&st, c->h.status, sizeof(int), cudaMemcpyDeviceToHost));
+    long long last = c->enq_step;
+    if (st != 0) {
+        c->failed = (pa_status)st;
+        // the failing step left its record incomplete; keep the steps before it
+        long long good = c->done_rows;
+        std::vector<StepDev> tmp((size_t)(last + 1));
+        PA_CUDA(cudaMemcpy(tmp.data(), c->h.rec, sizeof(StepDev) * (size_t)(last + 1), cudaMemcpyDeviceToHost));
+        for (long long i = std::max<long long>(good, 1); i <= last; i++) {
+            if (tmp[(size_t)i].R > c->h.cap || tmp[(size_t)i].R == 0) {
+                last = i - 1;
+                break;
+            }
+        }
+    }
+    if (last + 1 > c->done_rows) {
+        const size_t n = (size_t)(last + 1 - c->done_rows);
+        c->recs.resize((size_t)(last + 1));
+        PA_CUDA(cudaMemcpy(c->recs.data() + c->done_rows, c->h.rec + c->done_rows, sizeof(StepDev) * n,
+                           cudaMemcpyDeviceToHost));
+        c->done_rows = last + 1;
+    }
+    return c->failed;
+}
+
+// Host FP64 of the adaptive step (Sec. 2.3): overlap alpha(delta) of the
+// histogram H of population i-1 (levels ascending), bisection to alpha*.
+double overlap_alpha(const std::vector<long long>& H, int kmin, int kmax, long long R, long long Rprev,
+                     double delta, long long P)
+{
+    std::vector<double> w;
+    level_weights(delta, kmax - kmin + 1, w);
+    const double S = tree_sum(H, w, kmin, kmax, 0, P);
+    double acc = 0.0;
+    for (int k = kmin; k <= kmax; k++) {
+        const double tau = ((double)R * w[(size_t)(k - kmin)]) / S;
+        acc += (double)H[(size_t)k] * std::min(1.0, tau);
+    }
+    return acc / (double)Rprev;
+}
+
+pa_status enqueue_step(pa_ctx* c)
+{
+    if (c->done) return PA_DONE;
+    const long long i = c->enq_step + 1;
+    if (i > c->max_steps) return PA_ESTATE;
+    double beta, delta;
+    bool final_step;
+    if (!c->adaptive) {
+        delta = c->cfg.dbeta;
+        beta = 0.0 + (double)i * c->cfg.dbeta;
+        final_step = (i == c->n_fixed);
+    } else {
+        // read population i-1: its record and the occupied histogram range
+        PA_TRY(pull_records(c));
+        const StepDev& pr = c->recs[(size_t)(i - 1)];
+        const int kmin = pr.kmin, kmax = pr.kmax;
+        const int nl = kmax - kmin + 1;
+        std::vector<uint32_t> hr((size_t)nl);
+        PA_CUDA(cudaMemcpy(hr.data(), c->h.H[(i - 1) & 1] + kmin, sizeof(uint32_t) * (size_t)nl,
+                           cudaMemcpyDeviceToHost));
+        std::vector<long long> H((size_t)c->N + 1, 0);
+        for (int k = 0; k < nl; k++) H[(size_t)(kmin + k)] = hr[(size_t)k];
+        const long long P = pad_pow2(c->N + 1);
+        const double bprev = c->betas[(size_t)(i - 1)];
+        const double dmax = c->cfg.beta_f - bprev;
+        const double target = c->cfg.overlap;
+        if (overlap_alpha(H, kmin, kmax, c->cfg.R, pr.R, dmax, P) >= target) {
+            delta = dmax;
+            final_step = true;
+            beta = c->cfg.beta_f;
+        } else {
+            double lo = 0.0, hi = dmax;
+            for (int it = 0; it < 60; it++) {
+                const double mid = 0.5 * (lo + hi);
+                if (overlap_alpha(H, kmin, kmax, c->cfg.R, pr.R, mid, P) >= target) lo = mid;
+                else hi = mid;
+            }
+            if (!(lo > 0.0)) return PA_ESTALLED;
+            delta = lo;
+            final_step = false;
+            beta = bprev + delta;
+        }
+        // level weights for this step and its thresholds
+        std::vector<double> w;
+        level_weights(delta, nl, w);
+        uint32_t thr[2];
+        const uint64_t t4 = threshold(beta, 4.0), t8 = threshold(beta, 8.0);
+        thr[0] = (uint32_t)(t4 - 1);
+        thr[1] = (uint32_t)(t8 - 1);
+        char* st = (char*)c->h_stage;
+        std::memcpy(st, w.data(), sizeof(double) * (size_t)nl);
+        std::memcpy(st + sizeof(double) * (size_t)nl, thr, sizeof(thr));
+        PA_CUDA(cudaMemcpyAsync(c->h.tw, st, sizeof(double) * (size_t)nl, cudaMemcpyHostToDevice, c->stream));
+        PA_CUDA(cudaMemcpyAsync(c->h.thr + 2 * i, st + sizeof(double) * (size_t)nl, sizeof(thr),
+                                cudaMemcpyHostToDevice, c->stream));
+        c->T4.push_back(t4);
+        c->T8.push_back(t8);
+    }
+    PA_TRY(enqueue_kernels(c, (int)i));
+    c->betas.push_back(beta);
+    c->deltas.push_back(delta);
+    c->enq_step = i;
+    if (final_step) c->done = true;
+    return PA_OK;
+}
+
+// ---------------------------------------------------------------- rows
+void make_row(const pa_ctx* c, long long i, double sum_lnQ, double lnQ, pa_obs* o)
+{
+    const StepDev& r = c->recs[(size_t)i];
+    const double beta = c->betas[(size_t)i];
+    const double fR = (double)r.R, fN = (double)c->N;
+    const __int128 sE = i128_of(r.sums + 0), sE2 = i128_of(r.sums + 2), sAM = i128_of(r.sums + 4),
+                   sM2 = i128_of(r.sums + 6), sM4 = i128_of(r.sums + 8);
+    const __int128 num = (__int128)r.R * sE2 - sE * sE;
+    o->beta = beta;
+    o->e = (double)sE / (fR * fN);
+    o->C = beta * beta * (double)num / (fR * fR * fN);
+    o->abs_m = (double)sAM / (fR * fN);
+    o->m2 = (double)sM2 / (fR * fN * fN);
+    o->m4 = (double)sM4 / (fR * fN * fN * fN * fN);
+    o->betaF_per_N = -(fN * std::log(2.0) + sum_lnQ) / fN;
+    o->S_per_N = beta * o->e - o->betaF_per_N;
+    o->lnQ = lnQ;
+    o->R = r.R;
+    o->families = (int64_t)r.fam;
+}
+
+double lnQ_of(const pa_ctx* c, long long i)
+{
+    if (i == 0) return 0.0;
+    const StepDev& r = c->recs[(size_t)i];
+    const double Emin = (double)(-2ll * c->N + 4ll * r.kmin_prev);
+    return (std::log(r.S) - std::log((double)r.R_prev)) - c->deltas[(size_t)i] * Emin;
+}
+
+void all_rows(const pa_ctx* c, std::vector<pa_obs>& rows)
+{
+    rows.resize((size_t)c->done_rows);
+    double sum = 0.0;
+    for (long long i = 0; i < c->done_rows; i++) {
+        const double q = lnQ_of(c, i);
+        sum += q;
+        make_row(c, i, sum, q, &rows[(size_t)i]);
+    }
+}
+
+pa_status free_all(pa_ctx* c)
+{
+    if (c->graph) cudaGraphExecDestroy(c->graph);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    return PA_OK;
+}
+
+}  // namespace
+
+// ======================================================================= ABI
+extern "C" {
+
+void pa_config_default(pa_config* cfg)
+{
+    if (!cfg) return;
+    std::memset(cfg, 0, sizeof(*cfg));
+    cfg->L = 16;
+    cfg->theta = 10;
+    cfg->R = 1000;
+    cfg->beta_f = 1.0;
+    cfg->dbeta = 0.01;
+    cfg->overlap = 0.85;
+    cfg->seed = 1;
+    cfg->spin_format = PA_SPIN_BITS32;
+    cfg->use_graph = 1;
+}
+
+const char* pa_strerror(pa_status s)
+{
+    switch (s) {
+    case PA_OK: return "ok";
+    case PA_DONE: return "beta_f reached";
+    case PA_EINVAL: return "invalid argument";
+    case PA_ENOMEM: return "out of memory";
+    case PA_ECAPACITY: return "population exceeded its capacity";
+    case PA_EEXTINCT: return "population died out";
+    case PA_ETIMEOUT: return "bounded device wait timed out";
+    case PA_ECUDA: return "CUDA runtime error";
+    case PA_ESTATE: return "invalid state for this call";
+    case PA_ESTALLED: return "adaptive step found no positive step size";
+    }
+    return "unknown status";
+}
+
+size_t pa_footprint_bytes(const pa_config* cfg)
+{
+    if (!cfg || validate(*cfg) != PA_OK) return 0;
+    return footprint(*cfg);
+}
+
+pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
+{
+    if (!cfg || !out) return PA_EINVAL;
+    *out = nullptr;
+    PA_TRY(validate(*cfg));
+    pa_ctx* c = new (std::nothrow) pa_ctx();
+    if (!c) return PA_ENOMEM;
+    c->cfg = *cfg;
+    auto fail = [&](pa_status s) {
+        free_all(c);
+        delete c;
+        return s;
+    };
+    if (cuda_stream) {
+        c->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(PA_ECUDA);
+        c->own_stream = true;
+    }
+    const Sizes s = sizes_of(*cfg);
+    c->N = s.N;
+    c->adaptive = !(cfg->dbeta > 0.0);
+    c->n_fixed = c->adaptive ? 0 : s.steps;
+    c->max_steps = s.steps;
+    c->hist_steps = s.hist_steps;
+    RunDev& h = c->h;
+    h.L = cfg->L;
+    h.N = s.N;
+    h.half = cfg->L / 2;
+    h.words = s.words;
+    h.wp = s.N / 64;
+    h.theta = cfg->theta;
+    h.fmt = cfg->spin_format;
+    h.gt = cfg->group_threads ? cfg->group_threads : auto_group(*cfg);
+    if (h.fmt == PA_SPIN_BITS32 && (s.N / 64) % h.gt) return fail(PA_EINVAL);
+    h.R = cfg->R;
+    h.cap = s.cap;
+    h.k0 = (unsigned)(cfg->seed & 0xffffffffu);
+    h.k1 = (unsigned)(cfg->seed >> 32);
+    h.ntiles = (int)s.ntiles;
+    h.record_hist = cfg->record_histograms ? 1 : 0;
+    h.hist_steps = (int)s.hist_steps;
+    const size_t N1 = (size_t)s.N + 1;
+    pa_status st = PA_OK;
+#define PA_ALLOC(p, n)                            \
+    do {                                          \
+        st = dev_alloc(c, &(p), (n));             \
+        if (st != PA_OK) return fail(st);         \
+    } while (0)
+    for (int b = 0; b < 2; b++) {
+        PA_ALLOC(h.pop[b], (size_t)s.cap * s.words);
+        PA_ALLOC(h.elev[b], (size_t)s.cap);
+        PA_ALLOC(h.mlev[b], (size_t)s.cap);
+        PA_ALLOC(h.fam[b], (size_t)s.cap);
+        PA_ALLOC(h.H[b], 2 * N1);
+    }
+    PA_ALLOC(h.parent, (size_t)s.cap);
+    PA_ALLOC(h.cnt, (size_t)s.cap);
+    PA_ALLOC(h.loc, (size_t)s.cap);
+    PA_ALLOC(h.tile_sum, (size_t)s.ntiles);
+    PA_ALLOC(h.tile_off, (size_t)s.ntiles);
+    PA_ALLOC(h.Hsum, N1);
+    PA_ALLOC(h.tw, N1);
+    PA_ALLOC(h.F, N1);
+    PA_ALLOC(h.U, N1);
+    PA_ALLOC(h.thr, 2 * (size_t)(s.steps + 1));
+    PA_ALLOC(h.rec, (size_t)(s.steps + 1));
+    if (s.hist_steps) PA_ALLOC(h.hist_rec, (size_t)s.hist_steps * 2 * N1);
+    PA_ALLOC(h.status, 4);
+    PA_ALLOC(h.work, 4);
+#undef PA_ALLOC
+    if (cudaMemsetAsync(h.H[0], 0, 2 * N1 * 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(h.H[1], 0, 2 * N1 * 4, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(h.Hsum, 0, N1 * 8, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(h.rec, 0, sizeof(StepDev) * (size_t)(s.steps + 1), c->stream) != cudaSuccess ||
+        cudaMemsetAsync(h.status, 0, 16, c->stream) != cudaSuccess ||
+        cudaMemsetAsync(h.work, 0, 16, c->stream) != cudaSuccess)
+        return fail(PA_ECUDA);
+    // staging for adaptive uploads (level weights + thresholds)
+    c->h_stage_bytes = N1 * sizeof(double) + 64;
+    if (cudaMallocHost(&c->h_stage, c->h_stage_bytes) != cudaSuccess) return fail(PA_ENOMEM);
+    c->betas.push_back(0.0);
+    c->deltas.push_back(0.0);
+    c->T4.push_back(1ull << 32);
+    c->T8.push_back(1ull << 32);
+    if (!c->adaptive) {
+        // all thresholds and the (fixed) level weights up front
+        std::vector<uint32_t> thr(2 * (size_t)(s.steps + 1), 0xffffffffu);
+        for (long long i = 1; i <= s.steps; i++) {
+            const double beta = 0.0 + (double)i * cfg->dbeta;
+            const uint64_t t4 = threshold(beta, 4.0), t8 = threshold(beta, 8.0);
+            thr[2 * (size_t)i] = (uint32_t)(t4 - 1);
+            thr[2 * (size_t)i + 1] = (uint32_t)(t8 - 1);
+            c->T4.push_back(t4);
+            c->T8.push_back(t8);
+        }
+        std::vector<double> w;
+        level_weights(cfg->dbeta, (int)N1, w);
+        if (cudaMemcpy(h.thr, thr.data(), thr.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(h.tw, w.data(), N1 * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(PA_ECUDA);
+    }
+    if (pa::plan_sweep(h, &c->ln) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PA_EINVAL);
+    }
+    // step 0: random configurations at beta0 = 0, measured (no sweeps)
+    {
+        cudaEvent_t ev;
+        if (prof_begin(c, 6, &ev) != PA_OK) return fail(PA_ECUDA);
+        if (pa::launch_init(nullptr, h, c->ln, c->stream) != cudaSuccess) return fail(PA_ECUDA);
+        if (prof_end(c) != PA_OK) return fail(PA_ECUDA);
+        if (prof_begin(c, 5, &ev) != PA_OK) return fail(PA_ECUDA);
+        if (pa::launch_stats(nullptr, h, 0, c->stream) != cudaSuccess) return fail(PA_ECUDA);
+        if (prof_end(c) != PA_OK) return fail(PA_ECUDA);
+    }
+    c->enq_step = 0;
+    *out = c;
+    return PA_OK;
+}
+
+pa_status pa_step(pa_ctx* c)
+{
+    if (!c) return PA_EINVAL;
+    if (c->failed != PA_OK) return c->failed;
+    return enqueue_step(c);
+}
+
+pa_status pa_sync(pa_ctx* c)
+{
+    if (!c) return PA_EINVAL;
+    return pull_records(c);
+}
+
+pa_status pa_run(pa_ctx* c)
+{
+    if (!c) return PA_EINVAL;
+    if (c->failed != PA_OK) return c->failed;
+    if (!c->adaptive && c->cfg.use_graph && !c->cfg.profile && !c->done) {
+        // capture the remaining fixed schedule once and launch it as one graph
+        cudaStream_t cap = nullptr;
+        PA_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaEvent_t dep;
+        PA_CUDA(cudaEventCreateWithFlags(&dep, cudaEventDisableTiming));
+        cudaStream_t saved = c->stream;
+        c->stream = cap;
+        cudaGraph_t g = nullptr;
+        pa_status st = PA_OK;
+        const long long from = c->enq_step;
+        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = PA_ECUDA;
+        while (st == PA_OK && !c->done) st = enqueue_step(c);
+        if (st == PA_DONE) st = PA_OK;
+        cudaError_t ce = cudaStreamEndCapture(cap, &g);
+        c->stream = saved;
+        if (st == PA_OK && ce != cudaSuccess) st = PA_ECUDA;
+        if (st == PA_OK && cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) st = PA_ECUDA;
+        if (g) cudaGraphDestroy(g);
+        cudaStreamDestroy(cap);
+        cudaEventDestroy(dep);
+        if (st != PA_OK) {
+            // roll back the host schedule so a plain run can follow
+            c->betas.resize((size_t)from + 1);
+            c->deltas.resize((size_t)from + 1);
+            c->enq_step = from;
+            c->done = false;
+            return st;
+        }
+        PA_CUDA(cudaGraphLaunch(c->graph, c->stream));
+        return pull_records(c);
+    }
+    pa_status st = PA_OK;
+    while (st == PA_OK) st = enqueue_step(c);
+    if (st != PA_DONE) return st;
+    return pull_records(c);
+}
+
+pa_status pa_num_rows(pa_ctx* c, int64_t* n)
+{
+    if (!c || !n) return PA_EINVAL;
+    pa_status st = pull_records(c);
+    *n = c->done_rows;
+    return st == PA_OK || st == PA_ECAPACITY || st == PA_EEXTINCT ? PA_OK : st;
+}
+
+pa_status pa_observables(pa_ctx* c, pa_obs* rows, int64_t cap, int64_t* n)
+{
+    if (!c || !n || (cap > 0 && !rows)) return PA_EINVAL;
+    pa_status st = pull_records(c);
+    if (st != PA_OK && st != PA_ECAPACITY && st != PA_EEXTINCT) return st;
+    std::vector<pa_obs> all;
+    all_rows(c, all);
+    const long long m = std::min<long long>(cap, (long long)all.size());
+    for (long long i = 0; i < m; i++) rows[i] = all[(size_t)i];
+    *n = m;
+    return PA_OK;
+}
+
+pa_status pa_step_info_get(pa_ctx* c, int64_t step, pa_step_info* out)
+{
+    if (!c || !out) return PA_EINVAL;
+    pull_records(c);
+    if (step < 0 || step >= c->done_rows) return PA_EINVAL;
+    const StepDev& r = c->recs[(size_t)step];
+    out->beta = c->betas[(size_t)step];
+    out->delta = c->deltas[(size_t)step];
+    out->S = r.S;
+    out->R = r.R;
+    out->R_prev = r.R_prev;
+    out->kmin_prev = r.kmin_prev;
+    out->kmin = r.kmin;
+    out->kmax = r.kmax;
+    out->pad = 0;
+    out->T4 = c->T4[(size_t)step];
+    out->T8 = c->T8[(size_t)step];
+    out->families = (int64_t)r.fam;
+    return PA_OK;
+}
+
+pa_status pa_histogram(pa_ctx* c, int64_t step, int32_t kind, int64_t* out, int64_t cap)
+{
+    if (!c || !out || cap < c->N + 1) return PA_EINVAL;
+    pull_records(c);
+    const size_t N1 = (size_t)c->N + 1;
+    if (kind == PA_HIST_ESUM) {
+        std::vector<unsigned long long> t(N1);
+        PA_CUDA(cudaMemcpy(t.data(), c->h.Hsum, N1 * 8, cudaMemcpyDeviceToHost));
+        for (size_t k = 0; k < N1; k++) out[k] = (int64_t)t[k];
+        return PA_OK;
+    }
+    if (kind != PA_HIST_E && kind != PA_HIST_M) return PA_EINVAL;
+    if (step < 0 || step >= c->done_rows) return PA_EINVAL;
+    std::vector<uint32_t> t(N1);
+    const uint32_t* src = nullptr;
+    if (c->h.hist_rec && step < c->hist_steps) src = c->h.hist_rec + (size_t)step * 2 * N1;
+    else if (step == c->done_rows - 1 && c->failed == PA_OK) src = c->h.H[step & 1];
+    else return PA_ESTATE;
+    PA_CUDA(cudaMemcpy(t.data(), src + (kind == PA_HIST_M ? N1 : 0), N1 * 4, cudaMemcpyDeviceToHost));
+    for (size_t k = 0; k < N1; k++) out[k] = (int64_t)t[k];
+    return PA_OK;
+}
+
+pa_status pa_population(pa_ctx* c, int8_t* host_out, int64_t cap, int64_t* n)
+{
+    if (!c || !n) return PA_EINVAL;
+    pa_status st = pull_records(c);
+    if (st != PA_OK) return PA_ESTATE;
+    const long long last = c->done_rows - 1;
+    const long long R = c->recs[(size_t)last].R;
+    const int L = c->cfg.L, N = c->N, half = L / 2;
+    const long long m = std::min<long long>(cap, R);
+    std::vector<uint32_t> buf((size_t)m * c->h.words);
+    if (m > 0)
+        PA_CUDA(cudaMemcpy(buf.data(), c->h.pop[last & 1], buf.size() * 4, cudaMemcpyDeviceToHost));
+    for (long long r = 0; r < m; r++) {
+        const uint32_t* w = buf.data() + (size_t)r * c->h.words;
+        const uint8_t* bytes = (const uint8_t*)w;
+        for (int y = 0; y < L; y++)
+            for (int x = 0; x < L; x++) {
+                const int col = (x + y) & 1, b = y * half + (x >> 1);
+                int up;
+                if (c->h.fmt == PA_SPIN_BITS32) up = (w[col * (N / 64) + (b >> 5)] >> (b & 31)) & 1u;
+                else up = bytes[col * (N / 2) + b];
+                host_out[(size_t)r * N + (size_t)y * L + x] = up ? 1 : -1;
+            }
+    }
+    *n = m;
+    return PA_OK;
+}
+
+pa_status pa_replicas(pa_ctx* c, int32_t* E, int32_t* M, int64_t* family, int64_t cap, int64_t* n)
+{
+    if (!c || !n) return PA_EINVAL;
+    pa_status st = pull_records(c);
+    if (st != PA_OK) return PA_ESTATE;
+    const long long last = c->done_rows - 1;
+    const long long R = c->recs[(size_t)last].R;
+    const long long m = std::min<long long>(cap, R);
+    std::vector<int32_t> ev((size_t)m), mv((size_t)m);
+    std::vector<uint32_t> fv((size_t)m);
+    if (m > 0) {
+        PA_CUDA(cudaMemcpy(ev.data(), c->h.elev[last & 1], (size_t)m * 4, cudaMemcpyDeviceToHost));
+        PA_CUDA(cudaMemcpy(mv.data(), c->h.mlev[last & 1], (size_t)m * 4, cudaMemcpyDeviceToHost));
+        PA_CUDA(cudaMemcpy(fv.data(), c->h.fam[last & 1], (size_t)m * 4, cudaMemcpyDeviceToHost));
+    }
+    for (long long r = 0; r < m; r++) {
+        if (E) E[r] = 4 * ev[(size_t)r] - 2 * c->N;
+        if (M) M[r] = 2 * mv[(size_t)r] - c->N;
+        if (family) family[r] = fv[(size_t)r];
+    }
+    *n = m;
+    return PA_OK;
+}
+
+// Eq. MHReq1: Omega(E) = sum_i P_i(E) / sum_i R_i exp(beta_i F_i - beta_i E),
+// evaluated in logarithms: ln Omega_k = ln Hsum_k - LSE_i(ln R_i + beta_i F_i
+// - beta_i E_k) with beta_i F_i = -(N ln 2 + sum_{l<=i} ln Q_l); row 0 (an
+// exact beta = 0 sample) included.
+pa_status pa_ln_dos(pa_ctx* c, double* out, int64_t cap)
+{
+    if (!c || !out || cap < c->N + 1) return PA_EINVAL;
+    pa_status st = pull_records(c);
+    if (st != PA_OK && st != PA_ECAPACITY && st != PA_EEXTINCT) return st;
+    const size_t N1 = (size_t)c->N + 1;
+    std::vector<unsigned long long> hs(N1);
+    PA_CUDA(cudaMemcpy(hs.data(), c->h.Hsum, N1 * 8, cudaMemcpyDeviceToHost));
+    std::vector<pa_obs> rows;
+    all_rows(c, rows);
+    const size_t nr = rows.size();
+    std::vector<double> lnR(nr), bF(nr), b(nr);
+    for (size_t i = 0; i < nr; i++) {
+        lnR[i] = std::log((double)rows[i].R);
+        bF[i] = rows[i].betaF_per_N * (double)c->N;
+        b[i] = rows[i].beta;
+    }
+    std::vector<double> a(nr);
+    for (size_t k = 0; k < N1; k++) {
+        if (hs[k] == 0) {
+            out[k] = -INFINITY;
+            continue;
+        }
+        const double Ek = (double)(-2ll * c->N + 4ll * (long long)k);
+        double m = -INFINITY;
+        for (size_t i = 0; i < nr; i++) {
+            a[i] = lnR[i] + bF[i] - b[i] * Ek;
+            m = std::max(m, a[i]);
+        }
+        double s = 0.0;
+        for (size_t i = 0; i < nr; i++) s += std::exp(a[i] - m);
+        out[k] = std::log((double)hs[k]) - (m + std::log(s));
+    }
+    return PA_OK;
+}
+
+pa_status pa_mhr(pa_ctx* c, const double* betas, int64_t n, pa_obs* out)
+{
+    if (!c || (n > 0 && (!betas || !out))) return PA_EINVAL;
+    const size_t N1 = (size_t)c->N + 1;
+    std::vector<double> lno(N1);
+    PA_TRY(pa_ln_dos(c, lno.data(), (int64_t)N1));
+    for (int64_t t = 0; t < n; t++) {
+        const double beta = betas[t];
+        double m = -INFINITY;
+        for (size_t k = 0; k < N1; k++) {
+            if (!std::isfinite(lno[k])) continue;
+            const double Ek = (double)(-2ll * c->N + 4ll * (long long)k);
+            m = std::max(m, lno[k] - beta * Ek);
+        }
+        double Z = 0.0, e1 = 0.0, e2 = 0.0;
+        for (size_t k = 0; k < N1; k++) {
+            if (!std::isfinite(lno[k])) continue;
+            const double Ek = (double)(-2ll * c->N + 4ll * (long long)k);
+            const double w = std::exp(lno[k] - beta * Ek - m);
+            Z += w;
+            e1 += w * Ek;
+            e2 += w * Ek * Ek;
+        }
+        e1 /= Z;
+        e2 /= Z;
+        const double lnZ = m + std::log(Z);
+        pa_obs& o = out[t];
+        o.beta = beta;
+        o.e = e1 / (double)c->N;
+        o.C = beta * beta * (e2 - e1 * e1) / (double)c->N;
+        o.abs_m = o.m2 = o.m4 = NAN;
+        o.betaF_per_N = -lnZ / (double)c->N;
+        o.S_per_N = beta * o.e - o.betaF_per_N;
+        o.lnQ = NAN;
+        o.R = 0;
+        o.families = 0;
+    }
+    return PA_OK;
+}
+
+pa_status pa_phase_times(pa_ctx* c, double ms[7], int64_t launches[7])
+{
+    if (!c || !ms || !launches) return PA_EINVAL;
+    PA_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->cfg.profile) PA_TRY(prof_collect(c));
+    for (int p = 0; p < 7; p++) {
+        ms[p] = c->phase_ms[p];
+        launches[p] = c->phase_n[p];
+    }
+    return PA_OK;
+}
+
+pa_status pa_launch_shape(pa_ctx* c, int32_t* gt, int32_t* bt, int32_t* gb)
+{
+    if (!c) return PA_EINVAL;
+    if (gt) *gt = c->h.gt;
+    if (bt) *bt = c->ln.sweep_threads;
+    if (gb) *gb = c->ln.sweep_blocks;
+    return PA_OK;
+}
+
+void pa_destroy(pa_ctx* c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->stream);
+    free_all(c);
+    delete c;
+}
+
+pa_status pa_philox_device(const uint32_t* ctr, int64_t n, uint64_t seed, uint32_t* out, void* stream)
+{
+    if (n < 0 || (n > 0 && (!ctr || !out))) return PA_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    PA_CUDA(pa::launch_philox(ctr, n, pa::PhiloxKey{(unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32)}, out, s));
+    PA_CUDA(cudaStreamSynchronize(s));
+    return PA_OK;
+}
+
+}  // extern "C"

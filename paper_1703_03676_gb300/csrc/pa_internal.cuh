@@ -1,0 +1,129 @@
+// Internal declarations shared by the engine's kernels and its host code.
+//
+// Layout of one run in HBM (all buffers sized by the population capacity
+// `cap`, so R_i may fluctuate without reallocation):
+//   pop[2]      spins, ping-pong between steps. Bit-packed format: per
+//               replica 2 * N/64 uint32 words, colour plane 0 then plane 1,
+//               site b of a plane at bit b&31 of word b>>5 (bit 1 = spin +1).
+//               Byte format: per replica N bytes (0/1), plane 0 then plane 1,
+//               padded to a multiple of 16 bytes.
+//   elev/mlev   per-slot energy level k = (E+2N)/4 and magnetisation level
+//               m = (M+N)/2 of the population in pop[] with the same index.
+//   fam[2]      family id (index of the initial replica) per slot.
+//   cnt, loc    copy numbers r_j and their exclusive prefix within a tile.
+//   tile_sum/off  per-tile totals and their exclusive scan.
+//   parent      old slot of every new slot.
+//   H[2]        energy and magnetisation histograms (2 x (N+1) uint32),
+//               ping-pong by step parity.
+//   Hsum        running sum of energy histograms (Sec. 2.4).
+//   tw          level weights t[d] = exp(-4 delta d) (host-computed).
+//   F, U        copy tables per energy level: floor(tau_hat), ceil(frac 2^32).
+//   thr         per step: T4 - 1 and T8 - 1 (uint32).
+//   rec         per-step records read back by the host.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pa {
+
+constexpr int kTile = 1024;            // replicas per copy-count tile
+constexpr int kTileThreads = 256;      // 4 replicas (one Philox block) per thread
+constexpr int kOneCta = 1024;          // threads of the per-run single-CTA kernels
+
+// device status word values (mirror pa_status)
+constexpr int kStatusCapacity = -3;
+constexpr int kStatusExtinct = -4;
+
+struct StepDev {
+    long long R;              // R_i
+    long long R_prev;         // R_{i-1}
+    double S;                 // pairwise normaliser used by this step
+    int kmin_prev;            // lowest occupied level of population i-1
+    int kmin, kmax;           // occupied levels of population i
+    int pad0;
+    unsigned long long fam;   // number of distinct families in population i
+    // sum E, sum E^2, sum |M|, sum M^2, sum M^4 as signed 128-bit (lo, hi)
+    unsigned long long sums[10];
+};
+
+struct RunDev {
+    int L, N, half;           // lattice edge, sites, L/2
+    int words;                // uint32 words per replica in pop[]
+    int wp;                   // bit-packed words per colour plane (N/64)
+    int theta;
+    int fmt;                  // 0 byte spins, 1 bit-packed
+    int gt;                   // threads per replica in the sweep
+    long long R, cap;
+    unsigned k0, k1;          // Philox key
+    int ntiles;               // copy-count tiles covering cap
+    int record_hist;
+    int hist_steps;           // steps with a slot in hist_rec
+    uint32_t* pop[2];
+    int32_t* elev[2];
+    int32_t* mlev[2];
+    uint32_t* fam[2];
+    uint32_t* parent;
+    uint32_t* cnt;
+    uint32_t* loc;
+    uint32_t* tile_sum;
+    uint32_t* tile_off;
+    uint32_t* H[2];
+    unsigned long long* Hsum;
+    double* tw;
+    uint32_t* F;
+    unsigned long long* U;
+    uint32_t* thr;
+    StepDev* rec;
+    uint32_t* hist_rec;       // (steps) x 2 x (N+1) when record_hist
+    int* status;
+    unsigned* work;           // persistent-kernel work counter
+};
+
+// ---------------------------------------------------------------- Philox
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 products with the published multipliers, high halves XORed with
+// the other two counter words and the round key; Weyl key increments.
+struct PhiloxKey {
+    unsigned k0, k1;
+};
+
+__device__ __forceinline__ uint4 philox10(uint4 c, PhiloxKey key)
+{
+    unsigned k0 = key.k0, k1 = key.k1;
+#pragma unroll
+    for (int r = 0; r < 10; r++) {
+        const unsigned long long p0 = (unsigned long long)0xD2511F53u * c.x;
+        const unsigned long long p1 = (unsigned long long)0xCD9E8D57u * c.z;
+        c = make_uint4((unsigned)(p1 >> 32) ^ c.y ^ k0, (unsigned)p1,
+                       (unsigned)(p0 >> 32) ^ c.w ^ k1, (unsigned)p0);
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    return c;
+}
+
+// stream tags of the counter's fourth word
+constexpr unsigned kTagInit = 0u, kTagSweep = 1u, kTagResample = 2u;
+
+// ---------------------------------------------------------------- launches
+struct Launch {
+    int sweep_blocks, sweep_threads;  // persistent sweep grid
+    int count_blocks;                 // tiles over cap
+    size_t sweep_smem;
+};
+
+cudaError_t launch_init(const RunDev* d_run, const RunDev& h, const Launch& ln, cudaStream_t s);
+cudaError_t launch_tables(const RunDev* d_run, const RunDev& h, int step, cudaStream_t s);
+cudaError_t launch_counts(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s);
+cudaError_t launch_scan(const RunDev* d_run, const RunDev& h, int step, cudaStream_t s);
+cudaError_t launch_parent(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s);
+cudaError_t launch_sweep(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s);
+cudaError_t launch_stats(const RunDev* d_run, const RunDev& h, int step, cudaStream_t s);
+cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint32_t* out, cudaStream_t s);
+
+// Sweep launch shape: persistent CTAs for this run (group threads gt).
+cudaError_t plan_sweep(const RunDev& h, Launch* ln);
+const void* sweep_kernel(const RunDev& h, bool init);
+
+}  // namespace pa

@@ -1,0 +1,876 @@
+// Device kernels of the population-annealing engine (2D Ising, sm_103a).
+//
+// One temperature step i >= 1 (Sec. 2.1 steps 2-4) is six launches:
+//   k_tables  (1 CTA)   S = pairwise sum of H_{i-1}[k] t[k-kmin]  (Eq. Q) and
+//                       the copy tables F = floor(tau_hat), U = ceil(frac 2^32)
+//                       (Eq. resampling-factors)
+//   k_counts            r_j = F[k_j] + [x_j < U[k_j]], tile-local prefix
+//   k_scan    (1 CTA)   tile offsets, R_i, capacity check
+//   k_parent            parent[o_j + c] = j for c < r_j
+//   k_sweep             gather parent into shared memory, theta checkerboard
+//                       Metropolis sweeps, E and M by popcount, histograms
+//   k_stats   (1 CTA)   integer moments, occupied range, running histogram sum
+// Everything except S and the copy tables is integer arithmetic; S and the
+// tables use only IEEE +, x, / with round-to-nearest intrinsics in a fixed
+// order, so every result is reproducible bit for bit.
+//
+// Every kernel returns at once if the run's status word is set, so a failure
+// at step i leaves rows 0..i-1 intact and the rest of a captured graph inert.
+#include "pa_internal.cuh"
+
+#include <cstdio>
+
+namespace pa {
+
+// ======================================================== bit-packed geometry
+constexpr uint32_t row_first_mask(int hb)
+{
+    uint32_t m = 0;
+    for (int p = 0; p < 32; p += hb) m |= 1u << p;
+    return m;
+}
+constexpr uint32_t row_odd_mask(int hb)
+{
+    uint32_t m = 0;
+    for (int p = 0; p < 32; p++)
+        if ((p / hb) & 1) m |= 1u << p;
+    return m;
+}
+
+// Colour plane c holds the N/2 sites with (x + y) & 1 == c; site (x, y) is
+// bit b = y*L/2 + x/2 of its plane. All four neighbours lie in the other
+// plane: (x, y+-1) at b +- L/2, and along the row the same b plus b+1 when x
+// is odd or b-1 when x is even (cyclic within the row).
+template <int L>
+struct Geo {
+    static constexpr int N = L * L;
+    static constexpr int HB = L / 2;           // bits per plane row
+    static constexpr int WP = N / 64;          // words per plane
+    static constexpr int WORDS = N / 32;       // words per replica
+    static constexpr bool WIDE = HB >= 32;     // a row spans whole words
+    static constexpr int WR = WIDE ? HB / 32 : 1;
+    static constexpr uint32_t FIRST = WIDE ? 0u : row_first_mask(HB);
+    static constexpr uint32_t LAST = WIDE ? 0u : (row_first_mask(HB) << (HB - 1));
+    static constexpr uint32_t ODD = WIDE ? 0u : row_odd_mask(HB);
+};
+
+// The four neighbour words of word w of plane c; O is the other plane.
+template <int L>
+__device__ __forceinline__ void neighbours(const uint32_t* __restrict__ O, int c, int w, uint32_t& same,
+                                           uint32_t& side, uint32_t& up, uint32_t& down)
+{
+    using G = Geo<L>;
+    same = O[w];
+    if constexpr (G::WIDE) {
+        up = O[w >= G::WR ? w - G::WR : w - G::WR + G::WP];
+        down = O[w + G::WR < G::WP ? w + G::WR : w + G::WR - G::WP];
+        const int y = w / G::WR;
+        const int pos = w - y * G::WR;
+        if ((c + y) & 1) {  // x odd: neighbours at h and h + 1
+            const int wn = (pos == G::WR - 1) ? w - (G::WR - 1) : w + 1;
+            side = __funnelshift_r(same, O[wn], 1);
+        } else {            // x even: neighbours at h and h - 1
+            const int wv = (pos == 0) ? w + (G::WR - 1) : w - 1;
+            side = __funnelshift_l(O[wv], same, 1);
+        }
+    } else {
+        // several rows per word; word-row parity is even (32/HB is even)
+        const uint32_t prev = O[w > 0 ? w - 1 : G::WP - 1];
+        const uint32_t next = O[w + 1 < G::WP ? w + 1 : 0];
+        up = (same << G::HB) | (prev >> (32 - G::HB));
+        down = (same >> G::HB) | (next << (32 - G::HB));
+        const uint32_t plus = ((same >> 1) & ~G::LAST) | ((same << (G::HB - 1)) & G::LAST);
+        const uint32_t minus = ((same << 1) & ~G::FIRST) | ((same >> (G::HB - 1)) & G::FIRST);
+        // colour 0: odd rows have x odd; colour 1: even rows have x odd
+        side = c ? ((plus & ~G::ODD) | (minus & G::ODD)) : ((plus & G::ODD) | (minus & ~G::ODD));
+    }
+}
+
+// One Metropolis update of the 32 sites of word s (all of one colour).
+// A site with n aligned neighbours flips with certainty if n <= 2 (dE <= 0),
+// with x <= T4-1 if n = 3 and x <= T8-1 if n = 4, x the SWEEP word of the
+// site: counter (b>>2, k, 2u + c, 1), lane b&3. Bit-sliced counting of the
+// disagreeing neighbours d1..d4 gives "at least two disagree" (n <= 2) and
+// "none disagrees" (n = 4) for all 32 sites at once.
+__device__ __forceinline__ uint32_t metropolis_word(uint32_t s, uint32_t same, uint32_t side, uint32_t up,
+                                                    uint32_t down, unsigned c0, unsigned k, unsigned c2,
+                                                    uint32_t t4m1, uint32_t t8m1, PhiloxKey key)
+{
+    const uint32_t d1 = s ^ same, d2 = s ^ side, d3 = s ^ up, d4 = s ^ down;
+    const uint32_t a = d1 ^ d2, b = d1 & d2, cc = d3 ^ d4, e = d3 & d4;
+    const uint32_t ge2 = b | e | (a & cc);
+    const uint32_t any = d1 | d2 | d3 | d4;
+    uint32_t acc4 = 0, acc8 = 0;
+#pragma unroll
+    for (int q = 0; q < 8; q++) {
+        const uint4 x = philox10(make_uint4(c0 + q, k, c2, kTagSweep), key);
+        acc4 |= ((uint32_t)(x.x <= t4m1) << (4 * q)) | ((uint32_t)(x.y <= t4m1) << (4 * q + 1)) |
+                ((uint32_t)(x.z <= t4m1) << (4 * q + 2)) | ((uint32_t)(x.w <= t4m1) << (4 * q + 3));
+        acc8 |= ((uint32_t)(x.x <= t8m1) << (4 * q)) | ((uint32_t)(x.y <= t8m1) << (4 * q + 1)) |
+                ((uint32_t)(x.z <= t8m1) << (4 * q + 2)) | ((uint32_t)(x.w <= t8m1) << (4 * q + 3));
+    }
+    const uint32_t flip = ge2 | (acc4 & any & ~ge2) | (acc8 & ~any);
+    return s ^ flip;
+}
+
+// ======================================================== shared epilogue
+// Record a finished replica: levels, histograms, family.
+__device__ __forceinline__ void record_replica(const RunDev& r, int nxt, long long k, unsigned anti, unsigned ups,
+                                               uint32_t family)
+{
+    const int kl = (int)(anti >> 1);  // (E + 2N)/4 with E = 2*anti - 2N
+    r.elev[nxt][k] = kl;
+    r.mlev[nxt][k] = (int)ups;        // (M + N)/2 = number of up spins
+    r.fam[nxt][k] = family;
+    atomicAdd(&r.H[nxt][kl], 1u);
+    atomicAdd(&r.H[nxt][r.N + 1 + ups], 1u);
+}
+
+template <int G>
+__device__ __forceinline__ unsigned group_sum(unsigned v)
+{
+#pragma unroll
+    for (int off = G / 2; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+}
+
+template <int WORDS, int G>
+__device__ __forceinline__ void copy_words(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, int gl)
+{
+    if constexpr (WORDS % 4 == 0) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(src);
+        uint4* d4 = reinterpret_cast<uint4*>(dst);
+        for (int i = gl; i < WORDS / 4; i += G) d4[i] = s4[i];
+    } else {
+        for (int i = gl; i < WORDS; i += G) dst[i] = src[i];
+    }
+}
+
+// anti-parallel bonds and up spins of the replica in shared memory
+template <int L, int G>
+__device__ __forceinline__ void measure_bits(const uint32_t* sp, int gl, unsigned& anti, unsigned& ups)
+{
+    using Gm = Geo<L>;
+    anti = 0;
+    ups = 0;
+    for (int w = gl; w < Gm::WP; w += G) {
+        uint32_t same, side, up, down;
+        neighbours<L>(sp + Gm::WP, 0, w, same, side, up, down);
+        const uint32_t s = sp[w];
+        anti += __popc(s ^ same) + __popc(s ^ side) + __popc(s ^ up) + __popc(s ^ down);
+        ups += __popc(s) + __popc(sp[Gm::WP + w]);
+    }
+}
+
+// ======================================================== bit-packed kernels
+// Persistent warps: each warp takes 32/G replicas at a time from the run's
+// work counter; G threads share one replica held in shared memory, so the
+// colour phases synchronise with __syncwarp only.
+template <int L, int G>
+__global__ void __launch_bounds__(256) k_init_bits(const __grid_constant__ RunDev r)
+{
+    using Gm = Geo<L>;
+    constexpr int RPW = 32 / G;
+    extern __shared__ uint32_t smem[];
+    if (*r.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / G, gl = lane % G;
+    uint32_t* sp = smem + (warp * RPW + g) * Gm::WORDS;
+    const PhiloxKey key{r.k0, r.k1};
+    const long long R0 = r.R;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= R0) break;
+        const long long k = (long long)base + g;
+        const bool active = k < R0;
+        if (active) {
+            // INIT stream: site g = c*N/2 + b, counter (g>>2, k, 0, 0), spin up iff x < 2^31
+            for (int i = gl; i < Gm::WORDS; i += G) {
+                const int c = i / Gm::WP, w = i - c * Gm::WP;
+                const unsigned c0 = (unsigned)(c * (Gm::N / 8) + 8 * w);
+                uint32_t word = 0;
+#pragma unroll
+                for (int q = 0; q < 8; q++) {
+                    const uint4 x = philox10(make_uint4(c0 + q, (unsigned)k, 0u, kTagInit), key);
+                    word |= ((x.x >> 31) ^ 1u) << (4 * q) | ((x.y >> 31) ^ 1u) << (4 * q + 1) |
+                            ((x.z >> 31) ^ 1u) << (4 * q + 2) | ((x.w >> 31) ^ 1u) << (4 * q + 3);
+                }
+                sp[i] = word;
+            }
+        }
+        __syncwarp();
+        unsigned anti = 0, ups = 0;
+        if (active) measure_bits<L, G>(sp, gl, anti, ups);
+        anti = group_sum<G>(anti);
+        ups = group_sum<G>(ups);
+        if (active) {
+            copy_words<Gm::WORDS, G>(r.pop[0] + (size_t)k * Gm::WORDS, sp, gl);
+            if (gl == 0) record_replica(r, 0, k, anti, ups, (uint32_t)k);
+        }
+        __syncwarp();
+    }
+}
+
+template <int L, int G>
+__global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunDev r, int step)
+{
+    using Gm = Geo<L>;
+    constexpr int RPW = 32 / G;
+    constexpr int WPT = Gm::WP / G;  // words per thread per plane
+    static_assert(Gm::WP % G == 0, "group must divide the plane");
+    extern __shared__ uint32_t smem[];
+    if (*r.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / G, gl = lane % G;
+    uint32_t* sp = smem + (warp * RPW + g) * Gm::WORDS;
+    const int cur = (step - 1) & 1, nxt = step & 1;
+    const long long Ri = r.rec[step].R;
+    const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
+    const PhiloxKey key{r.k0, r.k1};
+    const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
+    const int theta = r.theta;
+    unsigned families = 0;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= Ri) break;
+        const long long k = (long long)base + g;
+        const bool active = k < Ri;
+        uint32_t p = 0;
+        if (active) {
+            p = r.parent[k];
+            copy_words<Gm::WORDS, G>(sp, r.pop[cur] + (size_t)p * Gm::WORDS, gl);
+        }
+        __syncwarp();
+        for (int sw = 0; sw < theta; sw++) {
+            const unsigned u = u0 + (unsigned)sw;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                if (active) {
+                    uint32_t* P = sp + c * Gm::WP;
+                    const uint32_t* O = sp + (1 - c) * Gm::WP;
+                    const unsigned c2 = 2u * u + (unsigned)c;
+#pragma unroll 2
+                    for (int m = 0; m < WPT; m++) {
+                        const int w = gl + m * G;
+                        uint32_t same, side, up, down;
+                        neighbours<L>(O, c, w, same, side, up, down);
+                        P[w] = metropolis_word(P[w], same, side, up, down, 8u * (unsigned)w, (unsigned)k, c2,
+                                               t4m1, t8m1, key);
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        unsigned anti = 0, ups = 0;
+        if (active) measure_bits<L, G>(sp, gl, anti, ups);
+        anti = group_sum<G>(anti);
+        ups = group_sum<G>(ups);
+        if (active) {
+            copy_words<Gm::WORDS, G>(r.pop[nxt] + (size_t)k * Gm::WORDS, sp, gl);
+            if (gl == 0) {
+                const uint32_t f = r.fam[cur][p];
+                record_replica(r, nxt, k, anti, ups, f);
+                families += (k == 0 || r.fam[cur][r.parent[k - 1]] != f) ? 1u : 0u;
+            }
+        }
+        __syncwarp();
+    }
+    families = group_sum<32>(families);
+    if (lane == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
+}
+
+// ======================================================== byte-spin kernels
+// Same RNG streams and update rule with one byte per spin (any even L >= 4).
+// Thread handles the sites of one Philox block (4 consecutive b) at a time.
+__device__ __forceinline__ int nb_index_side(int b, int c, int L, int half)
+{
+    const int y = b / half, h = b - y * half;
+    const int xodd = (c + y) & 1;
+    const int h2 = xodd ? (h + 1 == half ? 0 : h + 1) : (h == 0 ? half - 1 : h - 1);
+    return y * half + h2;
+}
+
+template <int G>
+__device__ __forceinline__ void measure_bytes(const uint8_t* sp, int L, int gl, unsigned& anti, unsigned& ups)
+{
+    const int N = L * L, half = L / 2, NP = N / 2;
+    const uint8_t* o = sp + NP;
+    anti = 0;
+    ups = 0;
+    for (int b = gl; b < NP; b += G) {
+        const int s = sp[b];
+        const int y = b / half, h = b - y * half;
+        const int up = ((y == 0 ? L - 1 : y - 1)) * half + h;
+        const int dn = ((y == L - 1 ? 0 : y + 1)) * half + h;
+        anti += (unsigned)((o[b] != s) + (o[nb_index_side(b, 0, L, half)] != s) + (o[up] != s) + (o[dn] != s));
+        ups += (unsigned)(s + o[b]);
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_init_bytes(const __grid_constant__ RunDev r)
+{
+    constexpr int RPW = 32 / G;
+    extern __shared__ uint32_t smem[];
+    if (*r.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / G, gl = lane % G;
+    uint8_t* sp = reinterpret_cast<uint8_t*>(smem + (warp * RPW + g) * r.words);
+    const PhiloxKey key{r.k0, r.k1};
+    const long long R0 = r.R;
+    const int N = r.N, NP = N / 2;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= R0) break;
+        const long long k = (long long)base + g;
+        const bool active = k < R0;
+        if (active) {
+            for (int gq = gl; gq < (N + 3) / 4; gq += G) {
+                const uint4 x = philox10(make_uint4((unsigned)gq, (unsigned)k, 0u, kTagInit), key);
+                const unsigned xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int l = 0; l < 4; l++) {
+                    const int gi = 4 * gq + l;  // = c*N/2 + b
+                    if (gi < N) sp[gi] = (uint8_t)(xs[l] < 0x80000000u);
+                }
+            }
+        }
+        (void)NP;
+        __syncwarp();
+        unsigned anti = 0, ups = 0;
+        if (active) measure_bytes<G>(sp, r.L, gl, anti, ups);
+        anti = group_sum<G>(anti);
+        ups = group_sum<G>(ups);
+        if (active) {
+            uint32_t* dst = r.pop[0] + (size_t)k * r.words;
+            const uint32_t* s32 = reinterpret_cast<const uint32_t*>(sp);
+            for (int i = gl; i < r.words; i += G) dst[i] = s32[i];
+            if (gl == 0) record_replica(r, 0, k, anti, ups, (uint32_t)k);
+        }
+        __syncwarp();
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ RunDev r, int step)
+{
+    constexpr int RPW = 32 / G;
+    extern __shared__ uint32_t smem[];
+    if (*r.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / G, gl = lane % G;
+    uint8_t* sp = reinterpret_cast<uint8_t*>(smem + (warp * RPW + g) * r.words);
+    const int cur = (step - 1) & 1, nxt = step & 1;
+    const long long Ri = r.rec[step].R;
+    const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
+    const PhiloxKey key{r.k0, r.k1};
+    const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
+    const int L = r.L, half = r.half, NP = r.N / 2, QP = (NP + 3) / 4;
+    unsigned families = 0;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= Ri) break;
+        const long long k = (long long)base + g;
+        const bool active = k < Ri;
+        uint32_t p = 0;
+        if (active) {
+            p = r.parent[k];
+            const uint32_t* src = r.pop[cur] + (size_t)p * r.words;
+            uint32_t* s32 = reinterpret_cast<uint32_t*>(sp);
+            for (int i = gl; i < r.words; i += G) s32[i] = src[i];
+        }
+        __syncwarp();
+        for (int sw = 0; sw < r.theta; sw++) {
+            const unsigned u = u0 + (unsigned)sw;
+            for (int c = 0; c < 2; c++) {
+                if (active) {
+                    uint8_t* P = sp + c * NP;
+                    const uint8_t* O = sp + (1 - c) * NP;
+                    for (int q = gl; q < QP; q += G) {
+                        const uint4 x = philox10(make_uint4((unsigned)q, (unsigned)k, 2u * u + (unsigned)c, kTagSweep),
+                                                 key);
+                        const unsigned xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                        for (int l = 0; l < 4; l++) {
+                            const int b = 4 * q + l;
+                            if (b < NP) {
+                                const int s = P[b];
+                                const int y = b / half, h = b - y * half;
+                                const int up = (y == 0 ? L - 1 : y - 1) * half + h;
+                                const int dn = (y == L - 1 ? 0 : y + 1) * half + h;
+                                const int n = (O[b] == s) + (O[nb_index_side(b, c, L, half)] == s) + (O[up] == s) +
+                                              (O[dn] == s);
+                                bool flip = n <= 2;
+                                if (n == 3) flip = xs[l] <= t4m1;
+                                if (n == 4) flip = xs[l] <= t8m1;
+                                if (flip) P[b] = (uint8_t)(s ^ 1);
+                            }
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        unsigned anti = 0, ups = 0;
+        if (active) measure_bytes<G>(sp, L, gl, anti, ups);
+        anti = group_sum<G>(anti);
+        ups = group_sum<G>(ups);
+        if (active) {
+            uint32_t* dst = r.pop[nxt] + (size_t)k * r.words;
+            const uint32_t* s32 = reinterpret_cast<const uint32_t*>(sp);
+            for (int i = gl; i < r.words; i += G) dst[i] = s32[i];
+            if (gl == 0) {
+                const uint32_t f = r.fam[cur][p];
+                record_replica(r, nxt, k, anti, ups, f);
+                families += (k == 0 || r.fam[cur][r.parent[k - 1]] != f) ? 1u : 0u;
+            }
+        }
+        __syncwarp();
+    }
+    families = group_sum<32>(families);
+    if (lane == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
+}
+
+// ======================================================== resampling kernels
+__device__ __forceinline__ int pad_pow2(int n)
+{
+    int p = 1;
+    while (p < n) p <<= 1;
+    return p;
+}
+
+// S = pairwise tree over T[k] = H[k] t[k - kmin] (k in [kmin, kmax], 0
+// elsewhere) padded to a power of two, then the copy tables over [kmin, kmax].
+// Thread t sums the aligned block [t*chunk, (t+1)*chunk) with a carry stack
+// (the block's subtree), then a shared-memory tree joins neighbours.
+__global__ void __launch_bounds__(kOneCta) k_tables(const __grid_constant__ RunDev r, int step)
+{
+    __shared__ double s[kOneCta];
+    if (*r.status) return;
+    const int t = threadIdx.x;
+    const StepDev& prev = r.rec[step - 1];
+    const int kmin = prev.kmin, kmax = prev.kmax;
+    const uint32_t* H = r.H[(step - 1) & 1];
+    const double* tw = r.tw;
+    const int P = pad_pow2(r.N + 1);
+    const int nthr = P < kOneCta ? P : kOneCta;
+    const int chunk = P / nthr;
+    double v = 0.0;
+    if (t < nthr) {
+        const int lo = t * chunk, hi = lo + chunk;  // [lo, hi)
+        if (hi > kmin && lo <= kmax) {
+            double stk[24];
+            int top = 0;
+            for (int e = 0; e < chunk; e++) {
+                const int kk = lo + e;
+                double x = (kk >= kmin && kk <= kmax) ? __dmul_rn((double)H[kk], tw[kk - kmin]) : 0.0;
+                for (int m = e; m & 1; m >>= 1) x = __dadd_rn(stk[--top], x);
+                stk[top++] = x;
+            }
+            v = stk[0];
+        }
+    }
+    s[t] = v;
+    __syncthreads();
+    for (int n = nthr; n > 1; n >>= 1) {
+        double x = 0.0;
+        if (t < n / 2) x = __dadd_rn(s[2 * t], s[2 * t + 1]);
+        __syncthreads();
+        if (t < n / 2) s[t] = x;
+        __syncthreads();
+    }
+    const double S = s[0];
+    const double Rd = (double)r.R;
+    for (int kk = kmin + t; kk <= kmax; kk += kOneCta) {
+        const double tau = __ddiv_rn(__dmul_rn(Rd, tw[kk - kmin]), S);
+        const double F = floor(tau);
+        const double frac = __dsub_rn(tau, F);
+        r.F[kk] = (uint32_t)F;
+        r.U[kk] = (unsigned long long)ceil(__dmul_rn(frac, 4294967296.0));
+    }
+    uint32_t* Hn = r.H[step & 1];
+    for (int i = t; i < 2 * (r.N + 1); i += kOneCta) Hn[i] = 0u;
+    if (t == 0) {
+        r.rec[step].S = S;
+        r.rec[step].kmin_prev = kmin;
+        r.rec[step].fam = 0ull;
+        *r.work = 0u;
+    }
+}
+
+// Copy numbers of the old population (Eq. resampling-factors): one Philox
+// block serves 4 consecutive old slots j (RESAMPLE stream (j>>2, i, 0, 2)).
+__global__ void __launch_bounds__(kTileThreads) k_counts(const __grid_constant__ RunDev r, int step)
+{
+    __shared__ uint32_t wsum[kTileThreads / 32];
+    if (*r.status) return;
+    const long long Rp = r.rec[step - 1].R;
+    const long long tile0 = (long long)blockIdx.x * kTile;
+    if (tile0 >= Rp) return;
+    const int cur = (step - 1) & 1;
+    const long long j0 = tile0 + 4 * threadIdx.x;
+    uint32_t c[4] = {0u, 0u, 0u, 0u};
+    if (j0 < Rp) {
+        const uint4 x = philox10(make_uint4((unsigned)(j0 >> 2), (unsigned)step, 0u, kTagResample),
+                                 PhiloxKey{r.k0, r.k1});
+        const unsigned xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int l = 0; l < 4; l++) {
+            const long long j = j0 + l;
+            if (j < Rp) {
+                const int lv = r.elev[cur][j];
+                c[l] = r.F[lv] + (((unsigned long long)xs[l] < r.U[lv]) ? 1u : 0u);
+            }
+        }
+    }
+    const uint32_t tsum = c[0] + c[1] + c[2] + c[3];
+    // block exclusive scan of tsum
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t incl = tsum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) wsum[warp] = incl;
+    __syncthreads();
+    uint32_t wbase = 0;
+    for (int w = 0; w < warp; w++) wbase += wsum[w];
+    uint32_t run = wbase + incl - tsum;
+#pragma unroll
+    for (int l = 0; l < 4; l++) {
+        const long long j = j0 + l;
+        if (j < Rp) {
+            r.cnt[j] = c[l];
+            r.loc[j] = run;
+        }
+        run += c[l];
+    }
+    if (threadIdx.x == kTileThreads - 1) {
+        uint32_t tot = 0;
+        for (int w = 0; w < kTileThreads / 32; w++) tot += wsum[w];
+        r.tile_sum[blockIdx.x] = tot;
+    }
+}
+
+// Exclusive scan of the tile totals; R_i and the capacity check.
+__global__ void __launch_bounds__(kOneCta) k_scan(const __grid_constant__ RunDev r, int step)
+{
+    __shared__ unsigned long long part[kOneCta];
+    if (*r.status) return;
+    const int t = threadIdx.x;
+    const long long Rp = r.rec[step - 1].R;
+    const int ntiles = (int)((Rp + kTile - 1) / kTile);
+    const int per = (ntiles + kOneCta - 1) / kOneCta;
+    const int lo = t * per, hi = min(lo + per, ntiles);
+    unsigned long long sum = 0;
+    for (int i = lo; i < hi; i++) sum += r.tile_sum[i];
+    part[t] = sum;
+    __syncthreads();
+    // inclusive Hillis-Steele scan over the 1024 partial sums
+    for (int off = 1; off < kOneCta; off <<= 1) {
+        const unsigned long long y = t >= off ? part[t - off] : 0ull;
+        __syncthreads();
+        part[t] += y;
+        __syncthreads();
+    }
+    unsigned long long run = part[t] - sum;
+    for (int i = lo; i < hi; i++) {
+        r.tile_off[i] = (uint32_t)run;
+        run += r.tile_sum[i];
+    }
+    if (t == 0) {
+        const unsigned long long Ri = part[kOneCta - 1];
+        r.rec[step].R = (long long)Ri;
+        r.rec[step].R_prev = Rp;
+        if ((long long)Ri > r.cap) *r.status = kStatusCapacity;
+        else if (Ri == 0) *r.status = kStatusExtinct;
+    }
+}
+
+// parent[o_j + c] = j for c < r_j: new slots keep the order of old slots.
+__global__ void __launch_bounds__(kTile) k_parent(const __grid_constant__ RunDev r, int step)
+{
+    if (*r.status) return;
+    const long long Rp = r.rec[step - 1].R;
+    const long long j = (long long)blockIdx.x * kTile + threadIdx.x;
+    if (j >= Rp) return;
+    const uint32_t n = r.cnt[j];
+    const uint32_t o = r.tile_off[blockIdx.x] + r.loc[j];
+    for (uint32_t c = 0; c < n; c++) r.parent[o + c] = (uint32_t)j;
+}
+
+// ======================================================== statistics
+struct I128 {
+    unsigned long long lo, hi;
+};
+__device__ __forceinline__ I128 to_i128(__int128 v)
+{
+    return I128{(unsigned long long)v, (unsigned long long)((unsigned __int128)v >> 64)};
+}
+__device__ __forceinline__ __int128 from_i128(I128 v)
+{
+    return (__int128)(((unsigned __int128)v.hi << 64) | v.lo);
+}
+__device__ __forceinline__ __int128 warp_sum128(__int128 v)
+{
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        I128 a = to_i128(v);
+        I128 b{__shfl_xor_sync(0xffffffffu, a.lo, off), __shfl_xor_sync(0xffffffffu, a.hi, off)};
+        v += from_i128(b);
+    }
+    return v;
+}
+
+// Integer moments of population i from its histograms (exact: every sum is
+// an integer, so no order matters), occupied range, running sum for MHR.
+__global__ void __launch_bounds__(kOneCta) k_stats(const __grid_constant__ RunDev r, int step)
+{
+    __shared__ __int128 ws[5][kOneCta / 32];
+    __shared__ int wmin[kOneCta / 32], wmax[kOneCta / 32];
+    if (*r.status) return;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const int N = r.N;
+    const uint32_t* HE = r.H[step & 1];
+    const uint32_t* HM = HE + N + 1;
+    __int128 sE = 0, sE2 = 0, sAM = 0, sM2 = 0, sM4 = 0;
+    int kmin = 0x7fffffff, kmax = -1;
+    uint32_t* rec_hist = nullptr;
+    if (r.record_hist && r.hist_rec && step < r.hist_steps) rec_hist = r.hist_rec + (size_t)step * 2 * (N + 1);
+    for (int k = t; k <= N; k += kOneCta) {
+        const uint32_t h = HE[k];
+        const uint32_t hm = HM[k];
+        if (h) {
+            kmin = min(kmin, k);
+            kmax = max(kmax, k);
+            const long long E = 4ll * k - 2ll * N;
+            sE += (__int128)h * E;
+            sE2 += (__int128)h * (E * E);
+            r.Hsum[k] += h;
+        }
+        if (hm) {
+            const long long M = 2ll * k - N;
+            const long long aM = M < 0 ? -M : M;
+            const long long M2 = M * M;
+            sAM += (__int128)hm * aM;
+            sM2 += (__int128)hm * M2;
+            sM4 += (__int128)hm * ((__int128)M2 * M2);
+        }
+        if (rec_hist) {
+            rec_hist[k] = h;
+            rec_hist[N + 1 + k] = hm;
+        }
+    }
+    sE = warp_sum128(sE);
+    sE2 = warp_sum128(sE2);
+    sAM = warp_sum128(sAM);
+    sM2 = warp_sum128(sM2);
+    sM4 = warp_sum128(sM4);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        kmin = min(kmin, __shfl_xor_sync(0xffffffffu, kmin, off));
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, off));
+    }
+    if (lane == 0) {
+        ws[0][warp] = sE;
+        ws[1][warp] = sE2;
+        ws[2][warp] = sAM;
+        ws[3][warp] = sM2;
+        ws[4][warp] = sM4;
+        wmin[warp] = kmin;
+        wmax[warp] = kmax;
+    }
+    __syncthreads();
+    if (t == 0) {
+        StepDev& rec = r.rec[step];
+        for (int q = 0; q < 5; q++) {
+            __int128 a = 0;
+            for (int w = 0; w < kOneCta / 32; w++) a += ws[q][w];
+            const I128 p = to_i128(a);
+            rec.sums[2 * q] = p.lo;
+            rec.sums[2 * q + 1] = p.hi;
+        }
+        int mn = 0x7fffffff, mx = -1;
+        for (int w = 0; w < kOneCta / 32; w++) {
+            mn = min(mn, wmin[w]);
+            mx = max(mx, wmax[w]);
+        }
+        rec.kmin = mn;
+        rec.kmax = mx;
+        if (step == 0) {
+            rec.R = r.R;
+            rec.R_prev = r.R;
+            rec.fam = (unsigned long long)r.R;
+        }
+    }
+}
+
+// ======================================================== Philox test kernel
+__global__ void k_philox(const uint32_t* __restrict__ ctr, long long n, PhiloxKey key, uint32_t* __restrict__ out)
+{
+    const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const uint4 c = reinterpret_cast<const uint4*>(ctr)[i];
+    reinterpret_cast<uint4*>(out)[i] = philox10(c, key);
+}
+
+// ======================================================== launch wrappers
+namespace {
+
+template <int L, int G>
+const void* bits_ptr(bool init)
+{
+    return init ? (const void*)k_init_bits<L, G> : (const void*)k_sweep_bits<L, G>;
+}
+
+template <int L>
+const void* bits_ptr_L(int gt, bool init)
+{
+    constexpr int WP = L * L / 64;
+    switch (gt) {
+    case 1: return bits_ptr<L, 1>(init);
+    case 2: if constexpr (WP % 2 == 0) return bits_ptr<L, 2>(init); break;
+    case 4: if constexpr (WP % 4 == 0) return bits_ptr<L, 4>(init); break;
+    case 8: if constexpr (WP % 8 == 0) return bits_ptr<L, 8>(init); break;
+    case 16: if constexpr (WP % 16 == 0) return bits_ptr<L, 16>(init); break;
+    case 32: if constexpr (WP % 32 == 0) return bits_ptr<L, 32>(init); break;
+    default: break;
+    }
+    return nullptr;
+}
+
+template <int G>
+const void* bytes_ptr(bool init)
+{
+    return init ? (const void*)k_init_bytes<G> : (const void*)k_sweep_bytes<G>;
+}
+
+}  // namespace
+
+// The init / sweep kernel of a run's (format, L, threads per replica).
+const void* sweep_kernel(const RunDev& h, bool init)
+{
+    if (h.fmt == 1) {
+        switch (h.L) {
+        case 8: return bits_ptr_L<8>(h.gt, init);
+        case 16: return bits_ptr_L<16>(h.gt, init);
+        case 32: return bits_ptr_L<32>(h.gt, init);
+        case 64: return bits_ptr_L<64>(h.gt, init);
+        case 128: return bits_ptr_L<128>(h.gt, init);
+        case 256: return bits_ptr_L<256>(h.gt, init);
+        case 512: return bits_ptr_L<512>(h.gt, init);
+        default: return nullptr;
+        }
+    }
+    switch (h.gt) {
+    case 1: return bytes_ptr<1>(init);
+    case 2: return bytes_ptr<2>(init);
+    case 4: return bytes_ptr<4>(init);
+    case 8: return bytes_ptr<8>(init);
+    case 16: return bytes_ptr<16>(init);
+    case 32: return bytes_ptr<32>(init);
+    default: return nullptr;
+    }
+}
+
+cudaError_t plan_sweep(const RunDev& h, Launch* ln)
+{
+    int dev = 0, sms = 0, max_optin = 0, smem_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+        return e;
+    const void* kin = sweep_kernel(h, true);
+    const void* ksw = sweep_kernel(h, false);
+    if (!kin || !ksw) return cudaErrorInvalidConfiguration;
+    // CTA of up to 8 warps; fewer when one warp's replicas need much shared memory
+    const size_t per_warp = (size_t)(32 / h.gt) * (size_t)h.words * 4u;
+    int warps = 8;
+    while (warps > 1 && per_warp * warps > (size_t)max_optin) warps >>= 1;
+    const size_t smem = per_warp * warps;
+    if (smem > (size_t)max_optin) return cudaErrorInvalidConfiguration;
+    const int threads = 32 * warps;
+    for (const void* k : {kin, ksw}) {
+        if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
+            return e;
+    }
+    int per_sm = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ksw, threads, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    ln->sweep_threads = threads;
+    ln->sweep_smem = smem;
+    ln->sweep_blocks = sms * per_sm;
+    ln->count_blocks = h.ntiles;
+    return cudaSuccess;
+}
+
+cudaError_t launch_init(const RunDev* /*d_run*/, const RunDev& h, const Launch& ln, cudaStream_t s)
+{
+    const void* k = sweep_kernel(h, true);
+    if (!k) return cudaErrorInvalidConfiguration;
+    RunDev arg = h;
+    void* args[] = {&arg};
+    return cudaLaunchKernel(k, dim3(ln.sweep_blocks), dim3(ln.sweep_threads), args, ln.sweep_smem, s);
+}
+
+cudaError_t launch_sweep(const RunDev* /*d_run*/, const RunDev& h, const Launch& ln, int step, cudaStream_t s)
+{
+    const void* k = sweep_kernel(h, false);
+    if (!k) return cudaErrorInvalidConfiguration;
+    RunDev arg = h;
+    int st = step;
+    void* args[] = {&arg, &st};
+    return cudaLaunchKernel(k, dim3(ln.sweep_blocks), dim3(ln.sweep_threads), args, ln.sweep_smem, s);
+}
+
+cudaError_t launch_tables(const RunDev* /*d_run*/, const RunDev& h, int step, cudaStream_t s)
+{
+    k_tables<<<1, kOneCta, 0, s>>>(h, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_counts(const RunDev* /*d_run*/, const RunDev& h, const Launch& ln, int step, cudaStream_t s)
+{
+    k_counts<<<ln.count_blocks, kTileThreads, 0, s>>>(h, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_scan(const RunDev* /*d_run*/, const RunDev& h, int step, cudaStream_t s)
+{
+    k_scan<<<1, kOneCta, 0, s>>>(h, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_parent(const RunDev* /*d_run*/, const RunDev& h, const Launch& ln, int step, cudaStream_t s)
+{
+    k_parent<<<ln.count_blocks, kTile, 0, s>>>(h, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_stats(const RunDev* /*d_run*/, const RunDev& h, int step, cudaStream_t s)
+{
+    k_stats<<<1, kOneCta, 0, s>>>(h, step);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint32_t* out, cudaStream_t s)
+{
+    if (n <= 0) return cudaSuccess;
+    const int threads = 256;
+    const long long blocks = (n + threads - 1) / threads;
+    k_philox<<<(unsigned)blocks, threads, 0, s>>>(ctr, n, key, out);
+    return cudaGetLastError();
+}
+
+}  // namespace pa
