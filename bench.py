@@ -1,0 +1,348 @@
+#!/usr/bin/env python3
+"""Throughput of full population-annealing runs on one GB300 (or N, one
+independent run per GPU).
+
+Metric: spin-flip attempts per ns, L^2 theta sum_{i>=1} R_i / t_run (the
+inverse of the paper's time per spin flip, Sec. 5 Eq. spinflip). One bench
+step is one complete run of the paper's default workload: L = 64,
+R = 20000, theta = 100, beta 0 -> 1 in steps of 0.005 (200 steps),
+bit-packed spins, a new seed every step (seed = 2 + step). Inputs are
+synthetic (random initial spins generated on the device).
+
+  value   device time (CUDA events on the run's stream) of pa_reset +
+          pa_launch, i.e. init, 200 temperature steps as one CUDA graph;
+  e2e     wall clock of the public API a user calls: pa_create (allocation,
+          host tables uploaded), pa_run, pa_observables (rows read back),
+          pa_destroy;
+  roofline  the sweep kernel's average launch time from CUDA events captured
+          in the same graph, against the integer-pipe peak of the device;
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload on
+          all host cores (independent processes).
+
+--impl reference times that oracle alone on the same metric and workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "spin-flip attempts/ns (batched vs single-run, bit-exact); p50/p99 run latency"
+UNIT = "flips/ns"
+WL = dict(L=64, R=20000, theta=100, beta_f=1.0, dbeta=0.005)
+WORKLOAD = "plain PA, 2D Ising L=64 periodic, R=20000, theta=100, beta 0->1 dbeta=0.005 (200 steps), bit-packed spins"
+# paper, program summary: 17 s on a Tesla K80 for this workload with multi-spin
+# coding (151 s single-spin); attempts = 4096 * 100 * sum R_i ~ 1.64e12
+PAPER_K80_MSC_FLIPS_PER_NS = 4096 * 100 * 200 * 20000 / 17.0 / 1e9
+
+# per-attempt integer work of the sweep (one site update): a quarter of a
+# Philox4x32-10 block = 5 wide 32x32->64 multiplies (FMA pipe) + 5 three-input
+# XORs (ALU pipe), one threshold compare (ALU), ~15 LOP3 per 32-site word for
+# the bit-sliced neighbour count and flip (ALU, 0.5 per attempt)
+ALU_OPS_PER_ATTEMPT = 5 + 1 + 0.5
+IMAD_OPS_PER_ATTEMPT = 5
+
+
+def clocks_sampler_start(path):
+    q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    try:
+        f = open(path, "w")
+        p = subprocess.Popen(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits", "-lms", "200"],
+                             stdout=f, stderr=subprocess.DEVNULL)
+        return p, f
+    except Exception:
+        return None, None
+
+
+def clocks_sampler_stop(h, path, gpu_index):
+    p, f = h
+    if p is None:
+        return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+    p.terminate()
+    try:
+        p.wait(timeout=5)
+    except Exception:
+        p.kill()
+    f.close()
+    sm, mx, reasons = [], None, set()
+    names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+    for line in open(path):
+        parts = [x.strip() for x in line.split(",")]
+        if len(parts) < 9 or not parts[0].isdigit() or int(parts[0]) != gpu_index:
+            continue
+        try:
+            sm.append(float(parts[1]))
+            mx = float(parts[2])
+        except ValueError:
+            continue
+        for n, v in zip(names, parts[5:9]):
+            if v.lower() == "active":
+                reasons.add(n)
+    return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx, "reasons": sorted(reasons),
+            "samples": len(sm)}
+
+
+# ------------------------------------------------------------------ CPU oracle
+def _oracle_sample(args):
+    """One worker: the oracle on R_s replicas of the workload for n_steps
+    temperature steps; returns (attempts, seconds)."""
+    R_s, n_steps, seed = args
+    sys.path.insert(0, ROOT)
+    from oracle.pa_oracle import PopulationAnnealing
+    t0 = time.perf_counter()
+    pa = PopulationAnnealing(WL["L"], R_s, WL["theta"], beta_f=WL["beta_f"], dbeta=WL["dbeta"], seed=seed)
+    att = 0
+    for _ in range(n_steps):
+        rec = pa.step()
+        att += WL["L"] ** 2 * WL["theta"] * rec.R
+    return att, time.perf_counter() - t0
+
+
+def cpu_oracle(workers: int, R_s: int, n_steps: int, seed0: int):
+    ctx = mp.get_context("spawn")
+    import oracle
+    oracle.build()
+    t0 = time.perf_counter()
+    with ctx.Pool(workers) as pool:
+        res = pool.map(_oracle_sample, [(R_s, n_steps, seed0 + w) for w in range(workers)])
+    wall = time.perf_counter() - t0
+    att = sum(a for a, _ in res)
+    return att / wall / 1e9, att, wall
+
+
+def cpu_baseline_obj(workers, R_s, n_steps):
+    v, att, wall = cpu_oracle(workers, R_s, n_steps, 9000)
+    return {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
+            "sample": f"{workers} independent oracle processes, each the first {n_steps} temperature step(s) of the "
+                      f"workload with R={R_s} (not R=20000): {att:.3e} attempts in {wall:.1f} s wall"}
+
+
+# ------------------------------------------------------------------ helpers
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return 0, 1, None
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ["RANK"])
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if torch.cuda.is_available() else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend)
+    return rank, ws, dist
+
+
+def max_over_ranks(x: float, dist) -> float:
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(x: float, dist) -> float:
+    if dist is None:
+        return x
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier(dist):
+    if dist is not None:
+        dist.barrier()
+
+
+# ------------------------------------------------------------------ reference arm
+def run_reference(args):
+    rank, ws, dist = dist_setup()
+    if rank != 0:
+        return 0
+    workers = os.cpu_count() or 1
+    R_s = args.ref_replicas
+    for _ in range(args.warmup):
+        cpu_oracle(workers, max(8, R_s // 4), 1, 500)
+    tot_att, tot_wall = 0, 0.0
+    for k in range(args.steps):
+        _, att, wall = cpu_oracle(workers, R_s, 1, 1000 + 100 * k)
+        tot_att += att
+        tot_wall += wall
+    v = tot_att / tot_wall / 1e9
+    sample = (f"each step: {workers} independent oracle processes, each the first temperature step of the workload "
+              f"with R={R_s} (not R=20000)")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_wall / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_replicas": R_s},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------------ engine arm
+def run_engine(args):
+    import torch
+
+    import paper_1703_03676_gb300 as eng
+    rank, ws, dist = dist_setup()
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.Stream(dev)  # the engine's stream; the timing events are recorded on it
+    torch.cuda.set_stream(stream)
+    L, theta = WL["L"], WL["theta"]
+    seed_of = lambda k: 2 + k + 100000 * rank  # noqa: E731
+    cfg = eng.PAConfig(L=L, R=WL["R"], theta=theta, beta_f=WL["beta_f"], dbeta=WL["dbeta"], seed=seed_of(0),
+                       spin_format=eng.SPIN_BITS32, use_graph=True, profile=args.profile)
+    run = eng.PARun(cfg, stream=stream)
+    n_steps = int(round(WL["beta_f"] / WL["dbeta"]))
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (126 MB)
+
+    def one(seed):
+        run.reset(seed)
+        run.launch()
+
+    for w in range(args.warmup):
+        one(seed_of(10_000 + w))
+        run.sync()
+    if args.profile:
+        run.phase_times()  # drop warm-up
+        base = run.phase_times()
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    clk_path = os.path.join(tempfile.gettempdir(), f"pa_clocks_{os.getpid()}.csv")
+    clk = clocks_sampler_start(clk_path)
+    time.sleep(0.3)
+    dev_ms = 0.0
+    attempts = 0
+    per_step_ms = []
+    for k in range(args.steps):
+        flush.fill_(k)  # evict L2 between timed steps (outside the events)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        one(seed_of(k))
+        e1.record(stream)
+        run.sync()
+        ms = e0.elapsed_time(e1)
+        rows = run.rows()
+        assert len(rows) == n_steps + 1
+        attempts += L * L * theta * int(rows["R"][1:].sum())
+        dev_ms += ms
+        per_step_ms.append(ms)
+    torch.cuda.synchronize(dev)
+    barrier(dist)
+    clocks = clocks_sampler_stop(clk, clk_path, local)
+    t_max = max_over_ranks(dev_ms, dist)
+    att_all = sum_over_ranks(attempts, dist)
+    value = att_all / (t_max * 1e6)
+
+    roofline = None
+    if args.profile:
+        pt = run.phase_times()
+        sw_ms = pt["sweep"][0] - base["sweep"][0]
+        sw_n = pt["sweep"][1] - base["sweep"][1]
+        avg_ms = sw_ms / max(sw_n, 1)
+        att_per_launch = attempts / max(sw_n, 1)
+        sm = torch.cuda.get_device_properties(dev).multi_processor_count
+        clk_max = clocks.get("sm_max_mhz") or 2070.0
+        alu_peak = sm * 64 * clk_max * 1e6 / 1e9  # Gop/s: 4 SMSPs x 16 lanes per SM
+        achieved = ALU_OPS_PER_ATTEMPT * att_per_launch / (avg_ms * 1e6)  # Gop/s
+        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
+                    "frac": achieved / alu_peak, "traffic": None, "kernel": "k_sweep_bits<64,32>",
+                    "ops_per_attempt": ALU_OPS_PER_ATTEMPT, "attempts_per_ns": att_per_launch / (avg_ms * 1e6),
+                    "launch_ms": avg_ms, "launches": sw_n,
+                    "peak_note": "ALU pipe: SMs x 64 lanes/clk x max SM clock (derived, not measured)",
+                    "share_of_step": sw_ms / dev_ms if dev_ms else None}
+        try:
+            roofline["rng_ceiling_words_per_ns"] = eng.measure_rng_peak(2048, stream)
+        except Exception as e:  # measurement only
+            roofline["rng_ceiling_words_per_ns"] = f"unavailable: {e}"
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        wall = 0.0
+        att_e2e = 0
+        h2d = d2h = 0
+        for k in range(max(1, args.e2e_steps)):
+            t0 = time.perf_counter()
+            r2 = eng.PARun(eng.PAConfig(L=L, R=WL["R"], theta=theta, beta_f=WL["beta_f"], dbeta=WL["dbeta"],
+                                        seed=seed_of(50_000 + k), spin_format=eng.SPIN_BITS32), stream=stream)
+            r2.run()
+            rows = r2.rows()
+            r2.close()
+            wall += time.perf_counter() - t0
+            att_e2e += L * L * theta * int(rows["R"][1:].sum())
+            # host tables uploaded by pa_create (thresholds, level weights, key)
+            h2d = 2 * (n_steps + 1) * 4 + (L * L + 1) * 8 + 8
+            d2h = (n_steps + 1) * 128 + 4 + rows.nbytes
+        wmax = max_over_ranks(wall, dist)
+        e2e = {"value": sum_over_ranks(att_e2e, dist) / (wmax * 1e9), "unit": UNIT,
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+               "note": "wall clock of pa_create + pa_run + pa_observables + pa_destroy per run"}
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline_obj(os.cpu_count() or 1, args.cpu_replicas, 1)
+
+    run.close()
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": value / PAPER_K80_MSC_FLIPS_PER_NS, "dtype": "u32",
+                "data": "synthetic",
+                "config": {"workload": WORKLOAD, "seeds": "2+step (+100000*rank)", "spin_format": "bits32",
+                           "l2": "flushed between timed steps (256 MB write)",
+                           "baseline_ref": "paper K80 multi-spin-coded run, 17 s for this workload",
+                           "parallelism": f"independent runs x{ws}"},
+                "clocks": clocks, "e2e": e2e, "gpu_launches": (2 + 6 * n_steps) * args.steps,
+                "roofline": roofline, "cpu_baseline": cpu,
+                "per_step_ms": per_step_ms}
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
+    ap.add_argument("--no-profile", dest="profile", action="store_false")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-replicas", type=int, default=400)
+    ap.add_argument("--ref-replicas", type=int, default=200)
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_engine(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

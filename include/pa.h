@@ -56,7 +56,7 @@ typedef enum { PA_HIST_E = 0, PA_HIST_M = 1, PA_HIST_ESUM = 2 } pa_hist_kind;
  * beta0, beta_f, the seed; plus the step rule of Sec. 2.1 / 2.3). */
 typedef struct {
     int32_t L;              /* lattice edge, even, 4 <= L <= 1024. PA_SPIN_BITS32
-                               needs L in {8, 16, 32} or L % 64 == 0              */
+                               needs L in {8, 16, 32, 64, 128, 256, 512}         */
     int32_t theta;          /* Metropolis sweeps per temperature step, >= 1       */
     int64_t R;              /* target population size, >= 1                      */
     double beta0;           /* must be 0 (Z_beta0 = 2^N, Eq. free-energy)         */
@@ -113,6 +113,17 @@ pa_status pa_step(pa_ctx *ctx);
  * schedule runs as one CUDA-graph launch. */
 pa_status pa_run(pa_ctx *ctx);
 
+/* Enqueue the rest of the schedule and return without waiting (adaptive
+ * runs still synchronise once per step). A fixed schedule started from step
+ * 0 with use_graph runs as one CUDA-graph launch, captured on first use and
+ * reused after pa_reset. */
+pa_status pa_launch(pa_ctx *ctx);
+
+/* Start the run again from step 0 with a new seed, keeping every device
+ * allocation (and a captured graph): histograms, records and the status are
+ * cleared and the beta0 population is regenerated from `seed`. */
+pa_status pa_reset(pa_ctx *ctx, uint64_t seed);
+
 /* Wait for enqueued work and report any device-side failure. */
 pa_status pa_sync(pa_ctx *ctx);
 
@@ -166,6 +177,10 @@ void pa_config_default(pa_config *cfg);
 void pa_destroy(pa_ctx *ctx);
 const char *pa_strerror(pa_status s);
 
+/* Text of the last CUDA failure seen by a call on this thread (the CUDA
+ * error name and the engine source line), or "" if none. */
+const char *pa_last_error_message(void);
+
 /* ---- kernel-level entry points (device pointers, for tests) ----------- */
 
 /* Philox4x32-10 on the device: out[4r..4r+3] = Philox(ctr[4r..4r+3], key =
@@ -173,6 +188,15 @@ const char *pa_strerror(pa_status s);
  * pointers of 4n uint32 each. Synchronous on `cuda_stream`. */
 pa_status pa_philox_device(const uint32_t *dev_ctr, int64_t n, uint64_t seed, uint32_t *dev_out,
                            void *cuda_stream);
+
+/* Throughput ceiling of the random-number generator alone: a persistent
+ * kernel that evaluates Philox4x32-10 on `blocks_per_thread` counters per
+ * thread over the whole device and XOR-folds the words (one store per
+ * thread into the device buffer `dev_sink`, >= 4 bytes per thread of a
+ * 152 x 2048-thread grid). *words_per_ns gets 4 x counters / elapsed ns.
+ * Synchronous on `cuda_stream`. */
+pa_status pa_measure_rng_peak(int64_t blocks_per_thread, uint32_t *dev_sink, void *cuda_stream,
+                              double *words_per_ns);
 
 #ifdef __cplusplus
 }

@@ -21,11 +21,13 @@
  * Counter layout ("stream map"). The paper seeds per thread from grid and
  * block indices, which would tie the result to the launch shape; here the
  * counter is a function of logical indices only, so any implementation that
- * visits the same (replica, site, sweep) gets the same number:
+ * visits the same (replica, site, sweep) gets the same number. The index
+ * that differs between neighbouring sites (or slots) sits in counter word 1
+ * and the stream tag in word 2:
  *   key = (seed & 0xffffffff, seed >> 32)
- *   INIT     (tag 0): g = c*N/2 + b,  ctr = (g>>2, k, 0, 0),       x = out[g&3]
- *   SWEEP    (tag 1): ctr = (b>>2, k, 2u + c, 1),                   x = out[b&3]
- *   RESAMPLE (tag 2): ctr = (j>>2, i, 0, 2),                        x = out[j&3]
+ *   INIT     (tag 0): g = c*N/2 + b,  ctr = (0, g>>2, 0, k),        x = out[g&3]
+ *   SWEEP    (tag 1): ctr = (2u + c, b>>2, 1, k),                   x = out[b&3]
+ *   RESAMPLE (tag 2): ctr = (i, j>>2, 2, 0),                        x = out[j&3]
  * where c = (x+y)&1 is the checkerboard colour of site (x, y),
  * b = y*(L/2) + (x>>1) its index within the colour, k the replica slot,
  * u the global sweep number, i the temperature step and j the old slot.
@@ -57,11 +59,11 @@ void oracle_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t
     out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
 }
 
-/* One 32-bit word of a tagged stream: lane l of Philox(ctr = (c0, c1, c2, tag)). */
-static uint32_t stream_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
-                            uint32_t tag, unsigned lane)
+/* One 32-bit word of a tagged stream: lane l of Philox(ctr = (c0, c1, tag, c3)). */
+static uint32_t stream_word(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t tag,
+                            uint32_t c3, unsigned lane)
 {
-    uint32_t ctr[4] = {c0, c1, c2, tag};
+    uint32_t ctr[4] = {c0, c1, tag, c3};
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     uint32_t out[4];
     oracle_philox4x32_10(ctr, key, out);
@@ -84,7 +86,7 @@ void oracle_init(int L, int64_t n, const int64_t *slot, uint64_t seed, int8_t *s
                 uint32_t c = (uint32_t)((x + y) & 1);
                 uint32_t b = (uint32_t)(y * half + (x >> 1));
                 uint32_t g = c * (uint32_t)(N / 2) + b;
-                uint32_t w = stream_word(seed, g >> 2, k, 0u, 0u, g & 3u);
+                uint32_t w = stream_word(seed, 0u, g >> 2, 0u, k, g & 3u);
                 S[y * L + x] = (w < 0x80000000u) ? 1 : -1;
             }
     }
@@ -128,7 +130,7 @@ void oracle_sweep(int L, int64_t n, const int64_t *slot, uint64_t seed, int64_t 
                             flip = 1;  /* dE <= 0 */
                         } else {
                             uint32_t b = (uint32_t)(y * half + (x >> 1));
-                            uint32_t w = stream_word(seed, b >> 2, k, 2u * u + (uint32_t)c, 1u, b & 3u);
+                            uint32_t w = stream_word(seed, 2u * u + (uint32_t)c, b >> 2, 1u, k, b & 3u);
                             uint64_t T = (aligned == 3) ? T4 : T8;
                             flip = ((uint64_t)w < T);
                         }
@@ -162,7 +164,7 @@ void oracle_measure(int L, int64_t n, const int8_t *s, int64_t *E, int64_t *M)
 void oracle_resample_words(uint64_t seed, int64_t step, int64_t n, uint32_t *out)
 {
     for (int64_t j = 0; j < n; j++)
-        out[j] = stream_word(seed, (uint32_t)(j >> 2), (uint32_t)step, 0u, 2u, (unsigned)(j & 3));
+        out[j] = stream_word(seed, (uint32_t)step, (uint32_t)(j >> 2), 2u, 0u, (unsigned)(j & 3));
 }
 
 /* Raw Philox block for tests: out[4*r .. 4*r+3] = Philox(ctr[4*r..], key). */

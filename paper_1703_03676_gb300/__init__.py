@@ -27,7 +27,10 @@ _STATUS = {0: "ok", 1: "done", -1: "invalid argument", -2: "out of memory", -3: 
 
 class PAError(RuntimeError):
     def __init__(self, status: int, where: str):
-        super().__init__(f"{where}: {_STATUS.get(status, status)} ({status})")
+        detail = ""
+        if status == -6 and _lib is not None:
+            detail = " - " + (_lib.pa_last_error_message() or b"").decode(errors="replace")
+        super().__init__(f"{where}: {_STATUS.get(status, status)} ({status}){detail}")
         self.status = status
         self.kind = _STATUS.get(status, str(status))
 
@@ -68,6 +71,8 @@ SIGNATURES = [
     ("pa_step", ctypes.c_int, [_P]),
     ("pa_run", ctypes.c_int, [_P]),
     ("pa_sync", ctypes.c_int, [_P]),
+    ("pa_launch", ctypes.c_int, [_P]),
+    ("pa_reset", ctypes.c_int, [_P, ctypes.c_uint64]),
     ("pa_num_rows", ctypes.c_int, [_P, _I64P]),
     ("pa_observables", ctypes.c_int, [_P, ctypes.POINTER(_Obs), ctypes.c_int64, _I64P]),
     ("pa_step_info_get", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(_StepInfo)]),
@@ -84,7 +89,9 @@ SIGNATURES = [
     ("pa_config_default", None, [ctypes.POINTER(_Config)]),
     ("pa_destroy", None, [_P]),
     ("pa_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("pa_last_error_message", ctypes.c_char_p, []),
     ("pa_philox_device", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_uint64, _P, _P]),
+    ("pa_measure_rng_peak", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
 ]
 
 
@@ -111,14 +118,15 @@ def _check(st: int, where: str, ok=(0,)):
 
 
 def _stream_handle(stream):
+    """cudaStream_t for the engine. None: the context creates its own stream.
+    torch's legacy default stream (handle 0) cannot be shared: pass a
+    torch.cuda.Stream to order engine work with other work on it."""
     if stream is None:
-        import torch
-        if not torch.cuda.is_available():
-            raise RuntimeError("a CUDA device is required")
-        return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
-    if isinstance(stream, int):
-        return ctypes.c_void_p(stream)
-    return ctypes.c_void_p(stream.cuda_stream)
+        return ctypes.c_void_p(None)
+    h = stream if isinstance(stream, int) else stream.cuda_stream
+    if h == 0:
+        raise ValueError("pass a torch.cuda.Stream (not the legacy default stream) or None")
+    return ctypes.c_void_p(h)
 
 
 @dataclass
@@ -195,6 +203,17 @@ class PARun:
 
     def run(self):
         _check(self._lib.pa_run(self._h), "pa_run")
+        return self
+
+    def launch(self):
+        """Enqueue the rest of the schedule without waiting."""
+        _check(self._lib.pa_launch(self._h), "pa_launch")
+        return self
+
+    def reset(self, seed: int):
+        """Back to step 0 with a new seed, keeping allocations."""
+        _check(self._lib.pa_reset(self._h, seed & 0xFFFFFFFFFFFFFFFF), "pa_reset")
+        self.cfg.seed = seed
         return self
 
     def sync(self):
@@ -287,6 +306,19 @@ def philox_device(ctr, seed: int, stream=None):
     import torch
     assert ctr.is_cuda and ctr.dtype in (torch.int32, torch.uint32) and ctr.is_contiguous()
     out = torch.empty_like(ctr)
+    torch.cuda.current_stream().synchronize()
     _check(lib().pa_philox_device(ctypes.c_void_p(ctr.data_ptr()), ctr.numel() // 4, seed & 0xFFFFFFFFFFFFFFFF,
                                   ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)), "pa_philox_device")
     return out
+
+
+def measure_rng_peak(blocks_per_thread: int = 4096, stream=None) -> float:
+    """Philox4x32-10 words per ns of the whole device (generator alone)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.empty(sms * 2048, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    out = ctypes.c_double()
+    _check(lib().pa_measure_rng_peak(blocks_per_thread, ctypes.c_void_p(sink.data_ptr()), _stream_handle(stream),
+                                     ctypes.byref(out)), "pa_measure_rng_peak")
+    return out.value

@@ -16,6 +16,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <new>
@@ -92,27 +93,36 @@ struct pa_ctx {
     std::vector<void*> allocs;
     void* h_stage = nullptr;      // pinned staging for adaptive uploads
     size_t h_stage_bytes = 0;
-    cudaGraphExec_t graph = nullptr;
-    // profiling
-    std::vector<cudaEvent_t> ev;  // pairs per phase launch
+    unsigned* d_key = nullptr;    // Philox key in device memory
+    cudaGraphExec_t graph = nullptr;  // steps 1..n of the fixed schedule
+    bool capturing = false;
+    // profiling: (start, end) event pairs per kernel launch and its phase
+    std::vector<cudaEvent_t> ev;  // plain launches, destroyed once read
     std::vector<int> ev_phase;
+    std::vector<cudaEvent_t> gev; // owned by the graph, read after each launch
+    std::vector<int> gev_phase;
+    bool gev_pending = false;
     double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};
     long long phase_n[7] = {0, 0, 0, 0, 0, 0, 0};
 };
 
 namespace {
 
-pa_status from_cuda(cudaError_t e)
+thread_local char g_last_error[256] = "";
+
+pa_status from_cuda(cudaError_t e, int line)
 {
     if (e == cudaSuccess) return PA_OK;
+    std::snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at pa_engine.cu:%d", cudaGetErrorName(e),
+                  cudaGetErrorString(e), line);
     if (e == cudaErrorMemoryAllocation) return PA_ENOMEM;
     return PA_ECUDA;
 }
 
-#define PA_CUDA(call)                                  \
-    do {                                               \
-        cudaError_t e_ = (call);                       \
-        if (e_ != cudaSuccess) return from_cuda(e_);   \
+#define PA_CUDA(call)                                          \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return from_cuda(e_, __LINE__); \
     } while (0)
 
 bool bits_L_ok(int L)
@@ -227,42 +237,55 @@ pa_status dev_alloc(pa_ctx* c, T** p, size_t count)
     } while (0)
 
 // ---------------------------------------------------------------- profiling
-pa_status prof_begin(pa_ctx* c, int phase, cudaEvent_t* out)
+pa_status prof_record(pa_ctx* c, int phase)
 {
-    *out = nullptr;
     if (!c->cfg.profile) return PA_OK;
     cudaEvent_t a;
     PA_CUDA(cudaEventCreate(&a));
-    PA_CUDA(cudaEventRecord(a, c->stream));
-    c->ev.push_back(a);
-    c->ev_phase.push_back(phase);
-    *out = a;
+    // inside a capture the record must become a graph node (external event)
+    PA_CUDA(cudaEventRecordWithFlags(a, c->stream, c->capturing ? cudaEventRecordExternal : 0u));
+    if (c->capturing) {
+        c->gev.push_back(a);
+        c->gev_phase.push_back(phase);
+    } else {
+        c->ev.push_back(a);
+        c->ev_phase.push_back(phase);
+    }
     return PA_OK;
+}
+
+pa_status prof_begin(pa_ctx* c, int phase, cudaEvent_t* out)
+{
+    *out = nullptr;
+    return prof_record(c, phase);
 }
 
 pa_status prof_end(pa_ctx* c)
 {
-    if (!c->cfg.profile) return PA_OK;
-    cudaEvent_t b;
-    PA_CUDA(cudaEventCreate(&b));
-    PA_CUDA(cudaEventRecord(b, c->stream));
-    c->ev.push_back(b);
-    c->ev_phase.push_back(-1);
-    return PA_OK;
+    return prof_record(c, -1);
 }
 
+// accumulate the elapsed time of every completed (start, end) pair
 pa_status prof_collect(pa_ctx* c)
 {
     for (size_t i = 0; i + 1 < c->ev.size(); i += 2) {
         float ms = 0.f;
         PA_CUDA(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
-        const int ph = c->ev_phase[i];
-        c->phase_ms[ph] += ms;
-        c->phase_n[ph] += 1;
+        c->phase_ms[c->ev_phase[i]] += ms;
+        c->phase_n[c->ev_phase[i]] += 1;
     }
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     c->ev.clear();
     c->ev_phase.clear();
+    if (c->gev_pending) {
+        for (size_t i = 0; i + 1 < c->gev.size(); i += 2) {
+            float ms = 0.f;
+            PA_CUDA(cudaEventElapsedTime(&ms, c->gev[i], c->gev[i + 1]));
+            c->phase_ms[c->gev_phase[i]] += ms;
+            c->phase_n[c->gev_phase[i]] += 1;
+        }
+        c->gev_pending = false;
+    }
     return PA_OK;
 }
 
@@ -441,10 +464,108 @@ void all_rows(const pa_ctx* c, std::vector<pa_obs>& rows)
     }
 }
 
+// Back to step 0 with a new seed: clear histograms, records and status,
+// then generate and measure the beta0 population (Sec. 2.1 step 1).
+pa_status reset_run(pa_ctx* c, uint64_t seed)
+{
+    RunDev& h = c->h;
+    const size_t N1 = (size_t)c->N + 1;
+    PA_CUDA(cudaStreamSynchronize(c->stream));
+    if (c->cfg.profile) PA_TRY(prof_collect(c));
+    unsigned* key = (unsigned*)c->h_stage;  // pinned; idle after the sync
+    key[0] = (unsigned)(seed & 0xffffffffu);
+    key[1] = (unsigned)(seed >> 32);
+    PA_CUDA(cudaMemcpyAsync(c->d_key, key, 8, cudaMemcpyHostToDevice, c->stream));
+    PA_CUDA(cudaMemsetAsync(h.H[0], 0, 2 * N1 * 4, c->stream));
+    PA_CUDA(cudaMemsetAsync(h.H[1], 0, 2 * N1 * 4, c->stream));
+    PA_CUDA(cudaMemsetAsync(h.Hsum, 0, N1 * 8, c->stream));
+    PA_CUDA(cudaMemsetAsync(h.rec, 0, sizeof(StepDev) * (size_t)(c->max_steps + 1), c->stream));
+    PA_CUDA(cudaMemsetAsync(h.status, 0, 16, c->stream));
+    PA_CUDA(cudaMemsetAsync(h.work, 0, 16, c->stream));
+    c->cfg.seed = seed;
+    c->failed = PA_OK;
+    c->betas.assign(1, 0.0);
+    c->deltas.assign(1, 0.0);
+    if (c->adaptive) {
+        c->T4.resize(1);
+        c->T8.resize(1);
+    }
+    c->recs.clear();
+    c->done_rows = 0;
+    c->enq_step = 0;
+    c->done = false;
+    cudaEvent_t ev;
+    PA_TRY(prof_begin(c, 6, &ev));
+    PA_CUDA(pa::launch_init(nullptr, h, c->ln, c->stream));
+    PA_TRY(prof_end(c));
+    PA_TRY(prof_begin(c, 5, &ev));
+    PA_CUDA(pa::launch_stats(nullptr, h, 0, c->stream));
+    PA_TRY(prof_end(c));
+    return PA_OK;
+}
+
+// Enqueue the remaining schedule without waiting. A fixed schedule started
+// from step 0 runs as one CUDA graph (captured on first use, reused after
+// pa_reset since every kernel reads the seed from device memory).
+pa_status launch_rest(pa_ctx* c)
+{
+    if (c->failed != PA_OK) return c->failed;
+    if (c->done) return PA_OK;
+    if (!c->adaptive && c->cfg.use_graph && c->enq_step == 0) {
+        if (!c->graph) {
+            cudaStream_t cap = nullptr;
+            PA_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+            cudaStream_t saved = c->stream;
+            c->stream = cap;
+            c->capturing = true;
+            cudaGraph_t g = nullptr;
+            pa_status st = PA_OK;
+            if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = PA_ECUDA;
+            while (st == PA_OK && !c->done) st = enqueue_step(c);
+            if (st == PA_DONE) st = PA_OK;
+            const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+            c->stream = saved;
+            c->capturing = false;
+            if (st == PA_OK && ce != cudaSuccess) st = PA_ECUDA;
+            if (st == PA_OK && cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) st = PA_ECUDA;
+            if (g) cudaGraphDestroy(g);
+            cudaStreamDestroy(cap);
+            if (st != PA_OK) {
+                cudaGetLastError();
+                for (cudaEvent_t e : c->gev) cudaEventDestroy(e);
+                c->gev.clear();
+                c->gev_phase.clear();
+                c->betas.resize(1);
+                c->deltas.resize(1);
+                c->enq_step = 0;
+                c->done = false;
+                c->graph = nullptr;
+                return st;
+            }
+        } else {
+            // replay: the host schedule is the same as at capture
+            while (!c->done) {
+                const long long i = c->enq_step + 1;
+                c->betas.push_back(0.0 + (double)i * c->cfg.dbeta);
+                c->deltas.push_back(c->cfg.dbeta);
+                c->enq_step = i;
+                if (i == c->n_fixed) c->done = true;
+            }
+        }
+        PA_CUDA(cudaGraphLaunch(c->graph, c->stream));
+        if (c->cfg.profile) c->gev_pending = true;
+        return PA_OK;
+    }
+    pa_status st = PA_OK;
+    while (st == PA_OK) st = enqueue_step(c);
+    return st == PA_DONE ? PA_OK : st;
+}
+
 pa_status free_all(pa_ctx* c)
 {
     if (c->graph) cudaGraphExecDestroy(c->graph);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    for (cudaEvent_t e : c->gev) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -469,6 +590,11 @@ void pa_config_default(pa_config* cfg)
     cfg->seed = 1;
     cfg->spin_format = PA_SPIN_BITS32;
     cfg->use_graph = 1;
+}
+
+const char* pa_last_error_message(void)
+{
+    return g_last_error;
 }
 
 const char* pa_strerror(pa_status s)
@@ -531,8 +657,6 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
     if (h.fmt == PA_SPIN_BITS32 && (s.N / 64) % h.gt) return fail(PA_EINVAL);
     h.R = cfg->R;
     h.cap = s.cap;
-    h.k0 = (unsigned)(cfg->seed & 0xffffffffu);
-    h.k1 = (unsigned)(cfg->seed >> 32);
     h.ntiles = (int)s.ntiles;
     h.record_hist = cfg->record_histograms ? 1 : 0;
     h.hist_steps = (int)s.hist_steps;
@@ -564,19 +688,12 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
     if (s.hist_steps) PA_ALLOC(h.hist_rec, (size_t)s.hist_steps * 2 * N1);
     PA_ALLOC(h.status, 4);
     PA_ALLOC(h.work, 4);
+    PA_ALLOC(c->d_key, 4);
+    h.key = c->d_key;
 #undef PA_ALLOC
-    if (cudaMemsetAsync(h.H[0], 0, 2 * N1 * 4, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(h.H[1], 0, 2 * N1 * 4, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(h.Hsum, 0, N1 * 8, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(h.rec, 0, sizeof(StepDev) * (size_t)(s.steps + 1), c->stream) != cudaSuccess ||
-        cudaMemsetAsync(h.status, 0, 16, c->stream) != cudaSuccess ||
-        cudaMemsetAsync(h.work, 0, 16, c->stream) != cudaSuccess)
-        return fail(PA_ECUDA);
     // staging for adaptive uploads (level weights + thresholds)
     c->h_stage_bytes = N1 * sizeof(double) + 64;
     if (cudaMallocHost(&c->h_stage, c->h_stage_bytes) != cudaSuccess) return fail(PA_ENOMEM);
-    c->betas.push_back(0.0);
-    c->deltas.push_back(0.0);
     c->T4.push_back(1ull << 32);
     c->T8.push_back(1ull << 32);
     if (!c->adaptive) {
@@ -600,15 +717,9 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
         cudaGetLastError();
         return fail(PA_EINVAL);
     }
-    // step 0: random configurations at beta0 = 0, measured (no sweeps)
     {
-        cudaEvent_t ev;
-        if (prof_begin(c, 6, &ev) != PA_OK) return fail(PA_ECUDA);
-        if (pa::launch_init(nullptr, h, c->ln, c->stream) != cudaSuccess) return fail(PA_ECUDA);
-        if (prof_end(c) != PA_OK) return fail(PA_ECUDA);
-        if (prof_begin(c, 5, &ev) != PA_OK) return fail(PA_ECUDA);
-        if (pa::launch_stats(nullptr, h, 0, c->stream) != cudaSuccess) return fail(PA_ECUDA);
-        if (prof_end(c) != PA_OK) return fail(PA_ECUDA);
+        const pa_status rs = reset_run(c, cfg->seed);
+        if (rs != PA_OK) return fail(rs);
     }
     c->enq_step = 0;
     *out = c;
@@ -631,43 +742,20 @@ pa_status pa_sync(pa_ctx* c)
 pa_status pa_run(pa_ctx* c)
 {
     if (!c) return PA_EINVAL;
-    if (c->failed != PA_OK) return c->failed;
-    if (!c->adaptive && c->cfg.use_graph && !c->cfg.profile && !c->done) {
-        // capture the remaining fixed schedule once and launch it as one graph
-        cudaStream_t cap = nullptr;
-        PA_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
-        cudaEvent_t dep;
-        PA_CUDA(cudaEventCreateWithFlags(&dep, cudaEventDisableTiming));
-        cudaStream_t saved = c->stream;
-        c->stream = cap;
-        cudaGraph_t g = nullptr;
-        pa_status st = PA_OK;
-        const long long from = c->enq_step;
-        if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = PA_ECUDA;
-        while (st == PA_OK && !c->done) st = enqueue_step(c);
-        if (st == PA_DONE) st = PA_OK;
-        cudaError_t ce = cudaStreamEndCapture(cap, &g);
-        c->stream = saved;
-        if (st == PA_OK && ce != cudaSuccess) st = PA_ECUDA;
-        if (st == PA_OK && cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) st = PA_ECUDA;
-        if (g) cudaGraphDestroy(g);
-        cudaStreamDestroy(cap);
-        cudaEventDestroy(dep);
-        if (st != PA_OK) {
-            // roll back the host schedule so a plain run can follow
-            c->betas.resize((size_t)from + 1);
-            c->deltas.resize((size_t)from + 1);
-            c->enq_step = from;
-            c->done = false;
-            return st;
-        }
-        PA_CUDA(cudaGraphLaunch(c->graph, c->stream));
-        return pull_records(c);
-    }
-    pa_status st = PA_OK;
-    while (st == PA_OK) st = enqueue_step(c);
-    if (st != PA_DONE) return st;
+    PA_TRY(launch_rest(c));
     return pull_records(c);
+}
+
+pa_status pa_launch(pa_ctx* c)
+{
+    if (!c) return PA_EINVAL;
+    return launch_rest(c);
+}
+
+pa_status pa_reset(pa_ctx* c, uint64_t seed)
+{
+    if (!c) return PA_EINVAL;
+    return reset_run(c, seed);
 }
 
 pa_status pa_num_rows(pa_ctx* c, int64_t* n)
@@ -902,6 +990,31 @@ pa_status pa_philox_device(const uint32_t* ctr, int64_t n, uint64_t seed, uint32
     cudaStream_t s = (cudaStream_t)stream;
     PA_CUDA(pa::launch_philox(ctr, n, pa::PhiloxKey{(unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32)}, out, s));
     PA_CUDA(cudaStreamSynchronize(s));
+    return PA_OK;
+}
+
+pa_status pa_measure_rng_peak(int64_t blocks_per_thread, uint32_t* sink, void* stream, double* words_per_ns)
+{
+    if (blocks_per_thread < 8 || !sink || !words_per_ns) return PA_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    PA_CUDA(cudaGetDevice(&dev));
+    PA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256, grid = sms * 8;  // 2048 resident threads per SM
+    const long long blocks = blocks_per_thread & ~7ll;
+    cudaEvent_t a, b;
+    PA_CUDA(cudaEventCreate(&a));
+    PA_CUDA(cudaEventCreate(&b));
+    PA_CUDA(pa::launch_rng_peak(blocks, sink, grid, threads, s));  // warm-up
+    PA_CUDA(cudaEventRecord(a, s));
+    PA_CUDA(pa::launch_rng_peak(blocks, sink, grid, threads, s));
+    PA_CUDA(cudaEventRecord(b, s));
+    PA_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    PA_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    *words_per_ns = 4.0 * (double)blocks * (double)grid * threads / ((double)ms * 1e6);
     return PA_OK;
 }
 

@@ -55,7 +55,7 @@ struct RunDev {
     int fmt;                  // 0 byte spins, 1 bit-packed
     int gt;                   // threads per replica in the sweep
     long long R, cap;
-    unsigned k0, k1;          // Philox key
+    const unsigned* key;      // Philox key (2 words) in device memory
     int ntiles;               // copy-count tiles covering cap
     int record_hist;
     int hist_steps;           // steps with a slot in hist_rec
@@ -120,6 +120,7 @@ cudaError_t launch_scan(const RunDev* d_run, const RunDev& h, int step, cudaStre
 cudaError_t launch_parent(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s);
 cudaError_t launch_sweep(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s);
 cudaError_t launch_stats(const RunDev* d_run, const RunDev& h, int step, cudaStream_t s);
+cudaError_t launch_rng_peak(long long blocks, uint32_t* sink, int grid, int threads, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint32_t* out, cudaStream_t s);
 
 // Sweep launch shape: persistent CTAs for this run (group threads gt).

@@ -89,7 +89,8 @@ __device__ __forceinline__ void neighbours(const uint32_t* __restrict__ O, int c
 // One Metropolis update of the 32 sites of word s (all of one colour).
 // A site with n aligned neighbours flips with certainty if n <= 2 (dE <= 0),
 // with x <= T4-1 if n = 3 and x <= T8-1 if n = 4, x the SWEEP word of the
-// site: counter (b>>2, k, 2u + c, 1), lane b&3. Bit-sliced counting of the
+// site: counter (2u + c, b>>2, 1, k), lane b&3. Only counter word 1 differs
+// between the lanes of a warp, so the first-round products are warp-uniform. Bit-sliced counting of the
 // disagreeing neighbours d1..d4 gives "at least two disagree" (n <= 2) and
 // "none disagrees" (n = 4) for all 32 sites at once.
 __device__ __forceinline__ uint32_t metropolis_word(uint32_t s, uint32_t same, uint32_t side, uint32_t up,
@@ -103,7 +104,7 @@ __device__ __forceinline__ uint32_t metropolis_word(uint32_t s, uint32_t same, u
     uint32_t acc4 = 0, acc8 = 0;
 #pragma unroll
     for (int q = 0; q < 8; q++) {
-        const uint4 x = philox10(make_uint4(c0 + q, k, c2, kTagSweep), key);
+        const uint4 x = philox10(make_uint4(c2, c0 + q, kTagSweep, k), key);
         acc4 |= ((uint32_t)(x.x <= t4m1) << (4 * q)) | ((uint32_t)(x.y <= t4m1) << (4 * q + 1)) |
                 ((uint32_t)(x.z <= t4m1) << (4 * q + 2)) | ((uint32_t)(x.w <= t4m1) << (4 * q + 3));
         acc8 |= ((uint32_t)(x.x <= t8m1) << (4 * q)) | ((uint32_t)(x.y <= t8m1) << (4 * q + 1)) |
@@ -176,7 +177,7 @@ __global__ void __launch_bounds__(256) k_init_bits(const __grid_constant__ RunDe
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane / G, gl = lane % G;
     uint32_t* sp = smem + (warp * RPW + g) * Gm::WORDS;
-    const PhiloxKey key{r.k0, r.k1};
+    const PhiloxKey key{r.key[0], r.key[1]};
     const long long R0 = r.R;
     for (;;) {
         unsigned base = 0;
@@ -186,14 +187,14 @@ __global__ void __launch_bounds__(256) k_init_bits(const __grid_constant__ RunDe
         const long long k = (long long)base + g;
         const bool active = k < R0;
         if (active) {
-            // INIT stream: site g = c*N/2 + b, counter (g>>2, k, 0, 0), spin up iff x < 2^31
+            // INIT stream: site g = c*N/2 + b, counter (0, g>>2, 0, k), spin up iff x < 2^31
             for (int i = gl; i < Gm::WORDS; i += G) {
                 const int c = i / Gm::WP, w = i - c * Gm::WP;
                 const unsigned c0 = (unsigned)(c * (Gm::N / 8) + 8 * w);
                 uint32_t word = 0;
 #pragma unroll
                 for (int q = 0; q < 8; q++) {
-                    const uint4 x = philox10(make_uint4(c0 + q, (unsigned)k, 0u, kTagInit), key);
+                    const uint4 x = philox10(make_uint4(0u, c0 + q, kTagInit, (unsigned)k), key);
                     word |= ((x.x >> 31) ^ 1u) << (4 * q) | ((x.y >> 31) ^ 1u) << (4 * q + 1) |
                             ((x.z >> 31) ^ 1u) << (4 * q + 2) | ((x.w >> 31) ^ 1u) << (4 * q + 3);
                 }
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunD
     const int cur = (step - 1) & 1, nxt = step & 1;
     const long long Ri = r.rec[step].R;
     const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
-    const PhiloxKey key{r.k0, r.k1};
+    const PhiloxKey key{r.key[0], r.key[1]};
     const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
     const int theta = r.theta;
     unsigned families = 0;
@@ -320,7 +321,7 @@ __global__ void __launch_bounds__(256) k_init_bytes(const __grid_constant__ RunD
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int g = lane / G, gl = lane % G;
     uint8_t* sp = reinterpret_cast<uint8_t*>(smem + (warp * RPW + g) * r.words);
-    const PhiloxKey key{r.k0, r.k1};
+    const PhiloxKey key{r.key[0], r.key[1]};
     const long long R0 = r.R;
     const int N = r.N, NP = N / 2;
     for (;;) {
@@ -332,7 +333,7 @@ __global__ void __launch_bounds__(256) k_init_bytes(const __grid_constant__ RunD
         const bool active = k < R0;
         if (active) {
             for (int gq = gl; gq < (N + 3) / 4; gq += G) {
-                const uint4 x = philox10(make_uint4((unsigned)gq, (unsigned)k, 0u, kTagInit), key);
+                const uint4 x = philox10(make_uint4(0u, (unsigned)gq, kTagInit, (unsigned)k), key);
                 const unsigned xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
                 for (int l = 0; l < 4; l++) {
@@ -369,7 +370,7 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
     const int cur = (step - 1) & 1, nxt = step & 1;
     const long long Ri = r.rec[step].R;
     const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
-    const PhiloxKey key{r.k0, r.k1};
+    const PhiloxKey key{r.key[0], r.key[1]};
     const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
     const int L = r.L, half = r.half, NP = r.N / 2, QP = (NP + 3) / 4;
     unsigned families = 0;
@@ -395,7 +396,7 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
                     uint8_t* P = sp + c * NP;
                     const uint8_t* O = sp + (1 - c) * NP;
                     for (int q = gl; q < QP; q += G) {
-                        const uint4 x = philox10(make_uint4((unsigned)q, (unsigned)k, 2u * u + (unsigned)c, kTagSweep),
+                        const uint4 x = philox10(make_uint4(2u * u + (unsigned)c, (unsigned)q, kTagSweep, (unsigned)k),
                                                  key);
                         const unsigned xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
@@ -507,7 +508,7 @@ __global__ void __launch_bounds__(kOneCta) k_tables(const __grid_constant__ RunD
 }
 
 // Copy numbers of the old population (Eq. resampling-factors): one Philox
-// block serves 4 consecutive old slots j (RESAMPLE stream (j>>2, i, 0, 2)).
+// block serves 4 consecutive old slots j (RESAMPLE stream (i, j>>2, 2, 0)).
 __global__ void __launch_bounds__(kTileThreads) k_counts(const __grid_constant__ RunDev r, int step)
 {
     __shared__ uint32_t wsum[kTileThreads / 32];
@@ -519,8 +520,8 @@ __global__ void __launch_bounds__(kTileThreads) k_counts(const __grid_constant__
     const long long j0 = tile0 + 4 * threadIdx.x;
     uint32_t c[4] = {0u, 0u, 0u, 0u};
     if (j0 < Rp) {
-        const uint4 x = philox10(make_uint4((unsigned)(j0 >> 2), (unsigned)step, 0u, kTagResample),
-                                 PhiloxKey{r.k0, r.k1});
+        const uint4 x = philox10(make_uint4((unsigned)step, (unsigned)(j0 >> 2), kTagResample, 0u),
+                                 PhiloxKey{r.key[0], r.key[1]});
         const unsigned xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
         for (int l = 0; l < 4; l++) {
@@ -723,6 +724,23 @@ __global__ void k_philox(const uint32_t* __restrict__ ctr, long long n, PhiloxKe
     reinterpret_cast<uint4*>(out)[i] = philox10(c, key);
 }
 
+// ======================================================== RNG ceiling
+// Philox alone, with the counter layout of the sweep (only word 1 varies
+// across lanes): the words are XOR-folded so none is dead code.
+__global__ void __launch_bounds__(256) k_rng_peak(long long blocks, PhiloxKey key, uint32_t* __restrict__ sink)
+{
+    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
+    uint32_t acc = 0;
+    for (long long q = 0; q < blocks; q += 8) {
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            const uint4 x = philox10(make_uint4(12345u, (unsigned)(q + j) + 64u * tid, kTagSweep, 77u), key);
+            acc ^= x.x ^ x.y ^ x.z ^ x.w;
+        }
+    }
+    sink[tid] = acc;
+}
+
 // ======================================================== launch wrappers
 namespace {
 
@@ -870,6 +888,12 @@ cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint3
     const int threads = 256;
     const long long blocks = (n + threads - 1) / threads;
     k_philox<<<(unsigned)blocks, threads, 0, s>>>(ctr, n, key, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rng_peak(long long blocks, uint32_t* sink, int grid, int threads, cudaStream_t s)
+{
+    k_rng_peak<<<grid, threads, 0, s>>>(blocks, PhiloxKey{0x1234u, 0x5678u}, sink);
     return cudaGetLastError();
 }
 

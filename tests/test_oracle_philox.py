@@ -69,8 +69,8 @@ def test_philox_words_uniform():
     # 2^16 counters -> 2^18 words; chi^2 over 256 byte bins of every byte
     n = 1 << 16
     ctr = np.zeros((n, 4), dtype=np.uint32)
-    ctr[:, 0] = np.arange(n)
-    ctr[:, 3] = 1
+    ctr[:, 1] = np.arange(n)
+    ctr[:, 2] = 1
     w = philox_many(ctr, 12345).ravel()
     for shift in (0, 8, 16, 24):
         h = np.bincount(((w >> shift) & 0xFF).astype(np.int64), minlength=256)
@@ -88,6 +88,6 @@ def test_streams_distinct():
     b = resample_words(1, 2, 64)
     c = resample_words(2, 1, 64)
     assert not np.array_equal(a, b) and not np.array_equal(a, c)
-    # lane layout: word j = lane j&3 of counter (j>>2, i, 0, 2)
-    blk = philox_many(np.array([[3, 1, 0, 2]], dtype=np.uint32), 1)[0]
+    # lane layout: word j = lane j&3 of counter (i, j>>2, 2, 0)
+    blk = philox_many(np.array([[1, 3, 2, 0]], dtype=np.uint32), 1)[0]
     np.testing.assert_array_equal(a[12:16], blk)
