@@ -46,12 +46,44 @@ WORKLOAD = "plain PA, 2D Ising L=64 periodic, R=20000, theta=100, beta 0->1 dbet
 # coding (151 s single-spin); attempts = 4096 * 100 * sum R_i ~ 1.64e12
 PAPER_K80_MSC_FLIPS_PER_NS = 4096 * 100 * 200 * 20000 / 17.0 / 1e9
 
-# per-attempt integer work of the sweep (one site update): a quarter of a
-# Philox4x32-10 block = 5 wide 32x32->64 multiplies (FMA pipe) + 5 three-input
-# XORs (ALU pipe), one threshold compare (ALU), ~15 LOP3 per 32-site word for
-# the bit-sliced neighbour count and flip (ALU, 0.5 per attempt)
-ALU_OPS_PER_ATTEMPT = 5 + 1 + 0.5
-IMAD_OPS_PER_ATTEMPT = 5
+# Integer work of one attempt (one site update) of the sweep kernel:
+#  - a quarter of a Philox4x32-10 block: 20 wide 32x32->64 multiplies and 20
+#    three-input XORs per block; with the counter layout of the sweep the two
+#    first-round products are the same for all lanes of a warp, leaving 16
+#    lane-varying multiplies and 18 XORs, i.e. 4 and 4.5 per attempt;
+#  - one threshold comparison and ~0.5 logic ops (15 LOP3 per 32-site word).
+# A wide multiply occupies the FMA-heavy pipe for 4 cycles per warp (32 lanes
+# per SM per clock, measured: the Philox-only kernel reaches 84% of it); LOP3
+# and compares go to the ALU pipe (64 lanes per SM per clock).
+MUL_OPS_PER_ATTEMPT = 4.0
+ALU_OPS_PER_ATTEMPT = 4.5 + 1.0 + 0.5
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_bits_L64_R20000_theta100.md")
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    with open(os.path.join(ROOT, "paper_1703_03676_gb300", "csrc", "pa_kernels.cu"), "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()[:16]
+
+
+def profiled_traffic():
+    """DRAM bytes per sweep launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    try:
+        text = open(PROFILE_SUMMARY).read()
+    except OSError:
+        return None
+    vals = {}
+    for line in text.splitlines():
+        if ":" in line and line.startswith("- "):
+            k, v = line[2:].split(":", 1)
+            vals[k.strip()] = v.strip().strip("`")
+    if vals.get("kernel_source_sha256") != kernel_source_hash():
+        return None
+    try:
+        return float(vals["dram_bytes_per_launch"])
+    except (KeyError, ValueError):
+        return None
 
 
 def clocks_sampler_start(path):
@@ -265,14 +297,21 @@ def run_engine(args):
         att_per_launch = attempts / max(sw_n, 1)
         sm = torch.cuda.get_device_properties(dev).multi_processor_count
         clk_max = clocks.get("sm_max_mhz") or 2070.0
-        alu_peak = sm * 64 * clk_max * 1e6 / 1e9  # Gop/s: 4 SMSPs x 16 lanes per SM
-        achieved = ALU_OPS_PER_ATTEMPT * att_per_launch / (avg_ms * 1e6)  # Gop/s
-        roofline = {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Gop/s",
-                    "frac": achieved / alu_peak, "traffic": None, "kernel": "k_sweep_bits<64,32>",
-                    "ops_per_attempt": ALU_OPS_PER_ATTEMPT, "attempts_per_ns": att_per_launch / (avg_ms * 1e6),
-                    "launch_ms": avg_ms, "launches": sw_n,
-                    "peak_note": "ALU pipe: SMs x 64 lanes/clk x max SM clock (derived, not measured)",
-                    "share_of_step": sw_ms / dev_ms if dev_ms else None}
+        apn = att_per_launch / (avg_ms * 1e6)  # attempts per ns in the sweep kernel
+        mul_peak = sm * 32 * clk_max * 1e6 / 1e9  # Gop/s, wide multiplies
+        alu_peak = sm * 64 * clk_max * 1e6 / 1e9  # Gop/s, ALU pipe
+        achieved = MUL_OPS_PER_ATTEMPT * apn
+        roofline = {"bound": "alu", "achieved": achieved, "peak": mul_peak, "unit": "Gop/s",
+                    "frac": achieved / mul_peak, "traffic": profiled_traffic(),
+                    "kernel": "k_sweep_bits<64,32>",
+                    "ops": "lane-varying 32x32->64 multiplies of Philox4x32-10, 4 per attempt",
+                    "peak_note": "FMA-heavy pipe: SMs x 32 wide multiplies/clk x max SM clock (derived)",
+                    "alu_pipe": {"achieved": ALU_OPS_PER_ATTEMPT * apn, "peak": alu_peak,
+                                 "frac": ALU_OPS_PER_ATTEMPT * apn / alu_peak,
+                                 "ops": "4.5 Philox XOR + 1 compare + 0.5 logic per attempt"},
+                    "attempts_per_ns": apn, "launch_ms": avg_ms, "launches": sw_n,
+                    "share_of_step": sw_ms / dev_ms if dev_ms else None,
+                    "algorithmic_bytes_per_launch": 2 * att_per_launch / (L * L * theta) * (L * L / 8)}
         try:
             roofline["rng_ceiling_words_per_ns"] = eng.measure_rng_peak(2048, stream)
         except Exception as e:  # measurement only
@@ -334,8 +373,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-replicas", type=int, default=400)
-    ap.add_argument("--ref-replicas", type=int, default=200)
+    ap.add_argument("--cpu-replicas", type=int, default=2000)
+    ap.add_argument("--ref-replicas", type=int, default=400)
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
