@@ -189,6 +189,23 @@ const char *pa_last_error_message(void);
 pa_status pa_philox_device(const uint32_t *dev_ctr, int64_t n, uint64_t seed, uint32_t *dev_out,
                            void *cuda_stream);
 
+/* Nearest-integer resampling of one population on the device (Sec. 2.1,
+ * Eq. resampling-factors, with the copy tables of Eq. Q): copy numbers
+ * r_j = F[k_j] + [x_j < U[k_j]], where k_j = dev_levels[j] is the energy
+ * level of old slot j and x_j the RESAMPLE word of slot j at step `step`
+ * (Philox counter (step, j>>2, 2, 0), lane j&3, key = seed); their
+ * exclusive scan; and dev_parent[o] = j for the r_j new slots o of each j,
+ * in old-slot order. Device inputs: dev_levels[n_old] (0 <= k < n_levels),
+ * dev_F[n_levels] = floor(tau_hat_k), dev_U[n_levels] = ceil(frac 2^32).
+ * Device output: dev_parent[parent_cap]. Host output: *n_new = R_i.
+ * Scratch (about 8 bytes per old slot) is allocated and freed inside the
+ * call. PA_ECAPACITY if R_i > parent_cap (dev_parent is then unspecified),
+ * PA_EEXTINCT if R_i = 0, PA_EINVAL on bad sizes. Synchronous on
+ * `cuda_stream` (NULL: the legacy default stream). */
+pa_status pa_resample(const int32_t *dev_levels, int64_t n_old, const uint32_t *dev_F, const uint64_t *dev_U,
+                      int64_t n_levels, uint64_t seed, int64_t step, uint32_t *dev_parent, int64_t parent_cap,
+                      int64_t *n_new, void *cuda_stream);
+
 /* Throughput ceiling of the random-number generator alone: a persistent
  * kernel that evaluates Philox4x32-10 on `blocks_per_thread` counters per
  * thread over the whole device and XOR-folds the words (one store per

@@ -92,6 +92,8 @@ SIGNATURES = [
     ("pa_last_error_message", ctypes.c_char_p, []),
     ("pa_philox_device", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_uint64, _P, _P]),
     ("pa_measure_rng_peak", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    ("pa_resample", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64, _P,
+                                   ctypes.c_int64, _I64P, _P]),
 ]
 
 
@@ -322,3 +324,24 @@ def measure_rng_peak(blocks_per_thread: int = 4096, stream=None) -> float:
     _check(lib().pa_measure_rng_peak(blocks_per_thread, ctypes.c_void_p(sink.data_ptr()), _stream_handle(stream),
                                      ctypes.byref(out)), "pa_measure_rng_peak")
     return out.value
+
+
+def resample(levels, F, U, seed: int, step: int, capacity: int, stream=None, parent=None):
+    """Nearest-integer resampling on the GPU (pa_resample). levels: CUDA int32
+    tensor of old-slot energy levels; F: CUDA int32 tensor (uint32 bits) of
+    floor(tau_hat) per level; U: CUDA int64 tensor of ceil(frac 2^32) per
+    level. Returns (parent, R_i) with parent a CUDA int32 tensor of length R_i.
+    `parent` may be a caller-provided CUDA int32 tensor of length capacity."""
+    import torch
+    assert levels.is_cuda and levels.dtype == torch.int32 and levels.is_contiguous()
+    assert F.is_cuda and F.dtype == torch.int32 and U.is_cuda and U.dtype == torch.int64 and F.numel() == U.numel()
+    if parent is None:
+        parent = torch.empty(capacity, dtype=torch.int32, device=levels.device)
+    assert parent.is_cuda and parent.dtype == torch.int32 and parent.numel() >= capacity
+    n = ctypes.c_int64()
+    torch.cuda.current_stream().synchronize()
+    _check(lib().pa_resample(ctypes.c_void_p(levels.data_ptr()), levels.numel(), ctypes.c_void_p(F.data_ptr()),
+                             ctypes.c_void_p(U.data_ptr()), F.numel(), seed & 0xFFFFFFFFFFFFFFFF, step,
+                             ctypes.c_void_p(parent.data_ptr()), capacity, ctypes.byref(n), _stream_handle(stream)),
+           "pa_resample")
+    return parent[: n.value], n.value

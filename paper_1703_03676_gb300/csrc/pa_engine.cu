@@ -993,6 +993,76 @@ pa_status pa_philox_device(const uint32_t* ctr, int64_t n, uint64_t seed, uint32
     return PA_OK;
 }
 
+pa_status pa_resample(const int32_t* lev, int64_t n_old, const uint32_t* F, const uint64_t* U, int64_t n_levels,
+                      uint64_t seed, int64_t step, uint32_t* parent, int64_t cap, int64_t* n_new, void* stream)
+{
+    if (!lev || !F || !U || !parent || !n_new || n_old < 1 || n_old > (1ll << 31) || n_levels < 1 || cap < 1 ||
+        step < 0 || step > 0xffffffffll)
+        return PA_EINVAL;
+    *n_new = 0;
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long tiles = (n_old + pa::kTile - 1) / pa::kTile;
+    // scratch: key, counts, local offsets, tile sums/offsets, R_i, status
+    unsigned* key = nullptr;
+    uint32_t *cnt = nullptr, *loc = nullptr, *tsum = nullptr, *toff = nullptr;
+    long long* nn = nullptr;
+    int* st = nullptr;
+    pa_status out = PA_OK;
+    auto grab = [&](void** p, size_t b) {
+        if (out == PA_OK && cudaMalloc(p, b) != cudaSuccess) {
+            cudaGetLastError();
+            out = PA_ENOMEM;
+        }
+    };
+    grab((void**)&key, 16);
+    grab((void**)&cnt, (size_t)n_old * 4);
+    grab((void**)&loc, (size_t)n_old * 4);
+    grab((void**)&tsum, (size_t)tiles * 4);
+    grab((void**)&toff, (size_t)tiles * 4);
+    grab((void**)&nn, 16);
+    grab((void**)&st, 16);
+    if (out == PA_OK) {
+        const unsigned hk[2] = {(unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32)};
+        pa::ResampleArgs a{};
+        a.n_old_dev = nullptr;
+        a.n_old = n_old;
+        a.lev = lev;
+        a.F = F;
+        a.U = (const unsigned long long*)U;
+        a.key = key;
+        a.step = (unsigned)step;
+        a.cnt = cnt;
+        a.loc = loc;
+        a.tile_sum = tsum;
+        a.tile_off = toff;
+        a.parent = parent;
+        a.cap = cap;
+        a.n_new = nn;
+        a.n_prev_out = nullptr;
+        a.status = st;
+        a.work = nullptr;
+        long long hn = 0;
+        int hs = 0;
+        cudaError_t e = cudaMemcpyAsync(key, hk, 8, cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, 16, s);
+        if (e == cudaSuccess) e = pa::launch_resample(a, (int)tiles, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hn, nn, 8, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, st, 4, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) out = from_cuda(e, __LINE__);
+        else if (hs != 0) out = (pa_status)hs;
+        *n_new = hn;
+    }
+    cudaFree(key);
+    cudaFree(cnt);
+    cudaFree(loc);
+    cudaFree(tsum);
+    cudaFree(toff);
+    cudaFree(nn);
+    cudaFree(st);
+    return out;
+}
+
 pa_status pa_measure_rng_peak(int64_t blocks_per_thread, uint32_t* sink, void* stream, double* words_per_ns)
 {
     if (blocks_per_thread < 8 || !sink || !words_per_ns) return PA_EINVAL;

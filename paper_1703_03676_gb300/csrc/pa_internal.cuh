@@ -106,6 +106,30 @@ __device__ __forceinline__ uint4 philox10(uint4 c, PhiloxKey key)
 // stream tags of the counter's fourth word
 constexpr unsigned kTagInit = 0u, kTagSweep = 1u, kTagResample = 2u;
 
+// ---------------------------------------------------------------- resampling
+// Arguments of the three resampling kernels (copy numbers, tile scan, parent
+// scatter). The old population size is read from device memory (n_old_dev,
+// as inside a captured run) or taken by value when n_old_dev is null.
+struct ResampleArgs {
+    const long long* n_old_dev;
+    long long n_old;
+    const int32_t* lev;              // energy level of every old slot
+    const uint32_t* F;               // floor(tau_hat) per level
+    const unsigned long long* U;     // ceil(frac(tau_hat) 2^32) per level
+    const unsigned* key;             // Philox key (2 words, device)
+    unsigned step;                   // temperature step i (RESAMPLE counter word 0)
+    uint32_t* cnt;                   // r_j
+    uint32_t* loc;                   // exclusive prefix of r_j within its tile
+    uint32_t* tile_sum;
+    uint32_t* tile_off;
+    uint32_t* parent;                // new slot -> old slot
+    long long cap;                   // capacity of parent
+    long long* n_new;                // R_i (device)
+    long long* n_prev_out;           // R_{i-1} echo (device, may be null)
+    int* status;                     // set to kStatusCapacity / kStatusExtinct
+    unsigned* work;                  // persistent-kernel counter reset for the sweep (may be null)
+};
+
 // ---------------------------------------------------------------- launches
 struct Launch {
     int sweep_blocks, sweep_threads;  // persistent sweep grid
@@ -118,6 +142,9 @@ cudaError_t launch_tables(const RunDev* d_run, const RunDev& h, int step, cudaSt
 cudaError_t launch_counts(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s);
 cudaError_t launch_scan(const RunDev* d_run, const RunDev& h, int step, cudaStream_t s);
 cudaError_t launch_parent(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s);
+// the same three kernels on plain arguments; tiles = blocks covering the
+// largest old population the launch may see
+cudaError_t launch_resample(const ResampleArgs& a, int tiles, cudaStream_t s);
 cudaError_t launch_sweep(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s);
 cudaError_t launch_stats(const RunDev* d_run, const RunDev& h, int step, cudaStream_t s);
 cudaError_t launch_rng_peak(long long blocks, uint32_t* sink, int grid, int threads, cudaStream_t s);

@@ -509,26 +509,30 @@ __global__ void __launch_bounds__(kOneCta) k_tables(const __grid_constant__ RunD
 
 // Copy numbers of the old population (Eq. resampling-factors): one Philox
 // block serves 4 consecutive old slots j (RESAMPLE stream (i, j>>2, 2, 0)).
-__global__ void __launch_bounds__(kTileThreads) k_counts(const __grid_constant__ RunDev r, int step)
+__device__ __forceinline__ long long n_old_of(const ResampleArgs& a)
+{
+    return a.n_old_dev ? *a.n_old_dev : a.n_old;
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_counts(const __grid_constant__ ResampleArgs a)
 {
     __shared__ uint32_t wsum[kTileThreads / 32];
-    if (*r.status) return;
-    const long long Rp = r.rec[step - 1].R;
+    if (*a.status) return;
+    const long long Rp = n_old_of(a);
     const long long tile0 = (long long)blockIdx.x * kTile;
     if (tile0 >= Rp) return;
-    const int cur = (step - 1) & 1;
     const long long j0 = tile0 + 4 * threadIdx.x;
     uint32_t c[4] = {0u, 0u, 0u, 0u};
     if (j0 < Rp) {
-        const uint4 x = philox10(make_uint4((unsigned)step, (unsigned)(j0 >> 2), kTagResample, 0u),
-                                 PhiloxKey{r.key[0], r.key[1]});
+        const uint4 x = philox10(make_uint4(a.step, (unsigned)(j0 >> 2), kTagResample, 0u),
+                                 PhiloxKey{a.key[0], a.key[1]});
         const unsigned xs[4] = {x.x, x.y, x.z, x.w};
 #pragma unroll
         for (int l = 0; l < 4; l++) {
             const long long j = j0 + l;
             if (j < Rp) {
-                const int lv = r.elev[cur][j];
-                c[l] = r.F[lv] + (((unsigned long long)xs[l] < r.U[lv]) ? 1u : 0u);
+                const int lv = a.lev[j];
+                c[l] = a.F[lv] + (((unsigned long long)xs[l] < a.U[lv]) ? 1u : 0u);
             }
         }
     }
@@ -550,30 +554,30 @@ __global__ void __launch_bounds__(kTileThreads) k_counts(const __grid_constant__
     for (int l = 0; l < 4; l++) {
         const long long j = j0 + l;
         if (j < Rp) {
-            r.cnt[j] = c[l];
-            r.loc[j] = run;
+            a.cnt[j] = c[l];
+            a.loc[j] = run;
         }
         run += c[l];
     }
     if (threadIdx.x == kTileThreads - 1) {
         uint32_t tot = 0;
         for (int w = 0; w < kTileThreads / 32; w++) tot += wsum[w];
-        r.tile_sum[blockIdx.x] = tot;
+        a.tile_sum[blockIdx.x] = tot;
     }
 }
 
 // Exclusive scan of the tile totals; R_i and the capacity check.
-__global__ void __launch_bounds__(kOneCta) k_scan(const __grid_constant__ RunDev r, int step)
+__global__ void __launch_bounds__(kOneCta) k_scan(const __grid_constant__ ResampleArgs a)
 {
     __shared__ unsigned long long part[kOneCta];
-    if (*r.status) return;
+    if (*a.status) return;
     const int t = threadIdx.x;
-    const long long Rp = r.rec[step - 1].R;
+    const long long Rp = n_old_of(a);
     const int ntiles = (int)((Rp + kTile - 1) / kTile);
     const int per = (ntiles + kOneCta - 1) / kOneCta;
     const int lo = t * per, hi = min(lo + per, ntiles);
     unsigned long long sum = 0;
-    for (int i = lo; i < hi; i++) sum += r.tile_sum[i];
+    for (int i = lo; i < hi; i++) sum += a.tile_sum[i];
     part[t] = sum;
     __syncthreads();
     // inclusive Hillis-Steele scan over the 1024 partial sums
@@ -585,28 +589,29 @@ __global__ void __launch_bounds__(kOneCta) k_scan(const __grid_constant__ RunDev
     }
     unsigned long long run = part[t] - sum;
     for (int i = lo; i < hi; i++) {
-        r.tile_off[i] = (uint32_t)run;
-        run += r.tile_sum[i];
+        a.tile_off[i] = (uint32_t)run;
+        run += a.tile_sum[i];
     }
     if (t == 0) {
         const unsigned long long Ri = part[kOneCta - 1];
-        r.rec[step].R = (long long)Ri;
-        r.rec[step].R_prev = Rp;
-        if ((long long)Ri > r.cap) *r.status = kStatusCapacity;
-        else if (Ri == 0) *r.status = kStatusExtinct;
+        *a.n_new = (long long)Ri;
+        if (a.n_prev_out) *a.n_prev_out = Rp;
+        if ((long long)Ri > a.cap) *a.status = kStatusCapacity;
+        else if (Ri == 0) *a.status = kStatusExtinct;
+        if (a.work) *a.work = 0u;
     }
 }
 
 // parent[o_j + c] = j for c < r_j: new slots keep the order of old slots.
-__global__ void __launch_bounds__(kTile) k_parent(const __grid_constant__ RunDev r, int step)
+__global__ void __launch_bounds__(kTile) k_parent(const __grid_constant__ ResampleArgs a)
 {
-    if (*r.status) return;
-    const long long Rp = r.rec[step - 1].R;
+    if (*a.status) return;
+    const long long Rp = n_old_of(a);
     const long long j = (long long)blockIdx.x * kTile + threadIdx.x;
     if (j >= Rp) return;
-    const uint32_t n = r.cnt[j];
-    const uint32_t o = r.tile_off[blockIdx.x] + r.loc[j];
-    for (uint32_t c = 0; c < n; c++) r.parent[o + c] = (uint32_t)j;
+    const uint32_t n = a.cnt[j];
+    const uint32_t o = a.tile_off[blockIdx.x] + a.loc[j];
+    for (uint32_t c = 0; c < n; c++) a.parent[o + c] = (uint32_t)j;
 }
 
 // ======================================================== statistics
@@ -858,21 +863,56 @@ cudaError_t launch_tables(const RunDev* /*d_run*/, const RunDev& h, int step, cu
     return cudaGetLastError();
 }
 
+static ResampleArgs resample_args(const RunDev& h, int step)
+{
+    ResampleArgs a{};
+    a.n_old_dev = &h.rec[step - 1].R;
+    a.n_old = 0;
+    a.lev = h.elev[(step - 1) & 1];
+    a.F = h.F;
+    a.U = h.U;
+    a.key = h.key;
+    a.step = (unsigned)step;
+    a.cnt = h.cnt;
+    a.loc = h.loc;
+    a.tile_sum = h.tile_sum;
+    a.tile_off = h.tile_off;
+    a.parent = h.parent;
+    a.cap = h.cap;
+    a.n_new = &h.rec[step].R;
+    a.n_prev_out = &h.rec[step].R_prev;
+    a.status = h.status;
+    a.work = h.work;
+    return a;
+}
+
 cudaError_t launch_counts(const RunDev* /*d_run*/, const RunDev& h, const Launch& ln, int step, cudaStream_t s)
 {
-    k_counts<<<ln.count_blocks, kTileThreads, 0, s>>>(h, step);
+    k_counts<<<ln.count_blocks, kTileThreads, 0, s>>>(resample_args(h, step));
     return cudaGetLastError();
 }
 
 cudaError_t launch_scan(const RunDev* /*d_run*/, const RunDev& h, int step, cudaStream_t s)
 {
-    k_scan<<<1, kOneCta, 0, s>>>(h, step);
+    k_scan<<<1, kOneCta, 0, s>>>(resample_args(h, step));
     return cudaGetLastError();
 }
 
 cudaError_t launch_parent(const RunDev* /*d_run*/, const RunDev& h, const Launch& ln, int step, cudaStream_t s)
 {
-    k_parent<<<ln.count_blocks, kTile, 0, s>>>(h, step);
+    k_parent<<<ln.count_blocks, kTile, 0, s>>>(resample_args(h, step));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample(const ResampleArgs& a, int tiles, cudaStream_t s)
+{
+    if (tiles < 1) return cudaErrorInvalidValue;
+    k_counts<<<tiles, kTileThreads, 0, s>>>(a);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    k_scan<<<1, kOneCta, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    k_parent<<<tiles, kTile, 0, s>>>(a);
     return cudaGetLastError();
 }
 
