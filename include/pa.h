@@ -206,6 +206,28 @@ pa_status pa_resample(const int32_t *dev_levels, int64_t n_old, const uint32_t *
                       int64_t n_levels, uint64_t seed, int64_t step, uint32_t *dev_parent, int64_t parent_cap,
                       int64_t *n_new, void *cuda_stream);
 
+/* Allocation-free pa_resample, for callers that must not allocate device
+ * memory once they are running: a server whose device memory is fixed by
+ * an admission budget, a host program whose device memory belongs to
+ * another allocator (a framework's caching allocator) that a raw cudaMalloc
+ * would bypass, or a loop where cudaMalloc/cudaFree would synchronise the
+ * device and stall other streams. The paper has no counterpart: it is an
+ * interface variant of pa_resample, with the same arguments, results and
+ * errors. Its scratch is one static device array of the library
+ * (PA_RESAMPLE_NOALLOC_MAX_OLD old slots: about 2 MiB, held on every GPU
+ * that loads the library until the process exits); the caller still
+ * provides the input and output buffers. n_old > PA_RESAMPLE_NOALLOC_MAX_OLD
+ * returns PA_EINVAL (see pa_last_error_message). The first call on a device
+ * looks up the array's device address with that device current; make that
+ * first call before any stream capture. All calls share the one array, so
+ * calls whose work overlaps on the GPU (several streams or threads at once)
+ * race and give wrong results: serialise them. No call allocates or frees
+ * device memory. */
+#define PA_RESAMPLE_NOALLOC_MAX_OLD 262144
+pa_status pa_resample_noalloc(const int32_t *dev_levels, int64_t n_old, const uint32_t *dev_F,
+                              const uint64_t *dev_U, int64_t n_levels, uint64_t seed, int64_t step,
+                              uint32_t *dev_parent, int64_t parent_cap, int64_t *n_new, void *cuda_stream);
+
 /* Throughput ceiling of the random-number generator alone: a persistent
  * kernel that evaluates Philox4x32-10 on `blocks_per_thread` counters per
  * thread over the whole device and XOR-folds the words (one store per

@@ -94,6 +94,8 @@ SIGNATURES = [
     ("pa_measure_rng_peak", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     ("pa_resample", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64, _P,
                                    ctypes.c_int64, _I64P, _P]),
+    ("pa_resample_noalloc", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.c_uint64,
+                                           ctypes.c_int64, _P, ctypes.c_int64, _I64P, _P]),
 ]
 
 
@@ -326,12 +328,18 @@ def measure_rng_peak(blocks_per_thread: int = 4096, stream=None) -> float:
     return out.value
 
 
-def resample(levels, F, U, seed: int, step: int, capacity: int, stream=None, parent=None):
+RESAMPLE_NOALLOC_MAX_OLD = 262144
+
+
+def resample(levels, F, U, seed: int, step: int, capacity: int, stream=None, parent=None, noalloc=False):
     """Nearest-integer resampling on the GPU (pa_resample). levels: CUDA int32
     tensor of old-slot energy levels; F: CUDA int32 tensor (uint32 bits) of
     floor(tau_hat) per level; U: CUDA int64 tensor of ceil(frac 2^32) per
     level. Returns (parent, R_i) with parent a CUDA int32 tensor of length R_i.
-    `parent` may be a caller-provided CUDA int32 tensor of length capacity."""
+    `parent` may be a caller-provided CUDA int32 tensor of length capacity.
+    noalloc=True calls pa_resample_noalloc, which allocates no device memory
+    (its scratch is a static array of the library; at most
+    RESAMPLE_NOALLOC_MAX_OLD old slots; calls must not overlap on the GPU)."""
     import torch
     assert levels.is_cuda and levels.dtype == torch.int32 and levels.is_contiguous()
     assert F.is_cuda and F.dtype == torch.int32 and U.is_cuda and U.dtype == torch.int64 and F.numel() == U.numel()
@@ -340,8 +348,9 @@ def resample(levels, F, U, seed: int, step: int, capacity: int, stream=None, par
     assert parent.is_cuda and parent.dtype == torch.int32 and parent.numel() >= capacity
     n = ctypes.c_int64()
     torch.cuda.current_stream().synchronize()
-    _check(lib().pa_resample(ctypes.c_void_p(levels.data_ptr()), levels.numel(), ctypes.c_void_p(F.data_ptr()),
+    fn = lib().pa_resample_noalloc if noalloc else lib().pa_resample
+    _check(fn(ctypes.c_void_p(levels.data_ptr()), levels.numel(), ctypes.c_void_p(F.data_ptr()),
                              ctypes.c_void_p(U.data_ptr()), F.numel(), seed & 0xFFFFFFFFFFFFFFFF, step,
                              ctypes.c_void_p(parent.data_ptr()), capacity, ctypes.byref(n), _stream_handle(stream)),
-           "pa_resample")
+           "pa_resample_noalloc" if noalloc else "pa_resample")
     return parent[: n.value], n.value

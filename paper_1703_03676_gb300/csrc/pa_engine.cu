@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -574,6 +575,45 @@ pa_status free_all(pa_ctx* c)
 
 }  // namespace
 
+// ============================================== allocation-free resampling
+// Scratch of pa_resample_noalloc: one static device array, laid out as
+// [key 16 B | R_i 8 B | status 4 B | tile sums | tile offsets | r_j | local
+// offsets], every part 256-byte aligned. Host code cannot use the array's
+// name as a device address: the address comes from cudaGetSymbolAddress,
+// looked up once per device with that device current.
+namespace {
+constexpr long long kNoAllocMaxOld = PA_RESAMPLE_NOALLOC_MAX_OLD;
+constexpr long long kNoAllocTiles = (kNoAllocMaxOld + pa::kTile - 1) / pa::kTile;
+constexpr size_t kOffKey = 0, kOffN = 256, kOffStatus = 512, kOffTileSum = 768;
+constexpr size_t kOffTileOff = ((kOffTileSum + kNoAllocTiles * 4 + 255) / 256) * 256;
+constexpr size_t kOffCnt = ((kOffTileOff + kNoAllocTiles * 4 + 255) / 256) * 256;
+constexpr size_t kOffLoc = kOffCnt + (size_t)kNoAllocMaxOld * 4;
+constexpr size_t kNoAllocBytes = kOffLoc + (size_t)kNoAllocMaxOld * 4;
+constexpr int kMaxDevices = 64;
+}  // namespace
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+namespace {
+std::mutex g_noalloc_mu;
+unsigned char* g_noalloc_addr[kMaxDevices] = {};
+
+pa_status noalloc_scratch(unsigned char** out)
+{
+    int dev = 0;
+    PA_CUDA(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return PA_EINVAL;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+        void* p = nullptr;
+        PA_CUDA(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        g_noalloc_addr[dev] = (unsigned char*)p;
+    }
+    *out = g_noalloc_addr[dev];
+    return PA_OK;
+}
+}  // namespace
+
 // ======================================================================= ABI
 extern "C" {
 
@@ -1061,6 +1101,60 @@ pa_status pa_resample(const int32_t* lev, int64_t n_old, const uint32_t* F, cons
     cudaFree(nn);
     cudaFree(st);
     return out;
+}
+
+pa_status pa_resample_noalloc(const int32_t* lev, int64_t n_old, const uint32_t* F, const uint64_t* U,
+                              int64_t n_levels, uint64_t seed, int64_t step, uint32_t* parent, int64_t cap,
+                              int64_t* n_new, void* stream)
+{
+    if (!lev || !F || !U || !parent || !n_new || n_old < 1 || n_levels < 1 || cap < 1 || step < 0 ||
+        step > 0xffffffffll)
+        return PA_EINVAL;
+    *n_new = 0;
+    if (n_old > kNoAllocMaxOld) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "pa_resample_noalloc: n_old %lld exceeds the static scratch limit %lld", (long long)n_old,
+                      kNoAllocMaxOld);
+        return PA_EINVAL;
+    }
+    unsigned char* base = nullptr;
+    PA_TRY(noalloc_scratch(&base));
+    cudaStream_t s = (cudaStream_t)stream;
+    const long long tiles = (n_old + pa::kTile - 1) / pa::kTile;
+    unsigned* key = (unsigned*)(base + kOffKey);
+    long long* nn = (long long*)(base + kOffN);
+    int* st = (int*)(base + kOffStatus);
+    pa::ResampleArgs a{};
+    a.n_old_dev = nullptr;
+    a.n_old = n_old;
+    a.lev = lev;
+    a.F = F;
+    a.U = (const unsigned long long*)U;
+    a.key = key;
+    a.step = (unsigned)step;
+    a.cnt = (uint32_t*)(base + kOffCnt);
+    a.loc = (uint32_t*)(base + kOffLoc);
+    a.tile_sum = (uint32_t*)(base + kOffTileSum);
+    a.tile_off = (uint32_t*)(base + kOffTileOff);
+    a.parent = parent;
+    a.cap = cap;
+    a.n_new = nn;
+    a.n_prev_out = nullptr;
+    a.status = st;
+    a.work = nullptr;
+    // the array keeps the previous call's contents: the status word must
+    // start at zero; every other part is written before it is read
+    const unsigned hk[2] = {(unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32)};
+    long long hn = 0;
+    int hs = 0;
+    PA_CUDA(cudaMemcpyAsync(key, hk, 8, cudaMemcpyHostToDevice, s));
+    PA_CUDA(cudaMemsetAsync(st, 0, 4, s));
+    PA_CUDA(pa::launch_resample(a, (int)tiles, s));
+    PA_CUDA(cudaMemcpyAsync(&hn, nn, 8, cudaMemcpyDeviceToHost, s));
+    PA_CUDA(cudaMemcpyAsync(&hs, st, 4, cudaMemcpyDeviceToHost, s));
+    PA_CUDA(cudaStreamSynchronize(s));
+    *n_new = hn;
+    return hs != 0 ? (pa_status)hs : PA_OK;
 }
 
 pa_status pa_measure_rng_peak(int64_t blocks_per_thread, uint32_t* sink, void* stream, double* words_per_ns)
