@@ -67,7 +67,9 @@ typedef struct {
     int32_t spin_format;    /* pa_spin_format                                     */
     int32_t record_histograms; /* != 0: keep H_E and H_M of every step            */
     int64_t capacity;       /* population buffer size; 0 -> ceil(1.05 R) + 1024   */
-    int32_t group_threads;  /* threads per replica in the sweep; 0 -> autotune    */
+    int32_t group_threads;  /* threads per replica in the sweep: 1..32 (power of
+                               two dividing the plane's words) or 256 (one
+                               replica per CTA, bit-packed); 0 -> default       */
     int32_t use_graph;      /* != 0: pa_run captures the fixed schedule as one
                                CUDA graph                                       */
     int32_t profile;        /* != 0: time every kernel phase with CUDA events     */
@@ -180,6 +182,43 @@ const char *pa_strerror(pa_status s);
 /* Text of the last CUDA failure seen by a call on this thread (the CUDA
  * error name and the engine source line), or "" if none. */
 const char *pa_last_error_message(void);
+
+/* ---- batches of independent runs ---------------------------------------
+ * Many independent fixed-schedule runs (spec batching; Sec. 2.2 notes
+ * that independent runs combine by free-energy weights) stepped together:
+ * every phase of a temperature step is one launch for all runs and the
+ * sweep is one persistent kernel whose warps take (run, replica batch) work
+ * items from a single queue ordered by descending work per replica. The
+ * whole schedule is one CUDA graph, captured on the first launch and reused
+ * after pa_batch_reset. Each run's results are those of the same pa_config
+ * run alone, bit for bit. Runs must use fixed steps (dbeta > 0), bit-packed
+ * spins and L <= 256; group_threads == 0 picks the threads per replica by a
+ * timed probe per L (cached per process). */
+typedef struct pa_batch pa_batch;
+
+/* Create n runs (their beta0 populations are generated). Errors as pa_create. */
+pa_status pa_batch_create(const pa_config *cfgs, int32_t n, void *cuda_stream, pa_batch **out);
+/* Enqueue every run's whole schedule (one graph launch) without waiting.
+ * PA_ESTATE unless every run is at step 0. */
+pa_status pa_batch_launch(pa_batch *b);
+/* Wait for the batch; returns the first failing run's status (others keep
+ * going and keep their rows). */
+pa_status pa_batch_sync(pa_batch *b);
+/* pa_batch_launch + pa_batch_sync. */
+pa_status pa_batch_run(pa_batch *b);
+/* Back to step 0 with seeds[i] for run i (host array of n seeds). */
+pa_status pa_batch_reset(pa_batch *b, const uint64_t *seeds);
+/* Borrow run i as a pa_ctx for read-only calls (observables, histograms,
+ * population, MHR); stepping calls on it return PA_ESTATE and pa_destroy on
+ * it does nothing. Valid until pa_batch_destroy. */
+pa_status pa_batch_get(pa_batch *b, int32_t i, pa_ctx **out);
+/* Accumulated device time per phase of the batched steps (needs profile in
+ * any of the configs): [0] tables, [1] counts, [2] scan, [3] parent,
+ * [4] plan + sweep, [5] stats. */
+pa_status pa_batch_phase_times(pa_batch *b, double ms[7], int64_t launches[7]);
+/* Threads per replica used for run i and the persistent sweep grid size. */
+pa_status pa_batch_shape(pa_batch *b, int32_t i, int32_t *group_threads, int32_t *sweep_blocks);
+void pa_batch_destroy(pa_batch *b);
 
 /* ---- kernel-level entry points (device pointers, for tests) ----------- */
 

@@ -91,6 +91,16 @@ SIGNATURES = [
     ("pa_strerror", ctypes.c_char_p, [ctypes.c_int]),
     ("pa_last_error_message", ctypes.c_char_p, []),
     ("pa_philox_device", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_uint64, _P, _P]),
+    ("pa_batch_create", ctypes.c_int, [ctypes.POINTER(_Config), ctypes.c_int32, _P, ctypes.POINTER(_P)]),
+    ("pa_batch_launch", ctypes.c_int, [_P]),
+    ("pa_batch_sync", ctypes.c_int, [_P]),
+    ("pa_batch_run", ctypes.c_int, [_P]),
+    ("pa_batch_reset", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
+    ("pa_batch_get", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(_P)]),
+    ("pa_batch_phase_times", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I64P]),
+    ("pa_batch_shape", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
+                                      ctypes.POINTER(ctypes.c_int32)]),
+    ("pa_batch_destroy", None, [_P]),
     ("pa_measure_rng_peak", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     ("pa_resample", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64, _P,
                                    ctypes.c_int64, _I64P, _P]),
@@ -304,6 +314,81 @@ class PARun:
         return {"group_threads": g.value, "block_threads": b.value, "grid_blocks": n.value}
 
 
+class _BorrowedRun(PARun):
+    """A run owned by a PABatch: read-only access through the PARun methods."""
+
+    def __init__(self, handle, cfg):  # noqa: D401 - no pa_create
+        self.cfg = cfg
+        self._lib = lib()
+        self._h = handle
+        self.N = cfg.L * cfg.L
+
+    def close(self):
+        self._h = ctypes.c_void_p()
+
+
+class PABatch:
+    """Independent fixed-schedule runs stepped together in one CUDA graph
+    (pa_batch_*). runs[i] gives read-only access to run i."""
+
+    def __init__(self, cfgs, stream=None):
+        self._lib = lib()
+        self.cfgs = list(cfgs)
+        arr = (_Config * len(self.cfgs))(*[c._c() for c in self.cfgs])
+        self._h = ctypes.c_void_p()
+        _check(self._lib.pa_batch_create(arr, len(self.cfgs), _stream_handle(stream), ctypes.byref(self._h)),
+               "pa_batch_create")
+        self.runs = []
+        for i, c in enumerate(self.cfgs):
+            h = ctypes.c_void_p()
+            _check(self._lib.pa_batch_get(self._h, i, ctypes.byref(h)), "pa_batch_get")
+            self.runs.append(_BorrowedRun(h, c))
+
+    def launch(self):
+        _check(self._lib.pa_batch_launch(self._h), "pa_batch_launch")
+        return self
+
+    def sync(self):
+        _check(self._lib.pa_batch_sync(self._h), "pa_batch_sync")
+        return self
+
+    def run(self):
+        _check(self._lib.pa_batch_run(self._h), "pa_batch_run")
+        return self
+
+    def reset(self, seeds):
+        arr = (ctypes.c_uint64 * len(self.cfgs))(*[int(s) & 0xFFFFFFFFFFFFFFFF for s in seeds])
+        _check(self._lib.pa_batch_reset(self._h, arr), "pa_batch_reset")
+        for c, s in zip(self.cfgs, seeds):
+            c.seed = int(s)
+        return self
+
+    def phase_times(self):
+        ms = (ctypes.c_double * 7)()
+        n = (ctypes.c_int64 * 7)()
+        _check(self._lib.pa_batch_phase_times(self._h, ms, n), "pa_batch_phase_times")
+        names = ["tables", "counts", "scan", "parent", "sweep", "stats", "init"]
+        return {k: (ms[i], n[i]) for i, k in enumerate(names)}
+
+    def shape(self, i):
+        g, nb = ctypes.c_int32(), ctypes.c_int32()
+        _check(self._lib.pa_batch_shape(self._h, i, ctypes.byref(g), ctypes.byref(nb)), "pa_batch_shape")
+        return {"group_threads": g.value, "sweep_blocks": nb.value}
+
+    def close(self):
+        if self._h:
+            for r in self.runs:
+                r.close()
+            self._lib.pa_batch_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 def philox_device(ctr, seed: int, stream=None):
     """Philox4x32-10 on the GPU: ctr is a CUDA int32/uint32 tensor of shape
     (n, 4); returns a tensor of the same shape with the outputs."""
@@ -354,3 +439,17 @@ def resample(levels, F, U, seed: int, step: int, capacity: int, stream=None, par
                              ctypes.c_void_p(parent.data_ptr()), capacity, ctypes.byref(n), _stream_handle(stream)),
            "pa_resample_noalloc" if noalloc else "pa_resample")
     return parent[: n.value], n.value
+
+
+def batch_config4_draw(n: int = 64, seed: int = 99, stream=None):
+    """(L, R, theta) of the batched-PA workload: run r draws Philox4x32-10
+    (key = seed) at counter (0, r, 3, 0); L = {16, 32, 64, 128}[w0 mod 4],
+    R = 2000 + w1 mod 48001 (uniform in 2000..50000), theta =
+    {10, 50, 100}[w2 mod 3]. Evaluated with the engine's device Philox."""
+    import torch
+    ctr = torch.zeros((n, 4), dtype=torch.int32)
+    ctr[:, 1] = torch.arange(n, dtype=torch.int32)
+    ctr[:, 2] = 3
+    w = philox_device(ctr.cuda(), seed, stream).cpu().numpy().view(np.uint32).astype(np.int64)
+    return [([16, 32, 64, 128][w[r, 0] % 4], 2000 + int(w[r, 1] % 48001), [10, 50, 100][w[r, 2] % 3])
+            for r in range(n)]

@@ -19,6 +19,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <vector>
@@ -87,6 +88,7 @@ struct pa_ctx {
     long long done_rows = 0;      // rows whose records are on the host
     bool done = false;            // beta_f reached
     pa_status failed = PA_OK;     // sticky device failure
+    bool in_batch = false;        // stepped by a pa_batch, read-only for the caller
     std::vector<double> betas;    // beta_i for i = 0..enq_step
     std::vector<double> deltas;   // step size used by step i (0 for i = 0)
     std::vector<uint64_t> T4, T8;
@@ -146,7 +148,8 @@ pa_status validate(const pa_config& c)
         if (n < 1 || n > 1e7) return PA_EINVAL;
     }
     if (c.capacity < 0 || (c.capacity > 0 && c.capacity < c.R)) return PA_EINVAL;
-    if (c.group_threads < 0 || c.group_threads > 32 || (c.group_threads & (c.group_threads - 1))) return PA_EINVAL;
+    if (c.group_threads < 0 || (c.group_threads & (c.group_threads - 1))) return PA_EINVAL;
+    if (c.group_threads > 32 && !(c.group_threads == 256 && c.spin_format == PA_SPIN_BITS32)) return PA_EINVAL;
     if (c.reserved[0] || c.reserved[1] || c.reserved[2]) return PA_EINVAL;
     return PA_OK;
 }
@@ -170,6 +173,7 @@ int auto_group(const pa_config& c)
     const long long N = (long long)c.L * c.L;
     if (c.spin_format == PA_SPIN_BITS32) {
         const long long wp = N / 64;
+        if (wp >= 4096) return 256;  // L >= 512: one replica per CTA
         int g = 32;
         while (g > 1 && wp % g) g >>= 1;
         return g;
@@ -700,6 +704,7 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
     h.ntiles = (int)s.ntiles;
     h.record_hist = cfg->record_histograms ? 1 : 0;
     h.hist_steps = (int)s.hist_steps;
+    h.nsteps = (int)s.steps;
     const size_t N1 = (size_t)s.N + 1;
     pa_status st = PA_OK;
 #define PA_ALLOC(p, n)                            \
@@ -769,6 +774,7 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
 pa_status pa_step(pa_ctx* c)
 {
     if (!c) return PA_EINVAL;
+    if (c->in_batch) return PA_ESTATE;
     if (c->failed != PA_OK) return c->failed;
     return enqueue_step(c);
 }
@@ -782,6 +788,7 @@ pa_status pa_sync(pa_ctx* c)
 pa_status pa_run(pa_ctx* c)
 {
     if (!c) return PA_EINVAL;
+    if (c->in_batch) return PA_ESTATE;
     PA_TRY(launch_rest(c));
     return pull_records(c);
 }
@@ -789,12 +796,14 @@ pa_status pa_run(pa_ctx* c)
 pa_status pa_launch(pa_ctx* c)
 {
     if (!c) return PA_EINVAL;
+    if (c->in_batch) return PA_ESTATE;
     return launch_rest(c);
 }
 
 pa_status pa_reset(pa_ctx* c, uint64_t seed)
 {
     if (!c) return PA_EINVAL;
+    if (c->in_batch) return PA_ESTATE;
     return reset_run(c, seed);
 }
 
@@ -1018,7 +1027,7 @@ pa_status pa_launch_shape(pa_ctx* c, int32_t* gt, int32_t* bt, int32_t* gb)
 
 void pa_destroy(pa_ctx* c)
 {
-    if (!c) return;
+    if (!c || c->in_batch) return;
     cudaStreamSynchronize(c->stream);
     free_all(c);
     delete c;
@@ -1180,6 +1189,351 @@ pa_status pa_measure_rng_peak(int64_t blocks_per_thread, uint32_t* sink, void* s
     cudaEventDestroy(b);
     *words_per_ns = 4.0 * (double)blocks * (double)grid * threads / ((double)ms * 1e6);
     return PA_OK;
+}
+
+}  // extern "C"
+
+// ================================================================== batches
+// Independent fixed-schedule runs stepped together (spec batching):
+// each phase of a temperature step is one launch over all runs, and the
+// sweep is one persistent kernel whose warps pull (run, replica batch)
+// items from a single queue ordered by descending work per replica. The
+// whole schedule is captured once as one CUDA graph.
+struct pa_batch {
+    std::vector<pa_ctx*> runs;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    std::vector<void*> allocs;
+    pa::BatchDev bd{};
+    pa::BatchLaunch ln{};
+    int max_steps = 0;
+    cudaGraphExec_t graph = nullptr;
+    bool profile = false;
+    std::vector<cudaEvent_t> ev;  // (start, end) per phase launch in the graph
+    std::vector<int> ev_phase;
+    bool ev_pending = false;
+    double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};
+    long long phase_n[7] = {0, 0, 0, 0, 0, 0, 0};
+};
+
+namespace {
+
+// Autotuned threads per replica for the batched sweep, per (L, SM count):
+// the candidate with the fastest sweep on a probe run. Results never depend
+// on the choice; only speed does.
+std::mutex g_tune_mu;
+std::map<long long, int> g_tuned;
+
+int batch_candidates(int L, int out[4])
+{
+    int n = 0;
+    for (int g : {1, 2, 4, 8, 16, 32})
+        if (pa::batch_supports(L, g)) out[n++] = g;
+    return n;
+}
+
+pa_status tune_group(int L, void* stream, int* out)
+{
+    int dev = 0, sms = 0;
+    PA_CUDA(cudaGetDevice(&dev));
+    PA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long key = (long long)L * 100000 + sms;
+    {
+        std::lock_guard<std::mutex> g(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) {
+            *out = it->second;
+            return PA_OK;
+        }
+    }
+    int cand[4];
+    const int nc = batch_candidates(L, cand);
+    if (nc == 0) return PA_EINVAL;
+    int best = cand[0];
+    double best_ms = 1e300;
+    for (int i = 0; i < nc && nc > 1; i++) {
+        pa_config pc;
+        pa_config_default(&pc);
+        pc.L = L;
+        pc.R = std::max(2048ll, 4ll * 152 * (32 / cand[i]) * 8);
+        pc.theta = 4;
+        pc.beta_f = 0.02;
+        pc.dbeta = 0.01;
+        pc.spin_format = PA_SPIN_BITS32;
+        pc.group_threads = cand[i];
+        pc.use_graph = 0;
+        pc.profile = 1;
+        pa_ctx* t = nullptr;
+        PA_TRY(pa_create(&pc, stream, &t));
+        pa_status st = pa_run(t);
+        double ms[7];
+        int64_t n[7];
+        if (st == PA_OK) st = pa_phase_times(t, ms, n);
+        pa_destroy(t);
+        PA_TRY(st);
+        if (ms[4] < best_ms) {
+            best_ms = ms[4];
+            best = cand[i];
+        }
+    }
+    std::lock_guard<std::mutex> g(g_tune_mu);
+    g_tuned[key] = best;
+    *out = best;
+    return PA_OK;
+}
+
+// host side of a fixed schedule: the betas of every step the graph runs
+void advance_fixed(pa_ctx* c)
+{
+    while (!c->done) {
+        const long long i = c->enq_step + 1;
+        c->betas.push_back(0.0 + (double)i * c->cfg.dbeta);
+        c->deltas.push_back(c->cfg.dbeta);
+        c->enq_step = i;
+        if (i == c->n_fixed) c->done = true;
+    }
+}
+
+void batch_free(pa_batch* b)
+{
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+    for (pa_ctx* c : b->runs) {
+        if (!c) continue;
+        c->in_batch = false;
+        c->own_stream = false;
+        pa_destroy(c);
+    }
+    for (void* p : b->allocs) cudaFree(p);
+    if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+}
+
+pa_status batch_record(pa_batch* b, int phase)
+{
+    if (!b->profile) return PA_OK;
+    cudaEvent_t e;
+    PA_CUDA(cudaEventCreate(&e));
+    PA_CUDA(cudaEventRecordWithFlags(e, b->stream, cudaEventRecordExternal));
+    b->ev.push_back(e);
+    b->ev_phase.push_back(phase);
+    return PA_OK;
+}
+
+pa_status batch_collect(pa_batch* b)
+{
+    if (!b->ev_pending) return PA_OK;
+    for (size_t i = 0; i + 1 < b->ev.size(); i += 2) {
+        float ms = 0.f;
+        PA_CUDA(cudaEventElapsedTime(&ms, b->ev[i], b->ev[i + 1]));
+        b->phase_ms[b->ev_phase[i]] += ms;
+        b->phase_n[b->ev_phase[i]] += 1;
+    }
+    b->ev_pending = false;
+    return PA_OK;
+}
+
+pa_status batch_capture(pa_batch* b)
+{
+    cudaStream_t cap = nullptr;
+    PA_CUDA(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaStream_t saved = b->stream;
+    b->stream = cap;
+    pa_status st = PA_OK;
+    cudaGraph_t g = nullptr;
+    if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = PA_ECUDA;
+    for (int step = 1; st == PA_OK && step <= b->max_steps; step++) {
+        for (int phase = 0; phase < 6 && st == PA_OK; phase++) {
+            st = batch_record(b, phase);
+            if (st == PA_OK && pa::launch_batch_step(b->bd, b->ln, step, cap, phase, nullptr) != cudaSuccess)
+                st = PA_ECUDA;
+            if (st == PA_OK) st = batch_record(b, -1);
+        }
+    }
+    const cudaError_t ce = cudaStreamEndCapture(cap, &g);
+    b->stream = saved;
+    if (st == PA_OK && ce != cudaSuccess) st = PA_ECUDA;
+    if (st == PA_OK && cudaGraphInstantiate(&b->graph, g, 0) != cudaSuccess) st = PA_ECUDA;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cap);
+    if (st != PA_OK) {
+        cudaGetLastError();
+        for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
+        b->ev.clear();
+        b->ev_phase.clear();
+        b->graph = nullptr;
+    }
+    return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, pa_batch** out)
+{
+    if (!cfgs || !out || n < 1 || n > pa::kMaxBatchRuns) return PA_EINVAL;
+    *out = nullptr;
+    for (int i = 0; i < n; i++) {
+        const pa_config& c = cfgs[i];
+        PA_TRY(validate(c));
+        if (!(c.dbeta > 0.0) || c.spin_format != PA_SPIN_BITS32 || c.L > 256) return PA_EINVAL;
+        if (c.group_threads && !pa::batch_supports(c.L, c.group_threads)) return PA_EINVAL;
+    }
+    pa_batch* b = new (std::nothrow) pa_batch();
+    if (!b) return PA_ENOMEM;
+    auto fail = [&](pa_status s) {
+        batch_free(b);
+        delete b;
+        return s;
+    };
+    if (cuda_stream) {
+        b->stream = (cudaStream_t)cuda_stream;
+    } else {
+        if (cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking) != cudaSuccess) return fail(PA_ECUDA);
+        b->own_stream = true;
+    }
+    b->profile = false;
+    std::vector<RunDev> hr((size_t)n);
+    int warp_words = 0;
+    for (int i = 0; i < n; i++) {
+        pa_config c = cfgs[i];
+        if (c.profile) b->profile = true;
+        if (!c.group_threads) {
+            const pa_status ts = tune_group(c.L, b->stream, &c.group_threads);
+            if (ts != PA_OK) return fail(ts);
+        }
+        c.use_graph = 0;
+        c.profile = 0;
+        pa_ctx* m = nullptr;
+        const pa_status cs = pa_create(&c, b->stream, &m);
+        if (cs != PA_OK) return fail(cs);
+        m->in_batch = true;
+        b->runs.push_back(m);
+        hr[(size_t)i] = m->h;
+        b->max_steps = std::max(b->max_steps, (int)m->n_fixed);
+        warp_words = std::max(warp_words, (32 / m->h.gt) * m->h.words);
+    }
+    // queue order: descending work per replica (theta * N)
+    std::vector<int> order((size_t)n), tile_run, tile_first((size_t)n);
+    for (int i = 0; i < n; i++) order[(size_t)i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return (long long)hr[(size_t)x].theta * hr[(size_t)x].N > (long long)hr[(size_t)y].theta * hr[(size_t)y].N;
+    });
+    for (int i = 0; i < n; i++) {
+        tile_first[(size_t)i] = (int)tile_run.size();
+        for (int t = 0; t < hr[(size_t)i].ntiles; t++) tile_run.push_back(i);
+    }
+    auto dalloc = [&](void** p, size_t bytes) -> bool {
+        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        b->allocs.push_back(*p);
+        return true;
+    };
+    RunDev* d_runs = nullptr;
+    int *d_order = nullptr, *d_tile_run = nullptr, *d_tile_first = nullptr;
+    long long* d_off = nullptr;
+    unsigned* d_work = nullptr;
+    if (!dalloc((void**)&d_runs, sizeof(RunDev) * (size_t)n) || !dalloc((void**)&d_order, 4 * (size_t)n) ||
+        !dalloc((void**)&d_tile_run, 4 * tile_run.size()) || !dalloc((void**)&d_tile_first, 4 * (size_t)n) ||
+        !dalloc((void**)&d_off, 8 * (size_t)(n + 1)) || !dalloc((void**)&d_work, 16))
+        return fail(PA_ENOMEM);
+    if (cudaMemcpy(d_runs, hr.data(), sizeof(RunDev) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_order, order.data(), 4 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_tile_run, tile_run.data(), 4 * tile_run.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(d_tile_first, tile_first.data(), 4 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess)
+        return fail(PA_ECUDA);
+    b->bd.runs = d_runs;
+    b->bd.order = d_order;
+    b->bd.tile_run = d_tile_run;
+    b->bd.tile_first = d_tile_first;
+    b->bd.item_off = d_off;
+    b->bd.work = d_work;
+    b->bd.nruns = n;
+    b->bd.warp_words = warp_words;
+    b->ln.tiles = (int)tile_run.size();
+    if (pa::plan_batch(b->bd, &b->ln) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(PA_EINVAL);
+    }
+    *out = b;
+    return PA_OK;
+}
+
+pa_status pa_batch_launch(pa_batch* b)
+{
+    if (!b) return PA_EINVAL;
+    for (pa_ctx* c : b->runs)
+        if (c->enq_step != 0 || c->failed != PA_OK) return PA_ESTATE;
+    if (!b->graph) PA_TRY(batch_capture(b));
+    for (pa_ctx* c : b->runs) advance_fixed(c);
+    PA_CUDA(cudaGraphLaunch(b->graph, b->stream));
+    if (b->profile) b->ev_pending = true;
+    return PA_OK;
+}
+
+pa_status pa_batch_sync(pa_batch* b)
+{
+    if (!b) return PA_EINVAL;
+    PA_CUDA(cudaStreamSynchronize(b->stream));
+    PA_TRY(batch_collect(b));
+    pa_status first = PA_OK;
+    for (pa_ctx* c : b->runs) {
+        const pa_status st = pull_records(c);
+        if (st != PA_OK && first == PA_OK) first = st;
+    }
+    return first;
+}
+
+pa_status pa_batch_run(pa_batch* b)
+{
+    PA_TRY(pa_batch_launch(b));
+    return pa_batch_sync(b);
+}
+
+pa_status pa_batch_reset(pa_batch* b, const uint64_t* seeds)
+{
+    if (!b || !seeds) return PA_EINVAL;
+    PA_CUDA(cudaStreamSynchronize(b->stream));
+    PA_TRY(batch_collect(b));
+    for (size_t i = 0; i < b->runs.size(); i++) PA_TRY(reset_run(b->runs[i], seeds[i]));
+    return PA_OK;
+}
+
+pa_status pa_batch_get(pa_batch* b, int32_t i, pa_ctx** out)
+{
+    if (!b || !out || i < 0 || i >= (int32_t)b->runs.size()) return PA_EINVAL;
+    *out = b->runs[(size_t)i];
+    return PA_OK;
+}
+
+pa_status pa_batch_phase_times(pa_batch* b, double ms[7], int64_t launches[7])
+{
+    if (!b || !ms || !launches) return PA_EINVAL;
+    PA_CUDA(cudaStreamSynchronize(b->stream));
+    PA_TRY(batch_collect(b));
+    for (int p = 0; p < 7; p++) {
+        ms[p] = b->phase_ms[p];
+        launches[p] = b->phase_n[p];
+    }
+    return PA_OK;
+}
+
+pa_status pa_batch_shape(pa_batch* b, int32_t i, int32_t* group_threads, int32_t* sweep_blocks)
+{
+    if (!b || i < 0 || i >= (int32_t)b->runs.size()) return PA_EINVAL;
+    if (group_threads) *group_threads = b->runs[(size_t)i]->h.gt;
+    if (sweep_blocks) *sweep_blocks = b->ln.sweep_blocks;
+    return PA_OK;
+}
+
+void pa_batch_destroy(pa_batch* b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->stream);
+    batch_free(b);
+    delete b;
 }
 
 }  // extern "C"

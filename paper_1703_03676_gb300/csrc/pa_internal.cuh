@@ -59,6 +59,8 @@ struct RunDev {
     int ntiles;               // copy-count tiles covering cap
     int record_hist;
     int hist_steps;           // steps with a slot in hist_rec
+    int nsteps;               // last step of a fixed schedule (batched runs stop there)
+    int pad1;
     uint32_t* pop[2];
     int32_t* elev[2];
     int32_t* mlev[2];
@@ -130,6 +132,20 @@ struct ResampleArgs {
     unsigned* work;                  // persistent-kernel counter reset for the sweep (may be null)
 };
 
+// ---------------------------------------------------------------- batches
+// Many independent runs stepped together: one launch per phase for all runs.
+constexpr int kMaxBatchRuns = 1024;
+struct BatchDev {
+    const RunDev* runs;       // device array of the runs' descriptors
+    const int* order;         // runs in queue order (descending work per replica)
+    const int* tile_run;      // copy-count tile -> run
+    const int* tile_first;    // first copy-count tile of each run
+    long long* item_off;      // nruns + 1 offsets of each run's work items (queue order)
+    unsigned* work;           // queue counter of the sweep
+    int nruns;
+    int warp_words;           // shared-memory words per warp in the sweep
+};
+
 // ---------------------------------------------------------------- launches
 struct Launch {
     int sweep_blocks, sweep_threads;  // persistent sweep grid
@@ -149,6 +165,16 @@ cudaError_t launch_sweep(const RunDev* d_run, const RunDev& h, const Launch& ln,
 cudaError_t launch_stats(const RunDev* d_run, const RunDev& h, int step, cudaStream_t s);
 cudaError_t launch_rng_peak(long long blocks, uint32_t* sink, int grid, int threads, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint32_t* out, cudaStream_t s);
+
+struct BatchLaunch {
+    int tiles;                // copy-count tiles over all runs
+    int sweep_blocks;         // persistent sweep CTAs (256 threads)
+    size_t sweep_smem;
+};
+cudaError_t plan_batch(const BatchDev& b, BatchLaunch* ln);
+cudaError_t launch_batch_step(const BatchDev& b, const BatchLaunch& ln, int step, cudaStream_t s, int phase,
+                              int* phase_of_launch);
+bool batch_supports(int L, int gt);
 
 // Sweep launch shape: persistent CTAs for this run (group threads gt).
 cudaError_t plan_sweep(const RunDev& h, Launch* ln);

@@ -163,54 +163,174 @@ __device__ __forceinline__ void measure_bits(const uint32_t* sp, int gl, unsigne
     }
 }
 
+// ======================================================== replica groups
+// G threads update one replica held in shared memory. G <= 32: 32/G groups
+// per warp and the colour phases synchronise with __syncwarp. G > 32: one
+// group per CTA (blockDim == G) synchronising with __syncthreads; such a
+// kernel also needs 33 words of shared memory after the replica (reduction
+// and broadcast).
+template <int G>
+struct Group {
+    static constexpr bool kCta = G > 32;
+    static constexpr int kPerWarp = kCta ? 1 : 32 / G;
+    __device__ static __forceinline__ void sync()
+    {
+        if constexpr (kCta) __syncthreads();
+        else __syncwarp();
+    }
+    // total over the group's threads, returned to every thread
+    __device__ static __forceinline__ unsigned sum(unsigned v, unsigned* red)
+    {
+        if constexpr (kCta) {
+            v = group_sum<32>(v);
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+            __syncthreads();
+            unsigned t = 0;
+#pragma unroll
+            for (int w = 0; w < G / 32; w++) t += red[w];
+            return t;
+        } else {
+            return group_sum<G>(v);
+        }
+    }
+    // first replica index of this group's next work item (persistent loop)
+    __device__ static __forceinline__ unsigned grab(unsigned* work, unsigned* bcast)
+    {
+        if constexpr (kCta) {
+            __syncthreads();
+            if (threadIdx.x == 0) *bcast = atomicAdd(work, 1u);
+            __syncthreads();
+            return *bcast;
+        } else {
+            unsigned base = 0;
+            if ((threadIdx.x & 31) == 0) base = atomicAdd(work, (unsigned)kPerWarp);
+            return __shfl_sync(0xffffffffu, base, 0) + (threadIdx.x & 31) / G;
+        }
+    }
+    __device__ static __forceinline__ int thread_in_group()
+    {
+        return kCta ? (int)threadIdx.x : (int)(threadIdx.x & 31) % G;
+    }
+    // this group's replica buffer within the CTA's shared memory
+    __device__ static __forceinline__ uint32_t* buffer(uint32_t* smem, int words)
+    {
+        if constexpr (kCta) return smem;
+        else return smem + ((threadIdx.x >> 5) * kPerWarp + (threadIdx.x & 31) / G) * words;
+    }
+};
+
+// One temperature step of the replica in new slot k (gather of its parent,
+// theta sweeps, measurement, write-back). Every thread of the group calls
+// this, active or not (inactive groups only take part in the syncs).
+template <int L, int G>
+__device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long long k, bool active,
+                                                uint32_t* sp, int gl, unsigned* red, unsigned& families)
+{
+    using Gm = Geo<L>;
+    using Gr = Group<G>;
+    constexpr int WPT = Gm::WP / G;  // words per thread per plane
+    static_assert(Gm::WP % G == 0, "group must divide the plane");
+    const int cur = (step - 1) & 1, nxt = step & 1;
+    const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
+    const PhiloxKey key{r.key[0], r.key[1]};
+    const int theta = r.theta;
+    const unsigned u0 = (unsigned)(step - 1) * (unsigned)theta;
+    uint32_t p = 0;
+    if (active) {
+        p = r.parent[k];
+        copy_words<Gm::WORDS, G>(sp, r.pop[cur] + (size_t)p * Gm::WORDS, gl);
+    }
+    Gr::sync();
+    for (int sw = 0; sw < theta; sw++) {
+        const unsigned u = u0 + (unsigned)sw;
+#pragma unroll
+        for (int c = 0; c < 2; c++) {
+            if (active) {
+                uint32_t* P = sp + c * Gm::WP;
+                const uint32_t* O = sp + (1 - c) * Gm::WP;
+                const unsigned c2 = 2u * u + (unsigned)c;
+#pragma unroll 2
+                for (int m = 0; m < WPT; m++) {
+                    const int w = gl + m * G;
+                    uint32_t same, side, up, down;
+                    neighbours<L>(O, c, w, same, side, up, down);
+                    P[w] = metropolis_word(P[w], same, side, up, down, 8u * (unsigned)w, (unsigned)k, c2, t4m1,
+                                           t8m1, key);
+                }
+            }
+            Gr::sync();
+        }
+    }
+    unsigned anti = 0, ups = 0;
+    if (active) measure_bits<L, G>(sp, gl, anti, ups);
+    anti = Gr::sum(anti, red);
+    ups = Gr::sum(ups, red);
+    if (active) {
+        copy_words<Gm::WORDS, G>(r.pop[nxt] + (size_t)k * Gm::WORDS, sp, gl);
+        if (gl == 0) {
+            const uint32_t f = r.fam[cur][p];
+            record_replica(r, nxt, k, anti, ups, f);
+            families += (k == 0 || r.fam[cur][r.parent[k - 1]] != f) ? 1u : 0u;
+        }
+    }
+    Gr::sync();
+}
+
+// Initial spins of replica k (INIT stream: site g = c*N/2 + b, counter
+// (0, g>>2, 0, k), spin up iff x < 2^31), measured and written to pop[0].
+template <int L, int G>
+__device__ __forceinline__ void bits_group_init(const RunDev& r, long long k, bool active, uint32_t* sp, int gl,
+                                                unsigned* red)
+{
+    using Gm = Geo<L>;
+    using Gr = Group<G>;
+    const PhiloxKey key{r.key[0], r.key[1]};
+    if (active) {
+        for (int i = gl; i < Gm::WORDS; i += G) {
+            const int c = i / Gm::WP, w = i - c * Gm::WP;
+            const unsigned c0 = (unsigned)(c * (Gm::N / 8) + 8 * w);
+            uint32_t word = 0;
+#pragma unroll
+            for (int q = 0; q < 8; q++) {
+                const uint4 x = philox10(make_uint4(0u, c0 + q, kTagInit, (unsigned)k), key);
+                word |= ((x.x >> 31) ^ 1u) << (4 * q) | ((x.y >> 31) ^ 1u) << (4 * q + 1) |
+                        ((x.z >> 31) ^ 1u) << (4 * q + 2) | ((x.w >> 31) ^ 1u) << (4 * q + 3);
+            }
+            sp[i] = word;
+        }
+    }
+    Gr::sync();
+    unsigned anti = 0, ups = 0;
+    if (active) measure_bits<L, G>(sp, gl, anti, ups);
+    anti = Gr::sum(anti, red);
+    ups = Gr::sum(ups, red);
+    if (active) {
+        copy_words<Gm::WORDS, G>(r.pop[0] + (size_t)k * Gm::WORDS, sp, gl);
+        if (gl == 0) record_replica(r, 0, k, anti, ups, (uint32_t)k);
+    }
+    Gr::sync();
+}
+
 // ======================================================== bit-packed kernels
-// Persistent warps: each warp takes 32/G replicas at a time from the run's
-// work counter; G threads share one replica held in shared memory, so the
-// colour phases synchronise with __syncwarp only.
+// Persistent: each group repeatedly takes the next replica of the run's
+// work counter, so the tail of a step is at most one replica's work.
 template <int L, int G>
 __global__ void __launch_bounds__(256) k_init_bits(const __grid_constant__ RunDev r)
 {
     using Gm = Geo<L>;
-    constexpr int RPW = 32 / G;
+    using Gr = Group<G>;
     extern __shared__ uint32_t smem[];
     if (*r.status) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane / G, gl = lane % G;
-    uint32_t* sp = smem + (warp * RPW + g) * Gm::WORDS;
-    const PhiloxKey key{r.key[0], r.key[1]};
+    uint32_t* sp = Gr::buffer(smem, Gm::WORDS);
+    unsigned* red = smem + Gm::WORDS;  // CTA groups only
+    const int gl = Gr::thread_in_group();
     const long long R0 = r.R;
     for (;;) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
-        base = __shfl_sync(0xffffffffu, base, 0);
+        const unsigned first = Gr::grab(r.work, red + 32);
+        const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
         if (base >= R0) break;
-        const long long k = (long long)base + g;
-        const bool active = k < R0;
-        if (active) {
-            // INIT stream: site g = c*N/2 + b, counter (0, g>>2, 0, k), spin up iff x < 2^31
-            for (int i = gl; i < Gm::WORDS; i += G) {
-                const int c = i / Gm::WP, w = i - c * Gm::WP;
-                const unsigned c0 = (unsigned)(c * (Gm::N / 8) + 8 * w);
-                uint32_t word = 0;
-#pragma unroll
-                for (int q = 0; q < 8; q++) {
-                    const uint4 x = philox10(make_uint4(0u, c0 + q, kTagInit, (unsigned)k), key);
-                    word |= ((x.x >> 31) ^ 1u) << (4 * q) | ((x.y >> 31) ^ 1u) << (4 * q + 1) |
-                            ((x.z >> 31) ^ 1u) << (4 * q + 2) | ((x.w >> 31) ^ 1u) << (4 * q + 3);
-                }
-                sp[i] = word;
-            }
-        }
-        __syncwarp();
-        unsigned anti = 0, ups = 0;
-        if (active) measure_bits<L, G>(sp, gl, anti, ups);
-        anti = group_sum<G>(anti);
-        ups = group_sum<G>(ups);
-        if (active) {
-            copy_words<Gm::WORDS, G>(r.pop[0] + (size_t)k * Gm::WORDS, sp, gl);
-            if (gl == 0) record_replica(r, 0, k, anti, ups, (uint32_t)k);
-        }
-        __syncwarp();
+        bits_group_init<L, G>(r, (long long)first, first < R0, sp, gl, red);
     }
 }
 
@@ -218,70 +338,22 @@ template <int L, int G>
 __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunDev r, int step)
 {
     using Gm = Geo<L>;
-    constexpr int RPW = 32 / G;
-    constexpr int WPT = Gm::WP / G;  // words per thread per plane
-    static_assert(Gm::WP % G == 0, "group must divide the plane");
+    using Gr = Group<G>;
     extern __shared__ uint32_t smem[];
     if (*r.status) return;
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int g = lane / G, gl = lane % G;
-    uint32_t* sp = smem + (warp * RPW + g) * Gm::WORDS;
-    const int cur = (step - 1) & 1, nxt = step & 1;
+    uint32_t* sp = Gr::buffer(smem, Gm::WORDS);
+    unsigned* red = smem + Gm::WORDS;  // CTA groups only
+    const int gl = Gr::thread_in_group();
     const long long Ri = r.rec[step].R;
-    const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
-    const PhiloxKey key{r.key[0], r.key[1]};
-    const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
-    const int theta = r.theta;
     unsigned families = 0;
     for (;;) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
-        base = __shfl_sync(0xffffffffu, base, 0);
+        const unsigned first = Gr::grab(r.work, red + 32);
+        const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
         if (base >= Ri) break;
-        const long long k = (long long)base + g;
-        const bool active = k < Ri;
-        uint32_t p = 0;
-        if (active) {
-            p = r.parent[k];
-            copy_words<Gm::WORDS, G>(sp, r.pop[cur] + (size_t)p * Gm::WORDS, gl);
-        }
-        __syncwarp();
-        for (int sw = 0; sw < theta; sw++) {
-            const unsigned u = u0 + (unsigned)sw;
-#pragma unroll
-            for (int c = 0; c < 2; c++) {
-                if (active) {
-                    uint32_t* P = sp + c * Gm::WP;
-                    const uint32_t* O = sp + (1 - c) * Gm::WP;
-                    const unsigned c2 = 2u * u + (unsigned)c;
-#pragma unroll 2
-                    for (int m = 0; m < WPT; m++) {
-                        const int w = gl + m * G;
-                        uint32_t same, side, up, down;
-                        neighbours<L>(O, c, w, same, side, up, down);
-                        P[w] = metropolis_word(P[w], same, side, up, down, 8u * (unsigned)w, (unsigned)k, c2,
-                                               t4m1, t8m1, key);
-                    }
-                }
-                __syncwarp();
-            }
-        }
-        unsigned anti = 0, ups = 0;
-        if (active) measure_bits<L, G>(sp, gl, anti, ups);
-        anti = group_sum<G>(anti);
-        ups = group_sum<G>(ups);
-        if (active) {
-            copy_words<Gm::WORDS, G>(r.pop[nxt] + (size_t)k * Gm::WORDS, sp, gl);
-            if (gl == 0) {
-                const uint32_t f = r.fam[cur][p];
-                record_replica(r, nxt, k, anti, ups, f);
-                families += (k == 0 || r.fam[cur][r.parent[k - 1]] != f) ? 1u : 0u;
-            }
-        }
-        __syncwarp();
+        bits_group_step<L, G>(r, step, (long long)first, first < Ri, sp, gl, red, families);
     }
     families = group_sum<32>(families);
-    if (lane == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
+    if ((threadIdx.x & 31) == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
 }
 
 // ======================================================== byte-spin kernels
@@ -452,10 +524,9 @@ __device__ __forceinline__ int pad_pow2(int n)
 // elsewhere) padded to a power of two, then the copy tables over [kmin, kmax].
 // Thread t sums the aligned block [t*chunk, (t+1)*chunk) with a carry stack
 // (the block's subtree), then a shared-memory tree joins neighbours.
-__global__ void __launch_bounds__(kOneCta) k_tables(const __grid_constant__ RunDev r, int step)
+__device__ __forceinline__ void tables_body(const RunDev& r, int step)
 {
     __shared__ double s[kOneCta];
-    if (*r.status) return;
     const int t = threadIdx.x;
     const StepDev& prev = r.rec[step - 1];
     const int kmin = prev.kmin, kmax = prev.kmax;
@@ -507,6 +578,19 @@ __global__ void __launch_bounds__(kOneCta) k_tables(const __grid_constant__ RunD
     }
 }
 
+__global__ void __launch_bounds__(kOneCta) k_tables(const __grid_constant__ RunDev r, int step)
+{
+    if (*r.status) return;
+    tables_body(r, step);
+}
+
+__global__ void __launch_bounds__(kOneCta) k_tables_batch(const __grid_constant__ BatchDev b, int step)
+{
+    const RunDev& r = b.runs[blockIdx.x];
+    if (*r.status || step > r.nsteps) return;
+    tables_body(r, step);
+}
+
 // Copy numbers of the old population (Eq. resampling-factors): one Philox
 // block serves 4 consecutive old slots j (RESAMPLE stream (i, j>>2, 2, 0)).
 __device__ __forceinline__ long long n_old_of(const ResampleArgs& a)
@@ -514,12 +598,11 @@ __device__ __forceinline__ long long n_old_of(const ResampleArgs& a)
     return a.n_old_dev ? *a.n_old_dev : a.n_old;
 }
 
-__global__ void __launch_bounds__(kTileThreads) k_counts(const __grid_constant__ ResampleArgs a)
+__device__ __forceinline__ void counts_body(const ResampleArgs& a, int tile)
 {
     __shared__ uint32_t wsum[kTileThreads / 32];
-    if (*a.status) return;
     const long long Rp = n_old_of(a);
-    const long long tile0 = (long long)blockIdx.x * kTile;
+    const long long tile0 = (long long)tile * kTile;
     if (tile0 >= Rp) return;
     const long long j0 = tile0 + 4 * threadIdx.x;
     uint32_t c[4] = {0u, 0u, 0u, 0u};
@@ -562,15 +645,20 @@ __global__ void __launch_bounds__(kTileThreads) k_counts(const __grid_constant__
     if (threadIdx.x == kTileThreads - 1) {
         uint32_t tot = 0;
         for (int w = 0; w < kTileThreads / 32; w++) tot += wsum[w];
-        a.tile_sum[blockIdx.x] = tot;
+        a.tile_sum[tile] = tot;
     }
 }
 
+__global__ void __launch_bounds__(kTileThreads) k_counts(const __grid_constant__ ResampleArgs a)
+{
+    if (*a.status) return;
+    counts_body(a, blockIdx.x);
+}
+
 // Exclusive scan of the tile totals; R_i and the capacity check.
-__global__ void __launch_bounds__(kOneCta) k_scan(const __grid_constant__ ResampleArgs a)
+__device__ __forceinline__ void scan_body(const ResampleArgs& a)
 {
     __shared__ unsigned long long part[kOneCta];
-    if (*a.status) return;
     const int t = threadIdx.x;
     const long long Rp = n_old_of(a);
     const int ntiles = (int)((Rp + kTile - 1) / kTile);
@@ -602,16 +690,74 @@ __global__ void __launch_bounds__(kOneCta) k_scan(const __grid_constant__ Resamp
     }
 }
 
+__global__ void __launch_bounds__(kOneCta) k_scan(const __grid_constant__ ResampleArgs a)
+{
+    if (*a.status) return;
+    scan_body(a);
+}
+
 // parent[o_j + c] = j for c < r_j: new slots keep the order of old slots.
+__device__ __forceinline__ void parent_body(const ResampleArgs& a, int tile)
+{
+    const long long Rp = n_old_of(a);
+    const long long j = (long long)tile * kTile + threadIdx.x;
+    if (j >= Rp) return;
+    const uint32_t n = a.cnt[j];
+    const uint32_t o = a.tile_off[tile] + a.loc[j];
+    for (uint32_t c = 0; c < n; c++) a.parent[o + c] = (uint32_t)j;
+}
+
 __global__ void __launch_bounds__(kTile) k_parent(const __grid_constant__ ResampleArgs a)
 {
     if (*a.status) return;
-    const long long Rp = n_old_of(a);
-    const long long j = (long long)blockIdx.x * kTile + threadIdx.x;
-    if (j >= Rp) return;
-    const uint32_t n = a.cnt[j];
-    const uint32_t o = a.tile_off[blockIdx.x] + a.loc[j];
-    for (uint32_t c = 0; c < n; c++) a.parent[o + c] = (uint32_t)j;
+    parent_body(a, blockIdx.x);
+}
+
+// Resampling arguments of step `step` of a run (its records hold R_{i-1}).
+__host__ __device__ __forceinline__ ResampleArgs resample_args(const RunDev& h, int step)
+{
+    ResampleArgs a{};
+    a.n_old_dev = &h.rec[step - 1].R;
+    a.n_old = 0;
+    a.lev = h.elev[(step - 1) & 1];
+    a.F = h.F;
+    a.U = h.U;
+    a.key = h.key;
+    a.step = (unsigned)step;
+    a.cnt = h.cnt;
+    a.loc = h.loc;
+    a.tile_sum = h.tile_sum;
+    a.tile_off = h.tile_off;
+    a.parent = h.parent;
+    a.cap = h.cap;
+    a.n_new = &h.rec[step].R;
+    a.n_prev_out = &h.rec[step].R_prev;
+    a.status = h.status;
+    a.work = h.work;
+    return a;
+}
+
+__global__ void __launch_bounds__(kTileThreads) k_counts_batch(const __grid_constant__ BatchDev b, int step)
+{
+    const int run = b.tile_run[blockIdx.x];
+    const RunDev& r = b.runs[run];
+    if (*r.status || step > r.nsteps) return;
+    counts_body(resample_args(r, step), blockIdx.x - b.tile_first[run]);
+}
+
+__global__ void __launch_bounds__(kOneCta) k_scan_batch(const __grid_constant__ BatchDev b, int step)
+{
+    const RunDev& r = b.runs[blockIdx.x];
+    if (*r.status || step > r.nsteps) return;
+    scan_body(resample_args(r, step));
+}
+
+__global__ void __launch_bounds__(kTile) k_parent_batch(const __grid_constant__ BatchDev b, int step)
+{
+    const int run = b.tile_run[blockIdx.x];
+    const RunDev& r = b.runs[run];
+    if (*r.status || step > r.nsteps) return;
+    parent_body(resample_args(r, step), blockIdx.x - b.tile_first[run]);
 }
 
 // ======================================================== statistics
@@ -639,11 +785,10 @@ __device__ __forceinline__ __int128 warp_sum128(__int128 v)
 
 // Integer moments of population i from its histograms (exact: every sum is
 // an integer, so no order matters), occupied range, running sum for MHR.
-__global__ void __launch_bounds__(kOneCta) k_stats(const __grid_constant__ RunDev r, int step)
+__device__ __forceinline__ void stats_body(const RunDev& r, int step)
 {
     __shared__ __int128 ws[5][kOneCta / 32];
     __shared__ int wmin[kOneCta / 32], wmax[kOneCta / 32];
-    if (*r.status) return;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     const int N = r.N;
     const uint32_t* HE = r.H[step & 1];
@@ -720,6 +865,87 @@ __global__ void __launch_bounds__(kOneCta) k_stats(const __grid_constant__ RunDe
     }
 }
 
+__global__ void __launch_bounds__(kOneCta) k_stats(const __grid_constant__ RunDev r, int step)
+{
+    if (*r.status) return;
+    stats_body(r, step);
+}
+
+__global__ void __launch_bounds__(kOneCta) k_stats_batch(const __grid_constant__ BatchDev b, int step)
+{
+    const RunDev& r = b.runs[blockIdx.x];
+    if (*r.status || step > r.nsteps) return;
+    stats_body(r, step);
+}
+
+// ======================================================== batched sweep
+// Work items of step `step`: ceil(R_i / (replicas per warp)) per live run,
+// laid out in queue order; the sweep's warps take items from one counter.
+__global__ void k_plan(const __grid_constant__ BatchDev b, int step)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    long long acc = 0;
+    for (int q = 0; q < b.nruns; q++) {
+        b.item_off[q] = acc;
+        const RunDev& r = b.runs[b.order[q]];
+        if (*r.status == 0 && step <= r.nsteps) {
+            const int per = 32 / r.gt;
+            acc += (r.rec[step].R + per - 1) / per;
+        }
+    }
+    b.item_off[b.nruns] = acc;
+    *b.work = 0u;
+}
+
+template <int L, int G>
+__device__ __forceinline__ void batch_item(const RunDev& r, int step, long long item, uint32_t* wsm)
+{
+    using Gm = Geo<L>;
+    using Gr = Group<G>;
+    static_assert(!Gr::kCta, "batched sweeps use warp groups");
+    const int lane = threadIdx.x & 31, g = lane / G;
+    const long long k = item * Gr::kPerWarp + g;
+    unsigned fam = 0;
+    bits_group_step<L, G>(r, step, k, k < r.rec[step].R, wsm + g * Gm::WORDS, lane % G, nullptr, fam);
+    fam = group_sum<32>(fam);
+    if (lane == 0 && fam) atomicAdd(&r.rec[step].fam, (unsigned long long)fam);
+}
+
+// (L, G) pairs a batched sweep can run: warp groups dividing the plane
+#define PA_BATCH_SHAPES(X) X(8, 1) X(16, 2) X(16, 4) X(32, 8) X(32, 16) X(64, 16) X(64, 32) X(128, 32) X(256, 32)
+
+__global__ void __launch_bounds__(256) k_sweep_batch(const __grid_constant__ BatchDev b, int step)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ long long s_off[kMaxBatchRuns + 1];
+    for (int i = threadIdx.x; i <= b.nruns; i += blockDim.x) s_off[i] = b.item_off[i];
+    __syncthreads();
+    const long long total = s_off[b.nruns];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* wsm = smem + warp * b.warp_words;
+    for (;;) {
+        unsigned it = 0;
+        if (lane == 0) it = atomicAdd(b.work, 1u);
+        it = __shfl_sync(0xffffffffu, it, 0);
+        if ((long long)it >= total) break;
+        int lo = 0, hi = b.nruns;  // largest q with s_off[q] <= it
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (s_off[mid] <= (long long)it) lo = mid;
+            else hi = mid;
+        }
+        const RunDev& r = b.runs[b.order[lo]];
+        const long long item = (long long)it - s_off[lo];
+        switch (r.L * 64 + r.gt) {
+#define PA_BATCH_CASE(LL, GG) \
+    case LL * 64 + GG: batch_item<LL, GG>(r, step, item, wsm); break;
+            PA_BATCH_SHAPES(PA_BATCH_CASE)
+#undef PA_BATCH_CASE
+        default: break;
+        }
+    }
+}
+
 // ======================================================== Philox test kernel
 __global__ void k_philox(const uint32_t* __restrict__ ctr, long long n, PhiloxKey key, uint32_t* __restrict__ out)
 {
@@ -766,6 +992,7 @@ const void* bits_ptr_L(int gt, bool init)
     case 8: if constexpr (WP % 8 == 0) return bits_ptr<L, 8>(init); break;
     case 16: if constexpr (WP % 16 == 0) return bits_ptr<L, 16>(init); break;
     case 32: if constexpr (WP % 32 == 0) return bits_ptr<L, 32>(init); break;
+    case 256: if constexpr (WP % 256 == 0) return bits_ptr<L, 256>(init); break;
     default: break;
     }
     return nullptr;
@@ -817,13 +1044,21 @@ cudaError_t plan_sweep(const RunDev& h, Launch* ln)
     const void* kin = sweep_kernel(h, true);
     const void* ksw = sweep_kernel(h, false);
     if (!kin || !ksw) return cudaErrorInvalidConfiguration;
-    // CTA of up to 8 warps; fewer when one warp's replicas need much shared memory
-    const size_t per_warp = (size_t)(32 / h.gt) * (size_t)h.words * 4u;
-    int warps = 8;
-    while (warps > 1 && per_warp * warps > (size_t)max_optin) warps >>= 1;
-    const size_t smem = per_warp * warps;
+    size_t smem;
+    int threads;
+    if (h.gt > 32) {
+        // one replica per CTA of gt threads, plus reduction/broadcast words
+        threads = h.gt;
+        smem = ((size_t)h.words + 33) * 4u;
+    } else {
+        // CTA of up to 8 warps; fewer when one warp's replicas need much shared memory
+        const size_t per_warp = (size_t)(32 / h.gt) * (size_t)h.words * 4u;
+        int warps = 8;
+        while (warps > 1 && per_warp * warps > (size_t)max_optin) warps >>= 1;
+        smem = per_warp * warps;
+        threads = 32 * warps;
+    }
     if (smem > (size_t)max_optin) return cudaErrorInvalidConfiguration;
-    const int threads = 32 * warps;
     for (const void* k : {kin, ksw}) {
         if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess)
             return e;
@@ -861,29 +1096,6 @@ cudaError_t launch_tables(const RunDev* /*d_run*/, const RunDev& h, int step, cu
 {
     k_tables<<<1, kOneCta, 0, s>>>(h, step);
     return cudaGetLastError();
-}
-
-static ResampleArgs resample_args(const RunDev& h, int step)
-{
-    ResampleArgs a{};
-    a.n_old_dev = &h.rec[step - 1].R;
-    a.n_old = 0;
-    a.lev = h.elev[(step - 1) & 1];
-    a.F = h.F;
-    a.U = h.U;
-    a.key = h.key;
-    a.step = (unsigned)step;
-    a.cnt = h.cnt;
-    a.loc = h.loc;
-    a.tile_sum = h.tile_sum;
-    a.tile_off = h.tile_off;
-    a.parent = h.parent;
-    a.cap = h.cap;
-    a.n_new = &h.rec[step].R;
-    a.n_prev_out = &h.rec[step].R_prev;
-    a.status = h.status;
-    a.work = h.work;
-    return a;
 }
 
 cudaError_t launch_counts(const RunDev* /*d_run*/, const RunDev& h, const Launch& ln, int step, cudaStream_t s)
@@ -928,6 +1140,57 @@ cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint3
     const int threads = 256;
     const long long blocks = (n + threads - 1) / threads;
     k_philox<<<(unsigned)blocks, threads, 0, s>>>(ctr, n, key, out);
+    return cudaGetLastError();
+}
+
+bool batch_supports(int L, int gt)
+{
+    switch (L * 64 + gt) {
+#define PA_BATCH_OK(LL, GG) case LL * 64 + GG:
+        PA_BATCH_SHAPES(PA_BATCH_OK)
+#undef PA_BATCH_OK
+        return true;
+    default: return false;
+    }
+}
+
+cudaError_t plan_batch(const BatchDev& b, BatchLaunch* ln)
+{
+    int dev = 0, sms = 0, max_optin = 0, per_sm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
+    const size_t smem = (size_t)8 * b.warp_words * 4;
+    if (smem + (kMaxBatchRuns + 1) * 8 > (size_t)max_optin) return cudaErrorInvalidConfiguration;
+    if ((e = cudaFuncSetAttribute((const void*)k_sweep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+        cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_batch, 256, smem)) != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    ln->sweep_blocks = sms * per_sm;
+    ln->sweep_smem = smem;
+    return cudaSuccess;
+}
+
+// One phase of a batched step: 0 tables, 1 counts, 2 scan, 3 parent, 4 plan +
+// sweep, 5 stats (the phase numbers of pa_phase_times).
+cudaError_t launch_batch_step(const BatchDev& b, const BatchLaunch& ln, int step, cudaStream_t s, int phase,
+                              int* /*unused*/)
+{
+    switch (phase) {
+    case 0: k_tables_batch<<<b.nruns, kOneCta, 0, s>>>(b, step); break;
+    case 1: k_counts_batch<<<ln.tiles, kTileThreads, 0, s>>>(b, step); break;
+    case 2: k_scan_batch<<<b.nruns, kOneCta, 0, s>>>(b, step); break;
+    case 3: k_parent_batch<<<ln.tiles, kTile, 0, s>>>(b, step); break;
+    case 4:
+        k_plan<<<1, 32, 0, s>>>(b, step);
+        if (cudaPeekAtLastError() != cudaSuccess) break;
+        k_sweep_batch<<<ln.sweep_blocks, 256, ln.sweep_smem, s>>>(b, step);
+        break;
+    case 5: k_stats_batch<<<b.nruns, kOneCta, 0, s>>>(b, step); break;
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

@@ -58,6 +58,12 @@ CASES = [
     ("L10-int8", 10, 1100, 2, 0.4, 0.1, 15, I8),
 ]
 
+CTA_CASES = [
+    # one replica per 256-thread CTA (CTA-wide barriers between colour phases)
+    ("L128-cta", 128, 300, 2, 0.3, 0.1, 10),
+    ("L256-cta", 256, 40, 1, 0.5, 0.25, 16),
+]
+
 
 @pytest.mark.parametrize("name,L,R,theta,beta_f,dbeta,seed,fmt", CASES, ids=[c[0] for c in CASES])
 def test_run_parity(name, L, R, theta, beta_f, dbeta, seed, fmt):
@@ -76,6 +82,21 @@ def test_run_parity(name, L, R, theta, beta_f, dbeta, seed, fmt):
     np.testing.assert_array_equal(M, pa.M)
     np.testing.assert_array_equal(fam, pa.fam)
     np.testing.assert_array_equal(run.histogram(0, 2), pa.Hsum)
+    run.close()
+
+
+@pytest.mark.parametrize("name,L,R,theta,beta_f,dbeta,seed", CTA_CASES, ids=[c[0] for c in CTA_CASES])
+def test_cta_group_parity(name, L, R, theta, beta_f, dbeta, seed):
+    pa = oracle_run(L, R, theta, beta_f, dbeta, seed)
+    pa.run()
+    run = engine_run(L, R, theta, beta_f, dbeta, seed, B32, group_threads=256)
+    assert run.launch_shape()["group_threads"] == 256
+    run.run()
+    rows = run.rows()
+    for i, ref in enumerate(pa.rows):
+        assert_row_close(rows[i], ref, f"{name} row {i}")
+        compare_step(run, pa, i)
+    np.testing.assert_array_equal(run.population(), pa.pop)
     run.close()
 
 
