@@ -38,6 +38,7 @@ typedef struct pa_ctx pa_ctx;
 typedef enum {
     PA_OK = 0,
     PA_DONE = 1,          /* pa_step: beta_f already reached, nothing done      */
+    PA_EAGAIN = 2,        /* pa_step_async: the previous step is still running  */
     PA_EINVAL = -1,       /* invalid argument or configuration                  */
     PA_ENOMEM = -2,       /* device or host allocation failed                   */
     PA_ECAPACITY = -3,    /* R_i exceeded the population capacity               */
@@ -110,6 +111,13 @@ pa_status pa_create(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
  * (capacity, extinction) are reported by this call or the next one that
  * synchronises. */
 pa_status pa_step(pa_ctx *ctx);
+
+/* Non-blocking pa_step: enqueues the next step and returns PA_OK, or
+ * PA_EAGAIN without doing anything if an adaptive run still waits for the
+ * previous step's histogram (it streams to pinned host memory as soon as the
+ * step ends), or PA_DONE once the last step is enqueued. Fixed steps never
+ * return PA_EAGAIN. */
+pa_status pa_step_async(pa_ctx *ctx);
 
 /* Steps until beta_f and synchronises. With use_graph the remaining fixed
  * schedule runs as one CUDA-graph launch. */
@@ -219,6 +227,48 @@ pa_status pa_batch_phase_times(pa_batch *b, double ms[7], int64_t launches[7]);
 /* Threads per replica used for run i and the persistent sweep grid size. */
 pa_status pa_batch_shape(pa_batch *b, int32_t i, int32_t *group_threads, int32_t *sweep_blocks);
 void pa_batch_destroy(pa_batch *b);
+
+/* ---- serving ------------------------------------------------------------
+ * A request loop with continuous batching (spec serving): requests
+ * arrive at given times; each is admitted, in arrival order, once it has
+ * arrived, fewer than max_active runs are resident and the sum of the
+ * resident runs' pa_footprint_bytes stays within hbm_budget (a request
+ * larger than the whole budget is admitted alone). Every admitted run gets
+ * its own stream and stays resident on the device until it finishes; the
+ * loop advances each run with pa_step_async, so the kernels of different
+ * runs overlap on the GPU while others wait for their host-side step
+ * decision, and a finished run frees its memory for the next request.
+ * Results are those of each request run alone. */
+typedef struct {
+    double arrival_s;       /* seconds after the loop starts                     */
+    pa_config cfg;
+} pa_request;
+
+typedef struct {
+    double admit_s;         /* seconds after the start: admitted (created)       */
+    double finish_s;        /* all steps done and rows available                 */
+    double attempts;        /* L^2 theta sum_{i>=1} R_i                          */
+    int64_t steps;          /* temperature steps taken                           */
+    int64_t footprint;      /* device bytes of the run                           */
+    int32_t status;         /* pa_status of the run (PA_OK on success)           */
+    int32_t pad;
+} pa_request_result;
+
+typedef struct {
+    uint64_t hbm_budget;    /* bytes of resident runs, 0: no limit               */
+    int32_t max_active;     /* resident runs at once, >= 1                       */
+    int32_t keep;           /* != 0: return the finished contexts in out_ctx
+                               (their memory stays allocated; the caller
+                               destroys them) instead of destroying them        */
+    double time_scale;      /* multiplies every arrival time (> 0)               */
+} pa_serve_options;
+
+/* Serve n requests sorted by arrival time; returns when all are finished.
+ * out[n] (host) gets per-request times and status; out_ctx[n] (host, only
+ * with keep) the contexts. Returns PA_OK even if some requests failed (see
+ * out[i].status); PA_EINVAL on bad arguments. */
+pa_status pa_serve(const pa_request *reqs, int32_t n, const pa_serve_options *opt, pa_request_result *out,
+                   pa_ctx **out_ctx);
 
 /* ---- kernel-level entry points (device pointers, for tests) ----------- */
 

@@ -21,7 +21,7 @@ __all__ = ["PAConfig", "PARun", "PAError", "lib", "philox_device", "footprint_by
 SPIN_INT8, SPIN_BITS32 = 0, 1
 HIST_E, HIST_M, HIST_ESUM = 0, 1, 2
 
-_STATUS = {0: "ok", 1: "done", -1: "invalid argument", -2: "out of memory", -3: "capacity",
+_STATUS = {0: "ok", 1: "done", 2: "again", -1: "invalid argument", -2: "out of memory", -3: "capacity",
            -4: "extinct", -5: "timeout", -6: "cuda error", -7: "invalid state", -8: "stalled"}
 
 
@@ -101,6 +101,8 @@ SIGNATURES = [
     ("pa_batch_shape", ctypes.c_int, [_P, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32),
                                       ctypes.POINTER(ctypes.c_int32)]),
     ("pa_batch_destroy", None, [_P]),
+    ("pa_step_async", ctypes.c_int, [_P]),
+    ("pa_serve", ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     ("pa_measure_rng_peak", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     ("pa_resample", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64, _P,
                                    ctypes.c_int64, _I64P, _P]),
@@ -219,6 +221,12 @@ class PARun:
         _check(self._lib.pa_run(self._h), "pa_run")
         return self
 
+    def step_async(self) -> int:
+        """Non-blocking step: 0 enqueued, 1 done, 2 previous step still running."""
+        st = self._lib.pa_step_async(self._h)
+        _check(st, "pa_step_async", ok=(0, 1, 2))
+        return st
+
     def launch(self):
         """Enqueue the rest of the schedule without waiting."""
         _check(self._lib.pa_launch(self._h), "pa_launch")
@@ -312,6 +320,69 @@ class PARun:
         _check(self._lib.pa_launch_shape(self._h, ctypes.byref(g), ctypes.byref(b), ctypes.byref(n)),
                "pa_launch_shape")
         return {"group_threads": g.value, "block_threads": b.value, "grid_blocks": n.value}
+
+
+class _Request(ctypes.Structure):
+    _fields_ = [("arrival_s", ctypes.c_double), ("cfg", _Config)]
+
+
+class _RequestResult(ctypes.Structure):
+    _fields_ = [("admit_s", ctypes.c_double), ("finish_s", ctypes.c_double), ("attempts", ctypes.c_double),
+                ("steps", ctypes.c_int64), ("footprint", ctypes.c_int64), ("status", ctypes.c_int32),
+                ("pad", ctypes.c_int32)]
+
+
+class _ServeOptions(ctypes.Structure):
+    _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_active", ctypes.c_int32), ("keep", ctypes.c_int32),
+                ("time_scale", ctypes.c_double)]
+
+
+def serve(requests, hbm_budget: int = 0, max_active: int = 8, time_scale: float = 1.0, keep: bool = False):
+    """Run the native request loop (pa_serve) on [(arrival_s, PAConfig)]
+    sorted by arrival. Returns (results, runs): results is a list of dicts
+    (admit_s, finish_s, attempts, steps, footprint, status); runs holds the
+    finished runs as PARun objects when keep is set."""
+    n = len(requests)
+    reqs = (_Request * max(n, 1))()
+    for i, (t, c) in enumerate(requests):
+        reqs[i].arrival_s = float(t)
+        reqs[i].cfg = c._c()
+    res = (_RequestResult * max(n, 1))()
+    ctxs = (_P * max(n, 1))()
+    opt = _ServeOptions(int(hbm_budget), int(max_active), int(bool(keep)), float(time_scale))
+    _check(lib().pa_serve(reqs, n, ctypes.byref(opt), res, ctxs if keep else None), "pa_serve")
+    out = [{f: getattr(res[i], f) for f, _ in _RequestResult._fields_ if f != "pad"} for i in range(n)]
+    runs = []
+    if keep:
+        for i, (t, c) in enumerate(requests):
+            if ctxs[i]:
+                r = PARun.__new__(PARun)
+                r.cfg, r._lib, r._h, r.N = c, lib(), ctypes.c_void_p(ctxs[i]), c.L * c.L
+                runs.append(r)
+            else:
+                runs.append(None)
+    return out, runs
+
+
+def served_trace(n: int = 500, rate: float = 20.0, seed: int = 999, stream=None):
+    """The served-PA request trace: request q draws Philox4x32-10 (key =
+    seed) at counter (0, q, 4, 0): the gap to the previous arrival is
+    -ln(1 - w0 2^-32)/rate seconds, L = {32, 64, 128, 256, 512}[w1 mod 5],
+    R = 10000 + w2 mod 90001 (uniform in 10^4..10^5); seed 1000 + q.
+    Returns [(arrival_s, L, R, seed)]. Uses the engine's device Philox."""
+    import math
+
+    import torch
+    ctr = torch.zeros((n, 4), dtype=torch.int32)
+    ctr[:, 1] = torch.arange(n, dtype=torch.int32)
+    ctr[:, 2] = 4
+    w = philox_device(ctr.cuda(), seed, stream).cpu().numpy().view(np.uint32).astype(np.int64)
+    t = 0.0
+    out = []
+    for q in range(n):
+        t += -math.log(1.0 - float(w[q, 0]) / 4294967296.0) / rate
+        out.append((t, [32, 64, 128, 256, 512][w[q, 1] % 5], 10000 + int(w[q, 2] % 90001), 1000 + q))
+    return out
 
 
 class _BorrowedRun(PARun):

@@ -18,7 +18,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
+#include <chrono>
 #include <cstring>
+#include <thread>
 #include <map>
 #include <mutex>
 #include <new>
@@ -96,6 +98,10 @@ struct pa_ctx {
     std::vector<void*> allocs;
     void* h_stage = nullptr;      // pinned staging for adaptive uploads
     size_t h_stage_bytes = 0;
+    // adaptive runs: record, status and energy histogram of the last enqueued
+    // step stream into pinned memory; ev_ready marks their arrival
+    void* h_down = nullptr;
+    cudaEvent_t ev_ready = nullptr;
     unsigned* d_key = nullptr;    // Philox key in device memory
     cudaGraphExec_t graph = nullptr;  // steps 1..n of the fixed schedule
     bool capturing = false;
@@ -362,7 +368,9 @@ double overlap_alpha(const std::vector<long long>& H, int kmin, int kmax, long l
     return acc / (double)Rprev;
 }
 
-pa_status enqueue_step(pa_ctx* c)
+pa_status enqueue_readback(pa_ctx* c);
+
+pa_status enqueue_step(pa_ctx* c, bool wait = true)
 {
     if (c->done) return PA_DONE;
     const long long i = c->enq_step + 1;
@@ -374,16 +382,25 @@ pa_status enqueue_step(pa_ctx* c)
         beta = 0.0 + (double)i * c->cfg.dbeta;
         final_step = (i == c->n_fixed);
     } else {
-        // read population i-1: its record and the occupied histogram range
-        PA_TRY(pull_records(c));
-        const StepDev& pr = c->recs[(size_t)(i - 1)];
+        // population i-1: its record, status and histogram (staged readback)
+        if (wait) {
+            PA_CUDA(cudaEventSynchronize(c->ev_ready));
+        } else {
+            const cudaError_t q = cudaEventQuery(c->ev_ready);
+            if (q == cudaErrorNotReady) return PA_EAGAIN;
+            if (q != cudaSuccess) return from_cuda(q, __LINE__);
+        }
+        const StepDev& pr = *(const StepDev*)c->h_down;
+        const int dstatus = *(const int*)((const char*)c->h_down + sizeof(StepDev));
+        if (dstatus != 0) {
+            c->failed = (pa_status)dstatus;
+            return c->failed;
+        }
+        const uint32_t* hr = (const uint32_t*)((const char*)c->h_down + sizeof(StepDev) + 16);
         const int kmin = pr.kmin, kmax = pr.kmax;
         const int nl = kmax - kmin + 1;
-        std::vector<uint32_t> hr((size_t)nl);
-        PA_CUDA(cudaMemcpy(hr.data(), c->h.H[(i - 1) & 1] + kmin, sizeof(uint32_t) * (size_t)nl,
-                           cudaMemcpyDeviceToHost));
         std::vector<long long> H((size_t)c->N + 1, 0);
-        for (int k = 0; k < nl; k++) H[(size_t)(kmin + k)] = hr[(size_t)k];
+        for (int k = kmin; k <= kmax; k++) H[(size_t)k] = hr[(size_t)k];
         const long long P = pad_pow2(c->N + 1);
         const double bprev = c->betas[(size_t)(i - 1)];
         const double dmax = c->cfg.beta_f - bprev;
@@ -425,6 +442,21 @@ pa_status enqueue_step(pa_ctx* c)
     c->deltas.push_back(delta);
     c->enq_step = i;
     if (final_step) c->done = true;
+    if (c->adaptive && !final_step) PA_TRY(enqueue_readback(c));
+    return PA_OK;
+}
+
+// Adaptive runs: stage what the next step decision needs.
+pa_status enqueue_readback(pa_ctx* c)
+{
+    if (!c->adaptive) return PA_OK;
+    const long long i = c->enq_step;
+    char* d = (char*)c->h_down;
+    PA_CUDA(cudaMemcpyAsync(d, c->h.rec + i, sizeof(StepDev), cudaMemcpyDeviceToHost, c->stream));
+    PA_CUDA(cudaMemcpyAsync(d + sizeof(StepDev), c->h.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+    PA_CUDA(cudaMemcpyAsync(d + sizeof(StepDev) + 16, c->h.H[i & 1], sizeof(uint32_t) * ((size_t)c->N + 1),
+                            cudaMemcpyDeviceToHost, c->stream));
+    PA_CUDA(cudaEventRecord(c->ev_ready, c->stream));
     return PA_OK;
 }
 
@@ -506,7 +538,7 @@ pa_status reset_run(pa_ctx* c, uint64_t seed)
     PA_TRY(prof_begin(c, 5, &ev));
     PA_CUDA(pa::launch_stats(nullptr, h, 0, c->stream));
     PA_TRY(prof_end(c));
-    return PA_OK;
+    return enqueue_readback(c);
 }
 
 // Enqueue the remaining schedule without waiting. A fixed schedule started
@@ -573,6 +605,8 @@ pa_status free_all(pa_ctx* c)
     for (cudaEvent_t e : c->gev) cudaEventDestroy(e);
     for (void* p : c->allocs) cudaFree(p);
     if (c->h_stage) cudaFreeHost(c->h_stage);
+    if (c->h_down) cudaFreeHost(c->h_down);
+    if (c->ev_ready) cudaEventDestroy(c->ev_ready);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     return PA_OK;
 }
@@ -654,6 +688,7 @@ const char* pa_strerror(pa_status s)
     case PA_ECUDA: return "CUDA runtime error";
     case PA_ESTATE: return "invalid state for this call";
     case PA_ESTALLED: return "adaptive step found no positive step size";
+    case PA_EAGAIN: return "previous step not finished yet";
     }
     return "unknown status";
 }
@@ -739,6 +774,10 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
     // staging for adaptive uploads (level weights + thresholds)
     c->h_stage_bytes = N1 * sizeof(double) + 64;
     if (cudaMallocHost(&c->h_stage, c->h_stage_bytes) != cudaSuccess) return fail(PA_ENOMEM);
+    if (c->adaptive) {
+        if (cudaMallocHost(&c->h_down, sizeof(StepDev) + 16 + 4 * N1) != cudaSuccess) return fail(PA_ENOMEM);
+        if (cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess) return fail(PA_ECUDA);
+    }
     c->T4.push_back(1ull << 32);
     c->T8.push_back(1ull << 32);
     if (!c->adaptive) {
@@ -777,6 +816,14 @@ pa_status pa_step(pa_ctx* c)
     if (c->in_batch) return PA_ESTATE;
     if (c->failed != PA_OK) return c->failed;
     return enqueue_step(c);
+}
+
+pa_status pa_step_async(pa_ctx* c)
+{
+    if (!c) return PA_EINVAL;
+    if (c->in_batch) return PA_ESTATE;
+    if (c->failed != PA_OK) return c->failed;
+    return enqueue_step(c, false);
 }
 
 pa_status pa_sync(pa_ctx* c)
@@ -1537,3 +1584,100 @@ void pa_batch_destroy(pa_batch* b)
 }
 
 }  // extern "C"
+
+// ================================================================== serving
+extern "C" pa_status pa_serve(const pa_request* reqs, int32_t n, const pa_serve_options* opt,
+                              pa_request_result* out, pa_ctx** out_ctx)
+{
+    if (!reqs || !opt || !out || n < 0 || opt->max_active < 1 || !(opt->time_scale > 0.0)) return PA_EINVAL;
+    if (opt->keep && !out_ctx) return PA_EINVAL;
+    for (int32_t i = 0; i < n; i++) {
+        if (i > 0 && reqs[i].arrival_s < reqs[i - 1].arrival_s) return PA_EINVAL;
+        std::memset(&out[i], 0, sizeof(out[i]));
+        out[i].status = PA_ESTATE;
+        if (out_ctx) out_ctx[i] = nullptr;
+    }
+    using clk = std::chrono::steady_clock;
+    const auto t0 = clk::now();
+    auto now_s = [&]() { return std::chrono::duration<double>(clk::now() - t0).count(); };
+    struct Active {
+        int32_t idx;
+        pa_ctx* ctx;
+        size_t fp;
+        bool enq_done;
+    };
+    std::vector<Active> active;
+    size_t used = 0;
+    int32_t next = 0, finished = 0;
+    while (finished < n) {
+        bool progress = false;
+        // admission: arrival order, concurrency limit, HBM budget
+        while (next < n && reqs[next].arrival_s * opt->time_scale <= now_s() &&
+               (int32_t)active.size() < opt->max_active) {
+            const size_t fp = pa_footprint_bytes(&reqs[next].cfg);
+            if (opt->hbm_budget && !active.empty() && used + fp > opt->hbm_budget) break;
+            pa_request_result& r = out[next];
+            r.admit_s = now_s();
+            r.footprint = (int64_t)fp;
+            pa_ctx* c = nullptr;
+            const pa_status st = pa_create(&reqs[next].cfg, nullptr, &c);
+            if (st != PA_OK) {
+                r.status = st;
+                r.finish_s = now_s();
+                finished++;
+            } else {
+                active.push_back({next, c, fp, false});
+                used += fp;
+            }
+            next++;
+            progress = true;
+        }
+        // advance every resident run
+        for (size_t a = 0; a < active.size();) {
+            Active& A = active[a];
+            bool retire = false;
+            if (!A.enq_done) {
+                const pa_status st = pa_step_async(A.ctx);
+                if (st == PA_OK) {
+                    progress = true;
+                } else if (st == PA_DONE) {
+                    A.enq_done = true;
+                    progress = true;
+                } else if (st != PA_EAGAIN) {
+                    out[A.idx].status = st;
+                    retire = true;
+                }
+            }
+            if (A.enq_done && !retire) {
+                const cudaError_t q = cudaStreamQuery(A.ctx->stream);
+                if (q == cudaSuccess) {
+                    out[A.idx].status = pull_records(A.ctx);
+                    retire = true;
+                } else if (q != cudaErrorNotReady) {
+                    out[A.idx].status = from_cuda(q, __LINE__);
+                    retire = true;
+                }
+            }
+            if (retire) {
+                pa_request_result& r = out[A.idx];
+                r.finish_s = now_s();
+                pa_ctx* c = A.ctx;
+                r.steps = c->done_rows > 0 ? c->done_rows - 1 : 0;
+                double att = 0.0;
+                for (long long i = 1; i < c->done_rows; i++)
+                    att += (double)c->N * (double)c->cfg.theta * (double)c->recs[(size_t)i].R;
+                r.attempts = att;
+                if (opt->keep) out_ctx[A.idx] = c;
+                else pa_destroy(c);
+                used -= A.fp;
+                finished++;
+                progress = true;
+                active.erase(active.begin() + (long)a);
+            } else {
+                a++;
+            }
+        }
+        if (!progress) std::this_thread::sleep_for(std::chrono::microseconds(20));
+    }
+    return PA_OK;
+}
