@@ -363,12 +363,120 @@ def run_engine(args):
     return 0
 
 
+# ------------------------------------------------------------------ other workloads
+def run_batched(args):
+    """Config 4: 64 runs (L, R, theta drawn from Philox tag 3, seed 99), fixed
+    dbeta = 0.005 over beta 0->1, seeds 100..163; all runs in one batched
+    graph launch vs the same runs one at a time (each a graph-captured run)."""
+    import torch
+
+    import paper_1703_03676_gb300 as eng
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    draw = eng.batch_config4_draw(64)
+    n_steps = args.c4_steps
+    bf = n_steps * 0.005
+    cfgs = [eng.PAConfig(L=L, R=R, theta=th, beta_f=bf, dbeta=0.005, seed=100 + i) for i, (L, R, th) in enumerate(draw)]
+    att_of = lambda rows, c: c.L * c.L * c.theta * int(rows["R"][1:].sum())  # noqa: E731
+    b = eng.PABatch(cfgs, stream=stream)
+    times = []
+    att_b = 0
+    for k in range(args.warmup + args.steps):
+        b.reset([100 + i + 1000 * k for i in range(64)])
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        b.launch()
+        e1.record(stream)
+        b.sync()
+        if k >= args.warmup:
+            times.append(e0.elapsed_time(e1))
+            att_b += sum(att_of(r.rows(), c) for r, c in zip(b.runs, cfgs))
+    v_batched = att_b / (sum(times) * 1e6)
+    shapes = {c.L: b.shape(i)["group_threads"] for i, c in enumerate(cfgs)}
+    b.close()
+    runs = [eng.PARun(c, stream=stream) for c in cfgs]
+    t_alone, att_a = 0.0, 0
+    for k in range(max(1, args.warmup // 3) + args.steps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for i, r in enumerate(runs):
+            r.reset(100 + i + 1000 * k)
+        e0.record(stream)
+        for r in runs:
+            r.launch()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= max(1, args.warmup // 3):
+            t_alone += e0.elapsed_time(e1)
+            att_a += sum(att_of(r.rows(), c) for r, c in zip(runs, cfgs))
+    for r in runs:
+        r.close()
+    v_alone = att_a / (t_alone * 1e6)
+    line = {"metric": METRIC, "workload": "batched", "value": v_batched, "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(times) / len(times),
+            "higher_is_better": True, "single_run_value": v_alone, "batched_over_single": v_batched / v_alone,
+            "config": {"workload": f"64 runs, L/R/theta from Philox tag 3 seed 99, dbeta 0.005, {n_steps} steps "
+                                   f"(beta 0->{bf:g}), seeds 100..163 (+1000 per bench step), bit-packed",
+                       "attempts_per_step": att_b / len(times), "group_threads_by_L": shapes},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_served(args):
+    """Config 5, scaled: the first n requests of the served trace (Poisson
+    arrivals at 20/s, L in {32..512}, seeds 1000+q, all drawn from Philox tag
+    4 seed 999), theta = 50, adaptive steps with overlap 0.85, with R divided
+    by r_div and beta_f lowered to beta_f_serve. Continuous batching
+    (max_active, HBM budget) vs one run at a time; p50/p99 latency."""
+    import torch
+
+    import paper_1703_03676_gb300 as eng
+    torch.cuda.set_device(0)
+    trace = eng.served_trace(args.serve_n)
+    reqs = [(t, eng.PAConfig(L=L, R=max(100, R // args.serve_rdiv), theta=50, beta_f=args.serve_beta_f, dbeta=0.0,
+                             overlap=0.85, seed=seed)) for (t, L, R, seed) in trace]
+    free, total = torch.cuda.mem_get_info()
+    budget = int(min(args.serve_budget_gb * 2 ** 30, 0.8 * free))
+    out = {}
+    for name, max_active in (("served", args.serve_active), ("one_at_a_time", 1)):
+        t0 = time.perf_counter()
+        res, _ = eng.serve(reqs, hbm_budget=budget, max_active=max_active)
+        wall = time.perf_counter() - t0
+        lat = sorted(r["finish_s"] - t for r, (t, _) in zip(res, reqs))
+        att = sum(r["attempts"] for r in res)
+        ok = all(r["status"] == 0 for r in res)
+        out[name] = {"flips_per_ns": att / (wall * 1e9), "makespan_s": wall, "p50_latency_s": lat[len(lat) // 2],
+                     "p99_latency_s": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                     "all_ok": ok, "attempts": att}
+    line = {"metric": METRIC, "workload": "served", "value": out["served"]["flips_per_ns"], "unit": UNIT,
+            "n_gpus": 1, "higher_is_better": True,
+            "p50_latency_s": out["served"]["p50_latency_s"], "p99_latency_s": out["served"]["p99_latency_s"],
+            "one_at_a_time": out["one_at_a_time"],
+            "served_over_one_at_a_time": out["served"]["flips_per_ns"] / out["one_at_a_time"]["flips_per_ns"],
+            "served": out["served"],
+            "config": {"workload": f"first {args.serve_n} requests of the 500-request trace (Poisson 20/s, L in "
+                                   f"32..512, seeds 1000+q); deviation: R/{args.serve_rdiv}, beta_f "
+                                   f"{args.serve_beta_f} instead of 1 (the full trace is ~1e17 attempts)",
+                       "max_active": args.serve_active, "hbm_budget_bytes": budget, "theta": 50, "overlap": 0.85},
+            "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
+    ap.add_argument("--workload", choices=["default", "batched", "served"], default="default")
+    ap.add_argument("--c4-steps", type=int, default=200)
+    ap.add_argument("--serve-n", type=int, default=48)
+    ap.add_argument("--serve-rdiv", type=int, default=50)
+    ap.add_argument("--serve-beta-f", type=float, default=0.5)
+    ap.add_argument("--serve-active", type=int, default=8)
+    ap.add_argument("--serve-budget-gb", type=float, default=100.0)
     ap.add_argument("--no-profile", dest="profile", action="store_false")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
@@ -380,6 +488,10 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batched":
+        return run_batched(args)
+    if args.workload == "served":
+        return run_served(args)
     return run_engine(args)
 
 

@@ -313,8 +313,9 @@ class PopulationAnnealing:
     # -- one temperature step (Sec. 2.1 steps 2-4)
     def step(self, sample: np.ndarray | None = None):
         """Advance one inverse-temperature step. With `sample` (new-slot
-        indices) only those replicas are swept and measured; the run then
-        stops (used for full-size spot checks). Returns the record."""
+        indices, or a function of R_i returning them) only those replicas are
+        swept and measured; the run then stops (used for full-size spot
+        checks). Returns the record."""
         if self.done or self.partial:
             raise RuntimeError("run finished")
         N, R = self.N, self.R
@@ -355,6 +356,8 @@ class PopulationAnnealing:
         rec.parent = parent
         u0 = (i - 1) * self.theta
         if sample is not None:
+            if callable(sample):
+                sample = sample(R_new)
             sample = np.asarray(sample, dtype=np.int64)
             sub = np.ascontiguousarray(self.pop[parent[sample]])
             sweep(sub, sample, self.seed, u0, self.theta, T4, T8)
