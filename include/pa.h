@@ -105,6 +105,25 @@ typedef struct {
  * Errors: PA_EINVAL (bad config), PA_ENOMEM, PA_ECUDA. */
 pa_status pa_create(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
 
+/* Create a run that follows a given schedule beta_1 < ... < beta_n (host
+ * array betas[n], 0 < beta_i <= 50), with step i using
+ * delta_i = beta_i - beta_{i-1} in Q and tau_hat. Sec. 2.3: with M runs the
+ * adaptive schedule is decided in the first run and kept for the others
+ * (pass that run's row betas). cfg->dbeta, overlap and beta_f are ignored.
+ * Steps run like adaptive ones (one histogram readback per step). */
+pa_status pa_create_scheduled(const pa_config *cfg, const double *betas, int64_t n, void *cuda_stream,
+                              pa_ctx **out);
+
+/* Combine M independent runs (Sec. 2.2, Eq. weighted-average): rows is the
+ * host array of M x n rows (run-major) of runs of N = L*L spins sharing the
+ * same betas. At each beta the weights are exp(-beta F_m) normalised, with
+ * -beta F_m = -N (beta F / N)_m; e, |m|, m^2, m^4 are averaged; C comes from
+ * the weighted <e> and <e^2> = C_m / (beta^2 N) + e_m^2 (beta > 0); the
+ * combined -beta F = ln((1/M) sum_m Z_m); S/N = beta e - beta F / N; R and
+ * families are summed; lnQ is NaN. Host-only (no GPU needed). PA_EINVAL if
+ * the betas differ by more than 1e-12 relative. */
+pa_status pa_weighted_average(const pa_obs *rows, int32_t m, int64_t n, int32_t N, pa_obs *out);
+
 /* One temperature step (Sec. 2.1 steps 2-4). Fixed steps only enqueue work;
  * adaptive steps synchronise once to read the previous histogram.
  * Returns PA_DONE if beta_f was already reached. Device-side failures

@@ -222,6 +222,8 @@ class Row:
     R: int
     families: int
 
+    N: int = 0
+
     def as_tuple(self):
         return (self.beta, self.e, self.C, self.abs_m, self.m2, self.m4,
                 self.betaF_per_N, self.S_per_N, self.lnQ, self.R, self.families)
@@ -247,7 +249,7 @@ def make_row(beta: float, N: int, R: int, sums, sum_lnQ: float, lnQ: float, fami
     m2 = float(sM2) / (fR * fN * fN)
     m4 = float(sM4) / (fR * fN * fN * fN * fN)
     betaF = -(fN * math.log(2.0) + sum_lnQ) / fN
-    return Row(beta, e, C, abs_m, m2, m4, betaF, beta * e - betaF, lnQ, R, families)
+    return Row(beta, e, C, abs_m, m2, m4, betaF, beta * e - betaF, lnQ, R, families, N)
 
 
 class PopulationAnnealing:
@@ -255,7 +257,7 @@ class PopulationAnnealing:
 
     def __init__(self, L: int, R: int, theta: int, beta_f: float = 1.0, dbeta: float = 0.01,
                  seed: int = 1, beta0: float = 0.0, overlap: float = 0.85,
-                 capacity: int = 0, record_hist: bool = True):
+                 capacity: int = 0, record_hist: bool = True, schedule=None):
         if L < 4 or L % 2:
             raise ValueError("L must be even and >= 4")
         if beta0 != 0.0:
@@ -266,11 +268,18 @@ class PopulationAnnealing:
         self.seed = int(seed)
         self.beta_f = float(beta_f)
         self.dbeta = float(dbeta)
-        self.adaptive = not (self.dbeta > 0.0)
+        # a given schedule beta_1 < ... < beta_n (Sec. 2.3: with M runs the
+        # adaptive schedule of the first run is reused); step i then uses
+        # delta_i = beta_i - beta_{i-1}
+        self.schedule = None if schedule is None else [float(b) for b in schedule]
+        self.adaptive = not (self.dbeta > 0.0) and self.schedule is None
         self.overlap = float(overlap)
         # default capacity ceil(1.05 R) + 1024 holds R_i = R +- O(sqrt R)
         self.R_cap = int(capacity) if capacity > 0 else int(math.ceil(self.R * 1.05)) + 1024
-        self.n_fixed = int(math.floor((self.beta_f - beta0) / self.dbeta + 0.5)) if not self.adaptive else None
+        if self.schedule is not None:
+            self.n_fixed = len(self.schedule)
+        else:
+            self.n_fixed = int(math.floor((self.beta_f - beta0) / self.dbeta + 0.5)) if not self.adaptive else None
         self.record_hist = record_hist
         self.step_index = 0
         self.beta = 0.0
@@ -325,7 +334,11 @@ class PopulationAnnealing:
         H = np.bincount(lv, minlength=N + 1).astype(np.int64)
         occ = np.nonzero(H)[0]
         kmin, kmax = int(occ[0]), int(occ[-1])
-        if self.adaptive:
+        if self.schedule is not None:
+            beta_new = self.schedule[i - 1]
+            delta = beta_new - self.beta
+            final = i == self.n_fixed
+        elif self.adaptive:
             delta, final = choose_delta(H, kmin, kmax, R, R_prev, self.beta, self.beta_f, self.overlap, N)
             if delta <= 0.0:
                 raise OracleError("stalled", "adaptive step found no positive delta")
@@ -421,3 +434,43 @@ class PopulationAnnealing:
             out.append({"beta": float(b), "e": e, "C": b * b * (e2 - e1 * e1) / N,
                         "betaF_per_N": bF, "S_per_N": b * e - bF, "lnZ": lnZ})
         return out
+
+
+# ------------------------------------------------------------- M runs (Sec. 2.2)
+def weighted_average(runs_rows):
+    """Combine M independent runs with the same inverse temperatures
+    (Eq. weighted-average). At each beta_i the weights are
+    omega_m = exp(-beta_i F_m) / sum_m exp(-beta_i F_m), where
+    -beta_i F_m = ln Z_m = -N (beta F / N)_m (Eq. free-energy). e, |m|, m^2
+    and m^4 are averaged with these weights; C is formed from the weighted
+    <e> and <e^2>, each run's <e^2> being C_m / (beta^2 N) + e_m^2 (at
+    beta = 0 the C_m are averaged); the combined free energy is
+    -beta F = ln((1/M) sum_m Z_m), and S/N = beta e - beta F / N.
+    runs_rows: M lists of Row (same length, same betas)."""
+    M = len(runs_rows)
+    out = []
+    for i in range(len(runs_rows[0])):
+        rows = [rr[i] for rr in runs_rows]
+        beta, N = rows[0].beta, rows[0].N
+        for r in rows:
+            if abs(r.beta - beta) > 1e-12 * max(1.0, abs(beta)) or r.N != N:
+                raise ValueError("runs must share N and the inverse temperatures")
+        lw = [-N * r.betaF_per_N for r in rows]
+        top = max(lw)
+        ex = [math.exp(x - top) for x in lw]
+        Z = sum(ex)
+        w = [x / Z for x in ex]
+        e = sum(wi * r.e for wi, r in zip(w, rows))
+        if beta > 0.0:
+            e2 = sum(wi * (r.C / (beta * beta * N) + r.e * r.e) for wi, r in zip(w, rows))
+            C = beta * beta * N * (e2 - e * e)
+        else:
+            C = sum(wi * r.C for wi, r in zip(w, rows))
+        bF = -(top + math.log(Z) - math.log(M)) / N
+        out.append({"beta": beta, "e": e, "C": C,
+                    "abs_m": sum(wi * r.abs_m for wi, r in zip(w, rows)),
+                    "m2": sum(wi * r.m2 for wi, r in zip(w, rows)),
+                    "m4": sum(wi * r.m4 for wi, r in zip(w, rows)),
+                    "betaF_per_N": bF, "S_per_N": beta * e - bF,
+                    "R": sum(r.R for r in rows), "families": sum(r.families for r in rows), "weights": w})
+    return out

@@ -102,6 +102,9 @@ SIGNATURES = [
                                       ctypes.POINTER(ctypes.c_int32)]),
     ("pa_batch_destroy", None, [_P]),
     ("pa_step_async", ctypes.c_int, [_P]),
+    ("pa_create_scheduled", ctypes.c_int, [ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
+                                           _P, ctypes.POINTER(_P)]),
+    ("pa_weighted_average", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P]),
     ("pa_serve", ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     ("pa_measure_rng_peak", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     ("pa_resample", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64, _P,
@@ -184,12 +187,20 @@ def footprint_bytes(cfg: PAConfig) -> int:
 class PARun:
     """One population-annealing run on the GPU (a pa_ctx)."""
 
-    def __init__(self, cfg: PAConfig, stream=None):
+    def __init__(self, cfg: PAConfig, stream=None, schedule=None):
+        """schedule: optional increasing betas beta_1..beta_n to follow
+        (pa_create_scheduled), e.g. the row betas of an adaptive first run."""
         self.cfg = cfg
         self._lib = lib()
         self._h = ctypes.c_void_p()
         c = cfg._c()
-        _check(self._lib.pa_create(ctypes.byref(c), _stream_handle(stream), ctypes.byref(self._h)), "pa_create")
+        if schedule is None:
+            _check(self._lib.pa_create(ctypes.byref(c), _stream_handle(stream), ctypes.byref(self._h)), "pa_create")
+        else:
+            b = np.ascontiguousarray(schedule, dtype=np.float64)
+            _check(self._lib.pa_create_scheduled(ctypes.byref(c), b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                                 b.size, _stream_handle(stream), ctypes.byref(self._h)),
+                   "pa_create_scheduled")
         self.N = cfg.L * cfg.L
 
     # -- lifecycle
@@ -510,6 +521,27 @@ def resample(levels, F, U, seed: int, step: int, capacity: int, stream=None, par
                              ctypes.c_void_p(parent.data_ptr()), capacity, ctypes.byref(n), _stream_handle(stream)),
            "pa_resample_noalloc" if noalloc else "pa_resample")
     return parent[: n.value], n.value
+
+
+def weighted_average(rows_list, N: int) -> np.ndarray:
+    """Combine M runs' row arrays (PARun.rows(), same betas) with free-energy
+    weights (pa_weighted_average, Eq. weighted-average)."""
+    m = len(rows_list)
+    n = len(rows_list[0])
+    buf = (_Obs * (m * n))()
+    for r, rows in enumerate(rows_list):
+        assert len(rows) == n
+        for i in range(n):
+            o = buf[r * n + i]
+            for f in OBS_FIELDS:
+                setattr(o, f, rows[f][i].item())
+    out = (_Obs * n)()
+    _check(lib().pa_weighted_average(buf, m, n, N, out), "pa_weighted_average")
+    res = np.zeros(n, dtype=_OBS_DTYPE)
+    for i in range(n):
+        for f in OBS_FIELDS:
+            res[f][i] = getattr(out[i], f)
+    return res
 
 
 def batch_config4_draw(n: int = 64, seed: int = 99, stream=None):

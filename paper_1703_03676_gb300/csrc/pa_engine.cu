@@ -91,6 +91,7 @@ struct pa_ctx {
     bool done = false;            // beta_f reached
     pa_status failed = PA_OK;     // sticky device failure
     bool in_batch = false;        // stepped by a pa_batch, read-only for the caller
+    std::vector<double> sched;    // given schedule beta_1..beta_n (empty: none)
     std::vector<double> betas;    // beta_i for i = 0..enq_step
     std::vector<double> deltas;   // step size used by step i (0 for i = 0)
     std::vector<uint64_t> T4, T8;
@@ -405,7 +406,12 @@ pa_status enqueue_step(pa_ctx* c, bool wait = true)
         const double bprev = c->betas[(size_t)(i - 1)];
         const double dmax = c->cfg.beta_f - bprev;
         const double target = c->cfg.overlap;
-        if (overlap_alpha(H, kmin, kmax, c->cfg.R, pr.R, dmax, P) >= target) {
+        if (!c->sched.empty()) {
+            // given schedule (Sec. 2.3: the first run's steps, reused)
+            beta = c->sched[(size_t)(i - 1)];
+            delta = beta - bprev;
+            final_step = (i == (long long)c->sched.size());
+        } else if (overlap_alpha(H, kmin, kmax, c->cfg.R, pr.R, dmax, P) >= target) {
             delta = dmax;
             final_step = true;
             beta = c->cfg.beta_f;
@@ -807,6 +813,74 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
     }
     c->enq_step = 0;
     *out = c;
+    return PA_OK;
+}
+
+pa_status pa_create_scheduled(const pa_config* cfg, const double* betas, int64_t n, void* cuda_stream,
+                              pa_ctx** out)
+{
+    if (!cfg || !betas || !out || n < 1 || n > kMaxAdaptiveSteps) return PA_EINVAL;
+    double prev = 0.0;
+    for (int64_t i = 0; i < n; i++) {
+        if (!(betas[i] > prev) || !(betas[i] <= 50.0)) return PA_EINVAL;
+        prev = betas[i];
+    }
+    pa_config c = *cfg;
+    c.dbeta = 0.0;  // stepped like an adaptive run, with the given betas
+    c.overlap = 0.5;
+    c.beta_f = betas[n - 1];
+    PA_TRY(pa_create(&c, cuda_stream, out));
+    (*out)->sched.assign(betas, betas + n);
+    return PA_OK;
+}
+
+// Eq. weighted-average over M runs sharing the inverse temperatures.
+pa_status pa_weighted_average(const pa_obs* rows, int32_t m, int64_t n, int32_t N, pa_obs* out)
+{
+    if (!rows || !out || m < 1 || n < 1 || N < 1) return PA_EINVAL;
+    std::vector<double> lw((size_t)m), w((size_t)m);
+    for (int64_t i = 0; i < n; i++) {
+        const double beta = rows[i].beta;
+        for (int32_t r = 0; r < m; r++) {
+            const pa_obs& o = rows[(size_t)r * (size_t)n + (size_t)i];
+            if (std::fabs(o.beta - beta) > 1e-12 * std::max(1.0, std::fabs(beta))) return PA_EINVAL;
+            lw[(size_t)r] = -(double)N * o.betaF_per_N;
+        }
+        double top = lw[0];
+        for (int32_t r = 1; r < m; r++) top = std::max(top, lw[(size_t)r]);
+        double Z = 0.0;
+        for (int32_t r = 0; r < m; r++) {
+            w[(size_t)r] = std::exp(lw[(size_t)r] - top);
+            Z += w[(size_t)r];
+        }
+        for (int32_t r = 0; r < m; r++) w[(size_t)r] /= Z;
+        double e = 0.0, am = 0.0, m2 = 0.0, m4 = 0.0, e2 = 0.0, Cavg = 0.0;
+        int64_t R = 0, fam = 0;
+        for (int32_t r = 0; r < m; r++) {
+            const pa_obs& o = rows[(size_t)r * (size_t)n + (size_t)i];
+            const double wi = w[(size_t)r];
+            e += wi * o.e;
+            am += wi * o.abs_m;
+            m2 += wi * o.m2;
+            m4 += wi * o.m4;
+            if (beta > 0.0) e2 += wi * (o.C / (beta * beta * N) + o.e * o.e);
+            Cavg += wi * o.C;
+            R += o.R;
+            fam += o.families;
+        }
+        pa_obs& d = out[i];
+        d.beta = beta;
+        d.e = e;
+        d.C = beta > 0.0 ? beta * beta * N * (e2 - e * e) : Cavg;
+        d.abs_m = am;
+        d.m2 = m2;
+        d.m4 = m4;
+        d.betaF_per_N = -(top + std::log(Z) - std::log((double)m)) / (double)N;
+        d.S_per_N = beta * e - d.betaF_per_N;
+        d.lnQ = NAN;
+        d.R = R;
+        d.families = fam;
+    }
     return PA_OK;
 }
 

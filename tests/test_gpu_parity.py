@@ -189,3 +189,39 @@ def test_invalid_configs_rejected():
         with pytest.raises(eng.PAError) as ei:
             eng.PARun(eng.PAConfig(**base))
         assert ei.value.kind == "invalid argument"
+
+
+def test_schedule_reuse_and_weighted_average():
+    """Sec. 2.3 / 2.2: run 1 adaptive, runs 2-3 follow its schedule with other
+    seeds, then the free-energy-weighted average; every run and the
+    combination match the oracle."""
+    from oracle.pa_oracle import PopulationAnnealing, weighted_average
+    L, R, theta = 16, 900, 4
+    p1 = oracle_run(L, R, theta, 0.5, 0.0, 61)
+    p1.run()
+    sched = [r.beta for r in p1.rows[1:]]
+    r1 = engine_run(L, R, theta, 0.5, 0.0, 61, B32)
+    r1.run()
+    rows1 = r1.rows()
+    np.testing.assert_array_equal(rows1["beta"][1:], np.array(sched))
+    oracle_runs, engine_rows = [p1], [rows1]
+    for seed in (62, 63):
+        pm = PopulationAnnealing(L, R, theta, seed=seed, schedule=sched)
+        pm.run()
+        rm = eng.PARun(eng.PAConfig(L=L, R=R, theta=theta, seed=seed, spin_format=B32, record_histograms=True),
+                       schedule=sched)
+        rm.run()
+        rows = rm.rows()
+        for i, ref in enumerate(pm.rows):
+            assert_row_close(rows[i], ref, f"scheduled seed {seed} row {i}")
+            compare_step(rm, pm, i)
+        np.testing.assert_array_equal(rm.population(), pm.pop)
+        oracle_runs.append(pm)
+        engine_rows.append(rows)
+        rm.close()
+    comb = eng.weighted_average(engine_rows, L * L)
+    ref = weighted_average([p.rows for p in oracle_runs])
+    for i, g in enumerate(ref):
+        for f in ("e", "C", "abs_m", "m2", "m4", "betaF_per_N", "S_per_N"):
+            assert math.isclose(float(comb[f][i]), g[f], rel_tol=1e-11, abs_tol=1e-13), (i, f)
+    r1.close()
