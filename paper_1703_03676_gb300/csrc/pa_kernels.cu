@@ -90,9 +90,10 @@ __device__ __forceinline__ void neighbours(const uint32_t* __restrict__ O, int c
 // A site with n aligned neighbours flips with certainty if n <= 2 (dE <= 0),
 // with x <= T4-1 if n = 3 and x <= T8-1 if n = 4, x the SWEEP word of the
 // site: counter (2u + c, b>>2, 1, k), lane b&3. Only counter word 1 differs
-// between the lanes of a warp, so the first-round products are warp-uniform. Bit-sliced counting of the
-// disagreeing neighbours d1..d4 gives "at least two disagree" (n <= 2) and
-// "none disagrees" (n = 4) for all 32 sites at once.
+// between the lanes of a warp, so the first-round products are warp-uniform.
+// Bit-sliced counting of the disagreeing neighbours d1..d4 gives "at least
+// two disagree" (n <= 2) and "none disagrees" (n = 4) for all 32 sites at
+// once; each site is then compared once, against the threshold its n selects.
 __device__ __forceinline__ uint32_t metropolis_word(uint32_t s, uint32_t same, uint32_t side, uint32_t up,
                                                     uint32_t down, unsigned c0, unsigned k, unsigned c2,
                                                     uint32_t t4m1, uint32_t t8m1, PhiloxKey key)
@@ -100,18 +101,20 @@ __device__ __forceinline__ uint32_t metropolis_word(uint32_t s, uint32_t same, u
     const uint32_t d1 = s ^ same, d2 = s ^ side, d3 = s ^ up, d4 = s ^ down;
     const uint32_t a = d1 ^ d2, b = d1 & d2, cc = d3 ^ d4, e = d3 & d4;
     const uint32_t ge2 = b | e | (a & cc);
-    const uint32_t any = d1 | d2 | d3 | d4;
-    uint32_t acc4 = 0, acc8 = 0;
+    const uint32_t eq0 = ~(d1 | d2 | d3 | d4);
+    uint32_t acc = 0;
 #pragma unroll
     for (int q = 0; q < 8; q++) {
         const uint4 x = philox10(make_uint4(c2, c0 + q, kTagSweep, k), key);
-        acc4 |= ((uint32_t)(x.x <= t4m1) << (4 * q)) | ((uint32_t)(x.y <= t4m1) << (4 * q + 1)) |
-                ((uint32_t)(x.z <= t4m1) << (4 * q + 2)) | ((uint32_t)(x.w <= t4m1) << (4 * q + 3));
-        acc8 |= ((uint32_t)(x.x <= t8m1) << (4 * q)) | ((uint32_t)(x.y <= t8m1) << (4 * q + 1)) |
-                ((uint32_t)(x.z <= t8m1) << (4 * q + 2)) | ((uint32_t)(x.w <= t8m1) << (4 * q + 3));
+        const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int l = 0; l < 4; l++) {
+            const int t = 4 * q + l;
+            const uint32_t thr = ((eq0 >> t) & 1u) ? t8m1 : t4m1;
+            acc |= (uint32_t)(xs[l] <= thr) << t;
+        }
     }
-    const uint32_t flip = ge2 | (acc4 & any & ~ge2) | (acc8 & ~any);
-    return s ^ flip;
+    return s ^ (ge2 | acc);
 }
 
 // ======================================================== shared epilogue
