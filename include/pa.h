@@ -182,8 +182,17 @@ pa_status pa_replicas(pa_ctx *ctx, int32_t *E, int32_t *M, int64_t *family, int6
 
 /* Multi-histogram reweighting (Sec. 2.4, Eq. MHReq1) over all completed
  * rows, evaluated at n inverse temperatures: out[t] gets beta, e, C,
- * beta F / N and S / N; the magnetisation fields are NaN. */
+ * beta F / N, S / N and the magnetisation moments |m|, m^2, m^4 (Sec. 2.4
+ * notes the generalisation to magnetisations: the Boltzmann weight depends
+ * on E only, so sum_M Omega(E, M) f(M) = Omega(E) (sum of f(M) over every
+ * sample at level E) / Hsum(E)); lnQ is NaN, R and families 0. */
 pa_status pa_mhr(pa_ctx *ctx, const double *betas, int64_t n, pa_obs *out);
+
+/* The per-level magnetisation sums behind pa_mhr, over all measured replicas
+ * of all completed steps: out[5k + 0] = sum |M|, out[5k + 1..2] = sum M^2
+ * (low, high 64 bits), out[5k + 3..4] = sum M^4 (low, high), for energy
+ * levels k = 0..N (cap >= 5 (N + 1)). */
+pa_status pa_mag_sums(pa_ctx *ctx, uint64_t *out, int64_t cap);
 
 /* ln Omega(E_k) for k = 0..N from Eq. MHReq1 (-inf where never visited). */
 pa_status pa_ln_dos(pa_ctx *ctx, double *out, int64_t cap);

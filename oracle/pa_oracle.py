@@ -292,6 +292,9 @@ class PopulationAnnealing:
         self.fam = np.arange(self.R, dtype=np.int64)
         self.sum_lnQ = 0.0
         self.Hsum = np.zeros(self.N + 1, dtype=np.int64)
+        # per energy level, summed over every measured replica of every step:
+        # sum |M|, sum M^2, sum M^4 (Python ints, exact)
+        self.Msums = [[0, 0, 0] for _ in range(self.N + 1)]
         self.records: list[StepRecord] = []
         self.rows: list[Row] = []
         self._measure_and_record(StepRecord(step=0, beta=0.0, delta=0.0, R=self.R, R_prev=self.R))
@@ -308,6 +311,11 @@ class PopulationAnnealing:
         H_E = np.bincount(self.levels(), minlength=N + 1).astype(np.int64)
         H_M = np.bincount(self.mlevels(), minlength=N + 1).astype(np.int64)
         self.Hsum += H_E
+        for k, m in zip(self.levels().tolist(), self.M.tolist()):
+            acc = self.Msums[k]
+            acc[0] += abs(m)
+            acc[1] += m * m
+            acc[2] += m ** 4
         rec.families = int(np.unique(self.fam).size)
         rec.sums = moment_sums(self.E, self.M)
         if self.record_hist:
@@ -415,11 +423,17 @@ class PopulationAnnealing:
         return E_k, out
 
     def mhr(self, betas) -> list[dict]:
-        """Reweighted e, C, beta F / N and S / N at each beta from ln Omega."""
+        """Reweighted e, C, beta F / N, S / N and magnetisation moments at each
+        beta. The Boltzmann weight depends on E only, so the joint estimate
+        Omega(E, M) of Eq. MHReq1 gives sum_M Omega(E, M) f(M) =
+        Omega(E) * (sum of f(M) over every sample at level E) / Hsum(E)."""
         N = self.N
         E_k, lno = self.ln_dos()
         ok = np.isfinite(lno)
         E, lo = E_k[ok], lno[ok]
+        idx = np.nonzero(ok)[0]
+        cnt = np.array([float(self.Hsum[k]) for k in idx])
+        mic = np.array([[float(self.Msums[k][j]) / c for j in range(3)] for k, c in zip(idx, cnt)])
         out = []
         for b in betas:
             a = lo - b * E
@@ -429,10 +443,12 @@ class PopulationAnnealing:
             lnZ = m + math.log(float(Z))
             e1 = float((w * E).sum() / Z)
             e2 = float((w * E * E).sum() / Z)
+            am, m2, m4 = (float((w * mic[:, j]).sum() / Z) for j in range(3))
             e = e1 / N
             bF = -lnZ / N
             out.append({"beta": float(b), "e": e, "C": b * b * (e2 - e1 * e1) / N,
-                        "betaF_per_N": bF, "S_per_N": b * e - bF, "lnZ": lnZ})
+                        "betaF_per_N": bF, "S_per_N": b * e - bF, "lnZ": lnZ,
+                        "abs_m": am / N, "m2": m2 / N ** 2, "m4": m4 / N ** 4})
         return out
 
 

@@ -82,6 +82,7 @@ SIGNATURES = [
                                    ctypes.c_int64, _I64P]),
     ("pa_mhr", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.POINTER(_Obs)]),
     ("pa_ln_dos", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
+    ("pa_mag_sums", ctypes.c_int, [_P, _P, ctypes.c_int64]),
     ("pa_phase_times", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I64P]),
     ("pa_launch_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32)]),
@@ -308,6 +309,12 @@ class PARun:
         _check(self._lib.pa_ln_dos(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size),
                "pa_ln_dos")
         return out
+
+    def mag_sums(self) -> np.ndarray:
+        """Per-level sums (N+1, 5) uint64: |M|, M^2 lo/hi, M^4 lo/hi."""
+        out = np.zeros((self.N + 1) * 5, dtype=np.uint64)
+        _check(self._lib.pa_mag_sums(self._h, ctypes.c_void_p(out.ctypes.data), out.size), "pa_mag_sums")
+        return out.reshape(self.N + 1, 5)
 
     def mhr(self, betas) -> np.ndarray:
         b = np.ascontiguousarray(betas, dtype=np.float64)

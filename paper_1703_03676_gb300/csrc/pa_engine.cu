@@ -220,6 +220,7 @@ size_t footprint(const pa_config& c)
     b += 2 * (size_t)s.ntiles * 4;                  // tile sums / offsets
     b += 2 * 2 * N1 * 4;                            // H
     b += N1 * 8 * 3 + N1 * 4;                       // Hsum, tw, U, F
+    b += N1 * 8 * 5;                                // magnetisation sums per level
     b += 2 * (size_t)(s.steps + 1) * 4;             // thresholds
     b += (size_t)(s.steps + 1) * sizeof(StepDev);   // records
     b += (size_t)s.hist_steps * 2 * N1 * 4;         // recorded histograms
@@ -522,6 +523,7 @@ pa_status reset_run(pa_ctx* c, uint64_t seed)
     PA_CUDA(cudaMemsetAsync(h.H[0], 0, 2 * N1 * 4, c->stream));
     PA_CUDA(cudaMemsetAsync(h.H[1], 0, 2 * N1 * 4, c->stream));
     PA_CUDA(cudaMemsetAsync(h.Hsum, 0, N1 * 8, c->stream));
+    PA_CUDA(cudaMemsetAsync(h.Msum, 0, 5 * N1 * 8, c->stream));
     PA_CUDA(cudaMemsetAsync(h.rec, 0, sizeof(StepDev) * (size_t)(c->max_steps + 1), c->stream));
     PA_CUDA(cudaMemsetAsync(h.status, 0, 16, c->stream));
     PA_CUDA(cudaMemsetAsync(h.work, 0, 16, c->stream));
@@ -766,6 +768,7 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
     PA_ALLOC(h.tile_sum, (size_t)s.ntiles);
     PA_ALLOC(h.tile_off, (size_t)s.ntiles);
     PA_ALLOC(h.Hsum, N1);
+    PA_ALLOC(h.Msum, 5 * N1);
     PA_ALLOC(h.tw, N1);
     PA_ALLOC(h.F, N1);
     PA_ALLOC(h.U, N1);
@@ -1085,12 +1088,38 @@ pa_status pa_ln_dos(pa_ctx* c, double* out, int64_t cap)
     return PA_OK;
 }
 
+pa_status pa_mag_sums(pa_ctx* c, uint64_t* out, int64_t cap)
+{
+    if (!c || !out || cap < 5 * ((int64_t)c->N + 1)) return PA_EINVAL;
+    pa_status st = pull_records(c);
+    if (st != PA_OK && st != PA_ECAPACITY && st != PA_EEXTINCT) return st;
+    PA_CUDA(cudaMemcpy(out, c->h.Msum, 5 * ((size_t)c->N + 1) * 8, cudaMemcpyDeviceToHost));
+    return PA_OK;
+}
+
+// Reweighted rows: energy moments from Omega(E); magnetisation moments from
+// sum_M Omega(E, M) f(M) = Omega(E) (sum of f(M) at level E) / Hsum(E), the
+// Boltzmann weight depending on E only.
 pa_status pa_mhr(pa_ctx* c, const double* betas, int64_t n, pa_obs* out)
 {
     if (!c || (n > 0 && (!betas || !out))) return PA_EINVAL;
     const size_t N1 = (size_t)c->N + 1;
     std::vector<double> lno(N1);
     PA_TRY(pa_ln_dos(c, lno.data(), (int64_t)N1));
+    std::vector<unsigned long long> hs(N1), ms(5 * N1);
+    PA_CUDA(cudaMemcpy(hs.data(), c->h.Hsum, N1 * 8, cudaMemcpyDeviceToHost));
+    PA_CUDA(cudaMemcpy(ms.data(), c->h.Msum, 5 * N1 * 8, cudaMemcpyDeviceToHost));
+    std::vector<double> mic(3 * N1, 0.0);
+    for (size_t k = 0; k < N1; k++) {
+        if (!hs[k]) continue;
+        const double cnt = (double)hs[k];
+        const unsigned __int128 m2 = ((unsigned __int128)ms[5 * k + 2] << 64) | ms[5 * k + 1];
+        const unsigned __int128 m4 = ((unsigned __int128)ms[5 * k + 4] << 64) | ms[5 * k + 3];
+        mic[3 * k + 0] = (double)ms[5 * k] / cnt;
+        mic[3 * k + 1] = (double)m2 / cnt;
+        mic[3 * k + 2] = (double)m4 / cnt;
+    }
+    const double fN = (double)c->N;
     for (int64_t t = 0; t < n; t++) {
         const double beta = betas[t];
         double m = -INFINITY;
@@ -1099,7 +1128,7 @@ pa_status pa_mhr(pa_ctx* c, const double* betas, int64_t n, pa_obs* out)
             const double Ek = (double)(-2ll * c->N + 4ll * (long long)k);
             m = std::max(m, lno[k] - beta * Ek);
         }
-        double Z = 0.0, e1 = 0.0, e2 = 0.0;
+        double Z = 0.0, e1 = 0.0, e2 = 0.0, a1 = 0.0, a2 = 0.0, a4 = 0.0;
         for (size_t k = 0; k < N1; k++) {
             if (!std::isfinite(lno[k])) continue;
             const double Ek = (double)(-2ll * c->N + 4ll * (long long)k);
@@ -1107,16 +1136,21 @@ pa_status pa_mhr(pa_ctx* c, const double* betas, int64_t n, pa_obs* out)
             Z += w;
             e1 += w * Ek;
             e2 += w * Ek * Ek;
+            a1 += w * mic[3 * k];
+            a2 += w * mic[3 * k + 1];
+            a4 += w * mic[3 * k + 2];
         }
         e1 /= Z;
         e2 /= Z;
         const double lnZ = m + std::log(Z);
         pa_obs& o = out[t];
         o.beta = beta;
-        o.e = e1 / (double)c->N;
-        o.C = beta * beta * (e2 - e1 * e1) / (double)c->N;
-        o.abs_m = o.m2 = o.m4 = NAN;
-        o.betaF_per_N = -lnZ / (double)c->N;
+        o.e = e1 / fN;
+        o.C = beta * beta * (e2 - e1 * e1) / fN;
+        o.abs_m = a1 / Z / fN;
+        o.m2 = a2 / Z / (fN * fN);
+        o.m4 = a4 / Z / (fN * fN * fN * fN);
+        o.betaF_per_N = -lnZ / fN;
         o.S_per_N = beta * o.e - o.betaF_per_N;
         o.lnQ = NAN;
         o.R = 0;

@@ -16,6 +16,8 @@
 //   H[2]        energy and magnetisation histograms (2 x (N+1) uint32),
 //               ping-pong by step parity.
 //   Hsum        running sum of energy histograms (Sec. 2.4).
+//   Msum        per energy level, over all steps: sum |M|, sum M^2, sum M^4
+//               (the last two as 128-bit lo/hi), for reweighting magnetisations.
 //   tw          level weights t[d] = exp(-4 delta d) (host-computed).
 //   F, U        copy tables per energy level: floor(tau_hat), ceil(frac 2^32).
 //   thr         per step: T4 - 1 and T8 - 1 (uint32).
@@ -72,6 +74,7 @@ struct RunDev {
     uint32_t* tile_off;
     uint32_t* H[2];
     unsigned long long* Hsum;
+    unsigned long long* Msum;  // per energy level: sum |M|, sum M^2 (lo, hi), sum M^4 (lo, hi)
     double* tw;
     uint32_t* F;
     unsigned long long* U;

@@ -118,7 +118,18 @@ __device__ __forceinline__ uint32_t metropolis_word(uint32_t s, uint32_t same, u
 }
 
 // ======================================================== shared epilogue
-// Record a finished replica: levels, histograms, family.
+// 128-bit unsigned accumulation (lo, hi) with an explicit carry: integer
+// addition is associative, so the total does not depend on the order.
+__device__ __forceinline__ void atomic_add_u128(unsigned long long* lohi, unsigned long long lo,
+                                                unsigned long long hi)
+{
+    const unsigned long long old = atomicAdd(&lohi[0], lo);
+    if (old + lo < old) hi += 1ull;
+    if (hi) atomicAdd(&lohi[1], hi);
+}
+
+// Record a finished replica: levels, histograms, family, and the per-level
+// magnetisation sums used to reweight magnetisations (Sec. 2.4).
 __device__ __forceinline__ void record_replica(const RunDev& r, int nxt, long long k, unsigned anti, unsigned ups,
                                                uint32_t family)
 {
@@ -128,6 +139,14 @@ __device__ __forceinline__ void record_replica(const RunDev& r, int nxt, long lo
     r.fam[nxt][k] = family;
     atomicAdd(&r.H[nxt][kl], 1u);
     atomicAdd(&r.H[nxt][r.N + 1 + ups], 1u);
+    const long long M = 2ll * (long long)ups - r.N;
+    const unsigned long long aM = (unsigned long long)(M < 0 ? -M : M);
+    const unsigned long long M2 = aM * aM;
+    const unsigned __int128 M4 = (unsigned __int128)M2 * M2;
+    unsigned long long* ms = r.Msum + 5 * (size_t)kl;
+    atomicAdd(&ms[0], aM);
+    atomic_add_u128(ms + 1, M2, 0ull);
+    atomic_add_u128(ms + 3, (unsigned long long)M4, (unsigned long long)(M4 >> 64));
 }
 
 template <int G>

@@ -158,8 +158,15 @@ def test_adaptive_parity(L, fmt):
     m_ref = pa.mhr(betas)
     m_got = run.mhr(betas)
     for a, b in zip(m_got, m_ref):
-        for f in ("e", "C", "betaF_per_N", "S_per_N"):
+        for f in ("e", "C", "betaF_per_N", "S_per_N", "abs_m", "m2", "m4"):
             assert math.isclose(float(a[f]), b[f], rel_tol=1e-11, abs_tol=1e-13), f
+    # the exact integer sums behind the magnetisation reweighting
+    ms = run.mag_sums()
+    for k in range(L * L + 1):
+        a, m2, m4 = pa.Msums[k]
+        assert int(ms[k, 0]) == a
+        assert int(ms[k, 1]) + (int(ms[k, 2]) << 64) == m2
+        assert int(ms[k, 3]) + (int(ms[k, 4]) << 64) == m4
     run.close()
 
 

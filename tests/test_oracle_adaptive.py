@@ -87,3 +87,26 @@ def test_mhr_dos_4x4_vs_enumeration():
             assert math.exp(lno[k]) == pytest.approx(dos[e], rel=0.08), e
             checked += 1
     assert checked >= 5
+
+
+def test_mhr_magnetisation_4x4_vs_enumeration():
+    """Sec. 2.4 notes that reweighting extends to magnetisations: <|m|>,
+    <m^2>, <m^4> from the per-level sums agree with enumeration."""
+    pa = PopulationAnnealing(4, 4000, 10, beta_f=1.0, dbeta=0.0, seed=19)
+    pa.run()
+    bf = BruteForce(4)
+    for b in (0.2, 0.4, 0.6, 0.9):
+        row = pa.mhr([b])[0]
+        ex = bf.averages(b)
+        for f in ("abs_m", "m2", "m4"):
+            assert row[f] == pytest.approx(ex[f], abs=0.02), (b, f, row[f], ex[f])
+
+
+def test_mhr_magnetisation_sums_are_consistent(run8):
+    N = run8.N
+    for k in range(N + 1):
+        c = int(run8.Hsum[k])
+        a, m2, m4 = run8.Msums[k]
+        assert 0 <= a <= N * c and 0 <= m2 <= N * N * c and 0 <= m4 <= N ** 4 * c
+        assert a * a <= m2 * c  # Cauchy-Schwarz
+        assert m2 * m2 <= m4 * c
