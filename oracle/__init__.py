@@ -9,8 +9,9 @@ shares no code with it.
 
 Modules
 -------
-pa_oracle_core.c : Philox4x32-10, initial spins, Metropolis sweeps,
-                   measurement and the resampling uniforms (natural layout).
+pa_oracle_core.c : Philox4x32-10, initial spins, Metropolis sweeps (also
+                   the multi-spin-coded LCG variant), measurement and the
+                   resampling uniforms (natural layout).
 pa_oracle.py     : the population-annealing step logic (Sec. 2.1-2.4).
 exact_ising.py   : exact 2D Ising references that pin the oracle.
 """
@@ -55,10 +56,11 @@ def core() -> ctypes.CDLL:
             lib.oracle_sweep.argtypes = [ctypes.c_int, ctypes.c_int64, i64p, ctypes.c_uint64,
                                          ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
                                          ctypes.c_uint64, i8p]
+            lib.oracle_sweep_msc.argtypes = lib.oracle_sweep.argtypes
             lib.oracle_measure.argtypes = [ctypes.c_int, ctypes.c_int64, i8p, i64p, i64p]
             lib.oracle_resample_words.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, u32p]
             lib.oracle_philox_many.argtypes = [ctypes.c_int64, u32p, ctypes.c_uint64, u32p]
-            for f in (lib.oracle_philox4x32_10, lib.oracle_init, lib.oracle_sweep,
+            for f in (lib.oracle_philox4x32_10, lib.oracle_init, lib.oracle_sweep, lib.oracle_sweep_msc,
                       lib.oracle_measure, lib.oracle_resample_words, lib.oracle_philox_many):
                 f.restype = None
             _lib = lib

@@ -85,14 +85,16 @@ def init_spins(L: int, slots: np.ndarray, seed: int) -> np.ndarray:
     return s
 
 
-def sweep(s: np.ndarray, slots: np.ndarray, seed: int, u0: int, theta: int, T4: int, T8: int) -> None:
-    """theta sweeps in place on s[r] (replica slot slots[r])."""
+def sweep(s: np.ndarray, slots: np.ndarray, seed: int, u0: int, theta: int, T4: int, T8: int,
+          msc: bool = False) -> None:
+    """theta sweeps in place on s[r] (replica slot slots[r]); msc selects the
+    multi-spin-coded random numbers (Philox-seeded LCG per 32 replicas)."""
     import ctypes
     assert s.dtype == np.int8 and s.flags.c_contiguous
     slots = np.ascontiguousarray(slots, dtype=np.int64)
     L = s.shape[1]
-    core().oracle_sweep(L, slots.size, _ptr(slots, ctypes.c_int64), seed, u0, theta, T4, T8,
-                        _ptr(s, ctypes.c_int8))
+    fn = core().oracle_sweep_msc if msc else core().oracle_sweep
+    fn(L, slots.size, _ptr(slots, ctypes.c_int64), seed, u0, theta, T4, T8, _ptr(s, ctypes.c_int8))
 
 
 def measure(s: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
@@ -257,7 +259,7 @@ class PopulationAnnealing:
 
     def __init__(self, L: int, R: int, theta: int, beta_f: float = 1.0, dbeta: float = 0.01,
                  seed: int = 1, beta0: float = 0.0, overlap: float = 0.85,
-                 capacity: int = 0, record_hist: bool = True, schedule=None):
+                 capacity: int = 0, record_hist: bool = True, schedule=None, msc: bool = False):
         if L < 4 or L % 2:
             raise ValueError("L must be even and >= 4")
         if beta0 != 0.0:
@@ -281,6 +283,7 @@ class PopulationAnnealing:
         else:
             self.n_fixed = int(math.floor((self.beta_f - beta0) / self.dbeta + 0.5)) if not self.adaptive else None
         self.record_hist = record_hist
+        self.msc = bool(msc)  # multi-spin-coded sweeps (Sec. 4, LCG variant)
         self.step_index = 0
         self.beta = 0.0
         self.done = False
@@ -381,7 +384,7 @@ class PopulationAnnealing:
                 sample = sample(R_new)
             sample = np.asarray(sample, dtype=np.int64)
             sub = np.ascontiguousarray(self.pop[parent[sample]])
-            sweep(sub, sample, self.seed, u0, self.theta, T4, T8)
+            sweep(sub, sample, self.seed, u0, self.theta, T4, T8, msc=self.msc)
             rec.sample = sample
             rec.sample_pop = sub
             rec.sample_E, rec.sample_M = measure(sub)
@@ -391,7 +394,7 @@ class PopulationAnnealing:
             return rec
         self.pop = np.ascontiguousarray(self.pop[parent])
         self.fam = self.fam[parent]
-        sweep(self.pop, np.arange(R_new, dtype=np.int64), self.seed, u0, self.theta, T4, T8)
+        sweep(self.pop, np.arange(R_new, dtype=np.int64), self.seed, u0, self.theta, T4, T8, msc=self.msc)
         self.E, self.M = measure(self.pop)
         self.step_index = i
         self.beta = beta_new

@@ -28,6 +28,7 @@
  *   INIT     (tag 0): g = c*N/2 + b,  ctr = (0, g>>2, 0, k),        x = out[g&3]
  *   SWEEP    (tag 1): ctr = (2u + c, b>>2, 1, k),                   x = out[b&3]
  *   RESAMPLE (tag 2): ctr = (i, j>>2, 2, 0),                        x = out[j&3]
+ *   MSC seed (tag 5): ctr = (2u + c, b>>2, 5, k/32),               x = out[b&3]
  * where c = (x+y)&1 is the checkerboard colour of site (x, y),
  * b = y*(L/2) + (x>>1) its index within the colour, k the replica slot,
  * u the global sweep number, i the temperature step and j the old slot.
@@ -131,6 +132,63 @@ void oracle_sweep(int L, int64_t n, const int64_t *slot, uint64_t seed, int64_t 
                         } else {
                             uint32_t b = (uint32_t)(y * half + (x >> 1));
                             uint32_t w = stream_word(seed, 2u * u + (uint32_t)c, b >> 2, 1u, k, b & 3u);
+                            uint64_t T = (aligned == 3) ? T4 : T8;
+                            flip = ((uint64_t)w < T);
+                        }
+                        if (flip)
+                            S[y * L + x] = (int8_t)(-si);
+                    }
+            }
+        }
+    }
+}
+
+/*
+ * Multi-spin-coded variant (Sec. 4): replicas are grouped 32 per machine
+ * word (replica k is bit k%32 of group k/32) and, as in the paper's LCG
+ * variant, one Philox word per (group, site, sweep, colour) seeds a linear
+ * congruential generator r_{n+1} = A r_n + C mod 2^32 with A = 1664525 and
+ * C = 1013904223 that supplies the 32 replicas' random numbers: replica bit
+ * j uses r_{j+1}, r_0 being the seed. The seed is the MSC stream word
+ * (tag 5): ctr = (2u + c, b>>2, 5, k/32), x = out[b&3]. Everything else
+ * (acceptance rule, thresholds, colour order) is as in oracle_sweep.
+ */
+#define LCG_A 1664525u
+#define LCG_C 1013904223u
+
+static uint32_t msc_word(uint64_t seed, uint32_t u, uint32_t c, uint32_t b, uint32_t k)
+{
+    uint32_t r = stream_word(seed, 2u * u + c, b >> 2, 5u, k >> 5, b & 3u);
+    for (uint32_t j = 0; j <= (k & 31u); j++)
+        r = LCG_A * r + LCG_C;
+    return r;
+}
+
+void oracle_sweep_msc(int L, int64_t n, const int64_t *slot, uint64_t seed, int64_t u0,
+                      int theta, uint64_t T4, uint64_t T8, int8_t *s)
+{
+    const int N = L * L, half = L / 2;
+    for (int64_t r = 0; r < n; r++) {
+        int8_t *S = s + (size_t)r * N;
+        uint32_t k = (uint32_t)slot[r];
+        for (int sw = 0; sw < theta; sw++) {
+            uint32_t u = (uint32_t)(u0 + sw);
+            for (int c = 0; c < 2; c++) {
+                for (int y = 0; y < L; y++)
+                    for (int x = 0; x < L; x++) {
+                        if (((x + y) & 1) != c)
+                            continue;
+                        int si = S[y * L + x];
+                        int aligned = (S[y * L + (x + 1) % L] == si) +
+                                      (S[y * L + (x + L - 1) % L] == si) +
+                                      (S[((y + 1) % L) * L + x] == si) +
+                                      (S[((y + L - 1) % L) * L + x] == si);
+                        int flip;
+                        if (aligned <= 2) {
+                            flip = 1;
+                        } else {
+                            uint32_t b = (uint32_t)(y * half + (x >> 1));
+                            uint32_t w = msc_word(seed, u, (uint32_t)c, b, k);
                             uint64_t T = (aligned == 3) ? T4 : T8;
                             flip = ((uint64_t)w < T);
                         }
