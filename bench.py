@@ -243,8 +243,9 @@ def run_engine(args):
     torch.cuda.set_stream(stream)
     L, theta = WL["L"], WL["theta"]
     seed_of = lambda k: 2 + k + 100000 * rank  # noqa: E731
+    fmt = {"bits": eng.SPIN_BITS32, "msc": eng.SPIN_MSC32, "int8": eng.SPIN_INT8}[args.format]
     cfg = eng.PAConfig(L=L, R=WL["R"], theta=theta, beta_f=WL["beta_f"], dbeta=WL["dbeta"], seed=seed_of(0),
-                       spin_format=eng.SPIN_BITS32, use_graph=True, profile=args.profile)
+                       spin_format=fmt, use_graph=True, profile=args.profile)
     run = eng.PARun(cfg, stream=stream)
     n_steps = int(round(WL["beta_f"] / WL["dbeta"]))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (126 MB)
@@ -289,7 +290,7 @@ def run_engine(args):
     value = att_all / (t_max * 1e6)
 
     roofline = None
-    if args.profile:
+    if args.profile and args.format == "bits":
         pt = run.phase_times()
         sw_ms = pt["sweep"][0] - base["sweep"][0]
         sw_n = pt["sweep"][1] - base["sweep"][1]
@@ -326,7 +327,7 @@ def run_engine(args):
         for k in range(max(1, args.e2e_steps)):
             t0 = time.perf_counter()
             r2 = eng.PARun(eng.PAConfig(L=L, R=WL["R"], theta=theta, beta_f=WL["beta_f"], dbeta=WL["dbeta"],
-                                        seed=seed_of(50_000 + k), spin_format=eng.SPIN_BITS32), stream=stream)
+                                        seed=seed_of(50_000 + k), spin_format=fmt), stream=stream)
             r2.run()
             rows = r2.rows()
             r2.close()
@@ -350,7 +351,9 @@ def run_engine(args):
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": value / PAPER_K80_MSC_FLIPS_PER_NS, "dtype": "u32",
                 "data": "synthetic",
-                "config": {"workload": WORKLOAD, "seeds": "2+step (+100000*rank)", "spin_format": "bits32",
+                "config": {"workload": WORKLOAD if args.format == "bits" else WORKLOAD.replace(
+                               "bit-packed spins", f"{args.format} spins"),
+                           "seeds": "2+step (+100000*rank)", "spin_format": args.format,
                            "l2": "flushed between timed steps (256 MB write)",
                            "baseline_ref": "paper K80 multi-spin-coded run, 17 s for this workload",
                            "parallelism": f"independent runs x{ws}"},
@@ -471,6 +474,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--workload", choices=["default", "batched", "served"], default="default")
+    ap.add_argument("--format", choices=["bits", "msc", "int8"], default="bits",
+                    help="spin format of the default workload: bits (Philox per attempt, the reference contract), "
+                         "msc (the paper's multi-spin coding with a Philox-seeded LCG), int8")
     ap.add_argument("--c4-steps", type=int, default=200)
     ap.add_argument("--serve-n", type=int, default=48)
     ap.add_argument("--serve-rdiv", type=int, default=50)

@@ -49,7 +49,18 @@ typedef enum {
     PA_ESTALLED = -8      /* adaptive step found no positive step size          */
 } pa_status;
 
-typedef enum { PA_SPIN_INT8 = 0, PA_SPIN_BITS32 = 1 } pa_spin_format;
+/* PA_SPIN_INT8: one byte per spin. PA_SPIN_BITS32: 32 same-colour sites of
+ * one replica per word (synchronous multi-spin coding). Both draw one
+ * Philox4x32-10 word per attempt and give identical results.
+ * PA_SPIN_MSC32: the paper's asynchronous multi-spin coding (Sec. 4): bit j
+ * of a site's word is replica 32g + j, and the 32 replicas' random numbers
+ * come from the linear congruential generator r <- 1664525 r + 1013904223
+ * (mod 2^32) seeded per (group g, site b, sweep u, colour c) by the Philox
+ * word at counter (2u + c, b>>2, 5, g), lane b&3; replica bit j uses the
+ * (j+1)-th output. A different random-number contract (its own oracle
+ * mode); L in {4, 6, 8, 10, 12, 16, 20, 24, 32, 48, 64, 96, 128}; not in
+ * batches. */
+typedef enum { PA_SPIN_INT8 = 0, PA_SPIN_BITS32 = 1, PA_SPIN_MSC32 = 2 } pa_spin_format;
 
 typedef enum { PA_HIST_E = 0, PA_HIST_M = 1, PA_HIST_ESUM = 2 } pa_hist_kind;
 

@@ -140,13 +140,24 @@ bool bits_L_ok(int L)
     return L == 8 || L == 16 || L == 32 || L == 64 || L == 128 || L == 256 || L == 512;
 }
 
+bool msc_L_ok(int L)
+{
+    switch (L) {
+    case 4: case 6: case 8: case 10: case 12: case 16: case 20: case 24: case 32: case 48: case 64: case 96:
+    case 128: return true;
+    default: return false;
+    }
+}
+
 pa_status validate(const pa_config& c)
 {
     if (c.L < 4 || c.L > 1024 || (c.L & 1)) return PA_EINVAL;
     if (c.theta < 1 || c.R < 1 || c.R > (1ll << 31)) return PA_EINVAL;
     if (c.beta0 != 0.0) return PA_EINVAL;
     if (!(c.beta_f > 0.0) || !(c.beta_f <= 50.0)) return PA_EINVAL;
-    if (c.spin_format != PA_SPIN_INT8 && c.spin_format != PA_SPIN_BITS32) return PA_EINVAL;
+    if (c.spin_format != PA_SPIN_INT8 && c.spin_format != PA_SPIN_BITS32 && c.spin_format != PA_SPIN_MSC32)
+        return PA_EINVAL;
+    if (c.spin_format == PA_SPIN_MSC32 && !msc_L_ok(c.L)) return PA_EINVAL;
     if (c.spin_format == PA_SPIN_BITS32 && !bits_L_ok(c.L)) return PA_EINVAL;
     if (!(c.dbeta > 0.0)) {
         if (!(c.overlap > 0.0 && c.overlap < 1.0)) return PA_EINVAL;
@@ -170,6 +181,7 @@ int words_of(const pa_config& c)
 {
     const long long N = (long long)c.L * c.L;
     if (c.spin_format == PA_SPIN_BITS32) return (int)(N / 32);
+    if (c.spin_format == PA_SPIN_MSC32) return (int)N;  // per group of 32 replicas
     return (int)(((N + 15) / 16) * 4);  // bytes padded to 16, in words
 }
 
@@ -214,7 +226,7 @@ size_t footprint(const pa_config& c)
     const Sizes s = sizes_of(c);
     const size_t N1 = (size_t)s.N + 1;
     size_t b = 0;
-    b += 2 * (size_t)s.cap * s.words * 4;           // pop
+    b += 2 * (size_t)(c.spin_format == PA_SPIN_MSC32 ? (s.cap + 31) / 32 : s.cap) * s.words * 4;  // pop
     b += 2 * (size_t)s.cap * 4 * 3;                 // elev, mlev, fam
     b += (size_t)s.cap * 4 * 3;                     // parent, cnt, loc
     b += 2 * (size_t)s.ntiles * 4;                  // tile sums / offsets
@@ -741,6 +753,7 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
     h.theta = cfg->theta;
     h.fmt = cfg->spin_format;
     h.gt = cfg->group_threads ? cfg->group_threads : auto_group(*cfg);
+    if (h.fmt == PA_SPIN_MSC32) h.gt = 1;  // a warp owns 32 replicas
     if (h.fmt == PA_SPIN_BITS32 && (s.N / 64) % h.gt) return fail(PA_EINVAL);
     h.R = cfg->R;
     h.cap = s.cap;
@@ -755,8 +768,9 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
         st = dev_alloc(c, &(p), (n));             \
         if (st != PA_OK) return fail(st);         \
     } while (0)
+    const size_t pop_units = cfg->spin_format == PA_SPIN_MSC32 ? (size_t)((s.cap + 31) / 32) : (size_t)s.cap;
     for (int b = 0; b < 2; b++) {
-        PA_ALLOC(h.pop[b], (size_t)s.cap * s.words);
+        PA_ALLOC(h.pop[b], pop_units * s.words);
         PA_ALLOC(h.elev[b], (size_t)s.cap);
         PA_ALLOC(h.mlev[b], (size_t)s.cap);
         PA_ALLOC(h.fam[b], (size_t)s.cap);
@@ -1005,6 +1019,22 @@ pa_status pa_population(pa_ctx* c, int8_t* host_out, int64_t cap, int64_t* n)
     const long long R = c->recs[(size_t)last].R;
     const int L = c->cfg.L, N = c->N, half = L / 2;
     const long long m = std::min<long long>(cap, R);
+    if (c->h.fmt == PA_SPIN_MSC32) {
+        std::vector<uint32_t> buf((size_t)((m + 31) / 32) * (size_t)N);
+        if (m > 0)
+            PA_CUDA(cudaMemcpy(buf.data(), c->h.pop[last & 1], buf.size() * 4, cudaMemcpyDeviceToHost));
+        for (long long r = 0; r < m; r++) {
+            const uint32_t* w = buf.data() + (size_t)(r / 32) * N;
+            for (int y = 0; y < L; y++)
+                for (int x = 0; x < L; x++) {
+                    const int col = (x + y) & 1, b = y * half + (x >> 1);
+                    const int up = (w[col * (N / 2) + b] >> (r % 32)) & 1u;
+                    host_out[(size_t)r * N + (size_t)y * L + x] = up ? 1 : -1;
+                }
+        }
+        *n = m;
+        return PA_OK;
+    }
     std::vector<uint32_t> buf((size_t)m * c->h.words);
     if (m > 0)
         PA_CUDA(cudaMemcpy(buf.data(), c->h.pop[last & 1], buf.size() * 4, cudaMemcpyDeviceToHost));
@@ -1531,7 +1561,7 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
     for (int i = 0; i < n; i++) {
         const pa_config& c = cfgs[i];
         PA_TRY(validate(c));
-        if (!(c.dbeta > 0.0) || c.spin_format != PA_SPIN_BITS32 || c.L > 256) return PA_EINVAL;
+        if (!(c.dbeta > 0.0) || c.spin_format != PA_SPIN_BITS32 || c.L > 256) return PA_EINVAL;  // bit-packed only
         if (c.group_threads && !pa::batch_supports(c.L, c.group_threads)) return PA_EINVAL;
     }
     pa_batch* b = new (std::nothrow) pa_batch();

@@ -534,6 +534,269 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
     if (lane == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
 }
 
+
+// ======================================================== multi-spin coding
+// Asynchronous multi-spin coding (Sec. 4): replica k is bit k%32 of its
+// group's words, one word per site (plane 0 sites then plane 1, site b of a
+// plane at word b). A warp owns one group; lane j is replica 32G + j. The 32
+// replicas of a site are updated together by bit-sliced neighbour counts;
+// their random numbers come from the linear congruential generator
+// r <- A r + C (mod 2^32), A = 1664525, C = 1013904223, seeded with the
+// Philox word at counter (2u + c, b>>2, 5, G), lane b&3: replica bit j uses
+// the (j+1)-th output, computed directly as a_{j+1} seed + c_{j+1}.
+constexpr unsigned kLcgA = 1664525u, kLcgC = 1013904223u;
+constexpr unsigned kTagMsc = 5u;
+
+struct LcgJump {
+    unsigned a[33], c[33];  // r_n = a[n] r_0 + c[n]
+    constexpr LcgJump() : a(), c()
+    {
+        a[0] = 1u;
+        c[0] = 0u;
+        for (int n = 1; n <= 32; n++) {
+            a[n] = kLcgA * a[n - 1];
+            c[n] = kLcgA * c[n - 1] + kLcgC;
+        }
+    }
+};
+__constant__ LcgJump c_lcg = LcgJump();
+
+template <int L>
+struct MscGeo {
+    static constexpr int N = L * L, HALF = L / 2, NP = N / 2, QP = (NP + 3) / 4;
+};
+
+// index of the row neighbour (other plane) of site b of plane c
+template <int L>
+__device__ __forceinline__ int msc_side(int b, int c)
+{
+    constexpr int HALF = L / 2;
+    const int y = b / HALF, h = b - y * HALF;
+    const int h2 = ((c + y) & 1) ? (h + 1 == HALF ? 0 : h + 1) : (h == 0 ? HALF - 1 : h - 1);
+    return y * HALF + h2;
+}
+
+// anti-parallel bonds and up spins of replica bit `lane` of the group in smem
+template <int L>
+__device__ __forceinline__ void msc_measure(const uint32_t* sp, int lane, unsigned& anti, unsigned& ups)
+{
+    using G = MscGeo<L>;
+    const uint32_t* o = sp + G::NP;
+    anti = 0;
+    ups = 0;
+    for (int b = 0; b < G::NP; b++) {
+        const uint32_t s = sp[b];
+        const int y = b / G::HALF, h = b - y * G::HALF;
+        const int up = (y == 0 ? L - 1 : y - 1) * G::HALF + h;
+        const int dn = (y == L - 1 ? 0 : y + 1) * G::HALF + h;
+        const uint32_t x = ((s ^ o[b]) >> lane & 1u) + ((s ^ o[msc_side<L>(b, 0)]) >> lane & 1u) +
+                           ((s ^ o[up]) >> lane & 1u) + ((s ^ o[dn]) >> lane & 1u);
+        anti += x;
+        ups += (s >> lane & 1u) + (o[b] >> lane & 1u);
+    }
+}
+
+// the 32 replicas' Metropolis update of site word s with neighbour words
+__device__ __forceinline__ uint32_t msc_update(uint32_t s, uint32_t n1, uint32_t n2, uint32_t n3, uint32_t n4,
+                                               unsigned seed, uint32_t t4m1, uint32_t t8m1)
+{
+    const uint32_t d1 = s ^ n1, d2 = s ^ n2, d3 = s ^ n3, d4 = s ^ n4;
+    const uint32_t a = d1 ^ d2, bb = d1 & d2, cc = d3 ^ d4, e = d3 & d4;
+    const uint32_t ge2 = bb | e | (a & cc);
+    const uint32_t eq0 = ~(d1 | d2 | d3 | d4);
+    uint32_t acc = 0;
+#pragma unroll
+    for (int j = 0; j < 32; j++) {
+        const unsigned xj = c_lcg.a[j + 1] * seed + c_lcg.c[j + 1];
+        const uint32_t thr = ((eq0 >> j) & 1u) ? t8m1 : t4m1;
+        acc |= (uint32_t)(xj <= thr) << j;
+    }
+    return s ^ (ge2 | acc);
+}
+
+// Warps per 32-replica group: enough that each thread updates one to four
+// Philox blocks of sites per colour phase (a group is one CTA).
+template <int L>
+__host__ __device__ constexpr int msc_warps()
+{
+    constexpr int qp = MscGeo<L>::QP;
+    return qp >= 32 * 16 ? 16 : (qp >= 32 * 8 ? 8 : (qp >= 32 * 4 ? 4 : (qp >= 64 ? 2 : 1)));
+}
+
+// Persistent CTAs, one 32-replica group at a time: thread 0 takes the next
+// group; warp w handles sites w, w + W, ... when gathering and measuring
+// (lane j = replica bit j); all threads share the colour phases.
+template <int L>
+__device__ __forceinline__ unsigned msc_grab(unsigned* work, unsigned* bcast)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) *bcast = atomicAdd(work, 1u);
+    __syncthreads();
+    return *bcast;
+}
+
+// anti-parallel bonds and up spins of replica bit `lane` over this warp's sites,
+// then summed over the CTA's warps (every lane of warp 0 gets its replica's totals)
+template <int L, int W>
+__device__ __forceinline__ void msc_measure_cta(const uint32_t* sp, unsigned* red, unsigned& anti, unsigned& ups)
+{
+    using G = MscGeo<L>;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t* o = sp + G::NP;
+    unsigned a = 0, u = 0;
+    for (int b = warp; b < G::NP; b += W) {
+        const uint32_t s = sp[b];
+        const int y = b / G::HALF, h = b - y * G::HALF;
+        const int up = (y == 0 ? L - 1 : y - 1) * G::HALF + h;
+        const int dn = (y == L - 1 ? 0 : y + 1) * G::HALF + h;
+        a += ((s ^ o[b]) >> lane & 1u) + ((s ^ o[msc_side<L>(b, 0)]) >> lane & 1u) + ((s ^ o[up]) >> lane & 1u) +
+             ((s ^ o[dn]) >> lane & 1u);
+        u += (s >> lane & 1u) + (o[b] >> lane & 1u);
+    }
+    __syncthreads();
+    red[warp * 32 + lane] = a;
+    red[(W + warp) * 32 + lane] = u;
+    __syncthreads();
+    anti = 0;
+    ups = 0;
+    if (warp == 0) {
+#pragma unroll
+        for (int w = 0; w < W; w++) {
+            anti += red[w * 32 + lane];
+            ups += red[(W + w) * 32 + lane];
+        }
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(32 * msc_warps<L>()) k_init_msc(const __grid_constant__ RunDev r)
+{
+    using Gm = MscGeo<L>;
+    constexpr int W = msc_warps<L>(), N = Gm::N;
+    extern __shared__ uint32_t smem[];
+    if (*r.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* sp = smem;
+    unsigned* red = smem + N;
+    const PhiloxKey key{r.key[0], r.key[1]};
+    const long long R0 = r.R, groups = (R0 + 31) / 32;
+    for (;;) {
+        const unsigned G = msc_grab<L>(r.work, red + 2 * W * 32);
+        if ((long long)G >= groups) break;
+        const long long k = 32ll * G + lane;
+        const bool valid = k < R0;
+        // INIT stream of replica k: site g = c*N/2 + b, counter (0, g>>2, 0, k)
+        for (int gq = warp; gq < (N + 3) / 4; gq += W) {
+            const uint4 x = philox10(make_uint4(0u, (unsigned)gq, kTagInit, (unsigned)k), key);
+            const unsigned xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int l = 0; l < 4; l++) {
+                const int g = 4 * gq + l;
+                const uint32_t w = __ballot_sync(0xffffffffu, valid && xs[l] < 0x80000000u);
+                if (g < N && lane == (g & 31)) sp[g] = w;
+            }
+        }
+        __syncthreads();
+        unsigned anti, ups;
+        msc_measure_cta<L, W>(sp, red, anti, ups);
+        uint32_t* dst = r.pop[0] + (size_t)G * N;
+        for (int i = threadIdx.x; i < N; i += 32 * W) dst[i] = sp[i];
+        if (warp == 0 && valid) record_replica(r, 0, k, anti, ups, (uint32_t)k);
+    }
+}
+
+template <int L>
+__global__ void __launch_bounds__(32 * msc_warps<L>()) k_sweep_msc(const __grid_constant__ RunDev r, int step)
+{
+    using Gm = MscGeo<L>;
+    constexpr int W = msc_warps<L>(), N = Gm::N, HALF = Gm::HALF, NP = Gm::NP, QP = Gm::QP;
+    extern __shared__ uint32_t smem[];
+    if (*r.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    uint32_t* sp = smem;
+    unsigned* red = smem + N;
+    const int cur = (step - 1) & 1, nxt = step & 1;
+    const long long Ri = r.rec[step].R, groups = (Ri + 31) / 32;
+    const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
+    const PhiloxKey key{r.key[0], r.key[1]};
+    const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
+    const int theta = r.theta;
+    unsigned families = 0;
+    for (;;) {
+        const unsigned G = msc_grab<L>(r.work, red + 2 * W * 32);
+        if ((long long)G >= groups) break;
+        const long long k = 32ll * G + lane;
+        const bool valid = k < Ri;
+        // gather: bit `lane` of every site word comes from this lane's parent
+        const uint32_t p = valid ? r.parent[k] : 0u;
+        const uint32_t* src = r.pop[cur] + (size_t)(p >> 5) * N;
+        const unsigned pb = p & 31u;
+        for (int g = warp; g < N; g += W) {
+            const uint32_t w = __ballot_sync(0xffffffffu, valid && ((src[g] >> pb) & 1u));
+            if (lane == (g & 31)) sp[g] = w;
+        }
+        __syncthreads();
+        for (int sw = 0; sw < theta; sw++) {
+            const unsigned u = u0 + (unsigned)sw;
+#pragma unroll
+            for (int c = 0; c < 2; c++) {
+                uint32_t* P = sp + c * NP;
+                const uint32_t* O = sp + (1 - c) * NP;
+                for (int q = threadIdx.x; q < QP; q += 32 * W) {
+                    const uint4 x = philox10(make_uint4(2u * u + (unsigned)c, (unsigned)q, kTagMsc, G), key);
+                    const unsigned seeds[4] = {x.x, x.y, x.z, x.w};
+                    if constexpr (HALF % 4 == 0) {
+                        // the 4 sites of a Philox block share one row
+                        const int b0 = 4 * q, y = b0 / HALF, h0 = b0 - y * HALF;
+                        const int rup = (y == 0 ? L - 1 : y - 1) * HALF, rdn = (y == L - 1 ? 0 : y + 1) * HALF;
+                        const bool xodd = (c + y) & 1;
+#pragma unroll
+                        for (int l = 0; l < 4; l++) {
+                            const int h = h0 + l, b = b0 + l;
+                            const int h2 = xodd ? (h + 1 == HALF ? 0 : h + 1) : (h == 0 ? HALF - 1 : h - 1);
+                            P[b] = msc_update(P[b], O[b], O[y * HALF + h2], O[rup + h], O[rdn + h], seeds[l], t4m1,
+                                              t8m1);
+                        }
+                    } else {
+#pragma unroll
+                        for (int l = 0; l < 4; l++) {
+                            const int b = 4 * q + l;
+                            if (b < NP) {
+                                const int y = b / HALF, h = b - y * HALF;
+                                const int up = (y == 0 ? L - 1 : y - 1) * HALF + h;
+                                const int dn = (y == L - 1 ? 0 : y + 1) * HALF + h;
+                                P[b] = msc_update(P[b], O[b], O[msc_side<L>(b, c)], O[up], O[dn], seeds[l], t4m1,
+                                                  t8m1);
+                            }
+                        }
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        unsigned anti, ups;
+        msc_measure_cta<L, W>(sp, red, anti, ups);
+        uint32_t* dst = r.pop[nxt] + (size_t)G * N;
+        for (int i = threadIdx.x; i < N; i += 32 * W) dst[i] = sp[i];
+        if (warp == 0 && valid) {
+            const uint32_t f = r.fam[cur][p];
+            record_replica(r, nxt, k, anti, ups, f);
+            families += (k == 0 || r.fam[cur][r.parent[k - 1]] != f) ? 1u : 0u;
+        }
+    }
+    families = group_sum<32>(families);
+    if (lane == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
+}
+
+template <int L>
+__host__ __device__ constexpr int msc_threads()
+{
+    return 32 * msc_warps<L>();
+}
+
+// L values with a multi-spin-coded kernel
+#define PA_MSC_SIZES(X) X(4) X(6) X(8) X(10) X(12) X(16) X(20) X(24) X(32) X(48) X(64) X(96) X(128)
+
 // ======================================================== resampling kernels
 __device__ __forceinline__ int pad_pow2(int n)
 {
@@ -1031,6 +1294,15 @@ const void* bytes_ptr(bool init)
 // The init / sweep kernel of a run's (format, L, threads per replica).
 const void* sweep_kernel(const RunDev& h, bool init)
 {
+    if (h.fmt == 2) {
+        switch (h.L) {
+#define PA_MSC_PTR(LL) \
+    case LL: return init ? (const void*)k_init_msc<LL> : (const void*)k_sweep_msc<LL>;
+            PA_MSC_SIZES(PA_MSC_PTR)
+#undef PA_MSC_PTR
+        default: return nullptr;
+        }
+    }
     if (h.fmt == 1) {
         switch (h.L) {
         case 8: return bits_ptr_L<8>(h.gt, init);
@@ -1054,6 +1326,17 @@ const void* sweep_kernel(const RunDev& h, bool init)
     }
 }
 
+static int msc_threads_of(int L)
+{
+    switch (L) {
+#define PA_MSC_THR(LL) \
+    case LL: return msc_threads<LL>();
+        PA_MSC_SIZES(PA_MSC_THR)
+#undef PA_MSC_THR
+    default: return 0;
+    }
+}
+
 cudaError_t plan_sweep(const RunDev& h, Launch* ln)
 {
     int dev = 0, sms = 0, max_optin = 0, smem_sm = 0;
@@ -1068,7 +1351,12 @@ cudaError_t plan_sweep(const RunDev& h, Launch* ln)
     if (!kin || !ksw) return cudaErrorInvalidConfiguration;
     size_t smem;
     int threads;
-    if (h.gt > 32) {
+    if (h.fmt == 2) {
+        // one 32-replica group per CTA: its N site words and the reductions
+        threads = msc_threads_of(h.L);
+        if (threads <= 0) return cudaErrorInvalidConfiguration;
+        smem = ((size_t)h.N + 2 * (size_t)threads + 1) * 4u;
+    } else if (h.gt > 32) {
         // one replica per CTA of gt threads, plus reduction/broadcast words
         threads = h.gt;
         smem = ((size_t)h.words + 33) * 4u;
