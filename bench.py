@@ -243,7 +243,8 @@ def run_engine(args):
     torch.cuda.set_stream(stream)
     L, theta = WL["L"], WL["theta"]
     seed_of = lambda k: 2 + k + 100000 * rank  # noqa: E731
-    fmt = {"bits": eng.SPIN_BITS32, "msc": eng.SPIN_MSC32, "int8": eng.SPIN_INT8}[args.format]
+    fmt = {"bits": eng.SPIN_BITS32, "msc": eng.SPIN_MSC32, "int8": eng.SPIN_INT8,
+           "replica": eng.SPIN_REPLICA8}[args.format]
     cfg = eng.PAConfig(L=L, R=WL["R"], theta=theta, beta_f=WL["beta_f"], dbeta=WL["dbeta"], seed=seed_of(0),
                        spin_format=fmt, use_graph=True, profile=args.profile)
     run = eng.PARun(cfg, stream=stream)
@@ -474,7 +475,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
     ap.add_argument("--workload", choices=["default", "batched", "served"], default="default")
-    ap.add_argument("--format", choices=["bits", "msc", "int8"], default="bits",
+    ap.add_argument("--format", choices=["bits", "msc", "int8", "replica"], default="bits",
                     help="spin format of the default workload: bits (Philox per attempt, the reference contract), "
                          "msc (the paper's multi-spin coding with a Philox-seeded LCG), int8")
     ap.add_argument("--c4-steps", type=int, default=200)

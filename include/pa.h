@@ -59,8 +59,12 @@ typedef enum {
  * word at counter (2u + c, b>>2, 5, g), lane b&3; replica bit j uses the
  * (j+1)-th output. A different random-number contract (its own oracle
  * mode); L in {4, 6, 8, 10, 12, 16, 20, 24, 32, 48, 64, 96, 128}; not in
- * batches. */
-typedef enum { PA_SPIN_INT8 = 0, PA_SPIN_BITS32 = 1, PA_SPIN_MSC32 = 2 } pa_spin_format;
+ * batches.
+ * PA_SPIN_REPLICA8: the paper's replica-parallel layout (Sec. 3): one thread
+ * per replica walks the lattice, byte spins stored with the replica index
+ * fastest; the generic fallback for models without a domain decomposition.
+ * Same contract as PA_SPIN_INT8 / PA_SPIN_BITS32 (identical results). */
+typedef enum { PA_SPIN_INT8 = 0, PA_SPIN_BITS32 = 1, PA_SPIN_MSC32 = 2, PA_SPIN_REPLICA8 = 3 } pa_spin_format;
 
 typedef enum { PA_HIST_E = 0, PA_HIST_M = 1, PA_HIST_ESUM = 2 } pa_hist_kind;
 

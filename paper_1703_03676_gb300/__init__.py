@@ -16,9 +16,9 @@ import numpy as np
 from . import build as _build
 
 __all__ = ["PAConfig", "PARun", "PAError", "lib", "philox_device", "footprint_bytes",
-           "SPIN_INT8", "SPIN_BITS32", "SPIN_MSC32", "OBS_FIELDS"]
+           "SPIN_INT8", "SPIN_BITS32", "SPIN_MSC32", "SPIN_REPLICA8", "OBS_FIELDS"]
 
-SPIN_INT8, SPIN_BITS32, SPIN_MSC32 = 0, 1, 2
+SPIN_INT8, SPIN_BITS32, SPIN_MSC32, SPIN_REPLICA8 = 0, 1, 2, 3
 HIST_E, HIST_M, HIST_ESUM = 0, 1, 2
 
 _STATUS = {0: "ok", 1: "done", 2: "again", -1: "invalid argument", -2: "out of memory", -3: "capacity",

@@ -155,7 +155,8 @@ pa_status validate(const pa_config& c)
     if (c.theta < 1 || c.R < 1 || c.R > (1ll << 31)) return PA_EINVAL;
     if (c.beta0 != 0.0) return PA_EINVAL;
     if (!(c.beta_f > 0.0) || !(c.beta_f <= 50.0)) return PA_EINVAL;
-    if (c.spin_format != PA_SPIN_INT8 && c.spin_format != PA_SPIN_BITS32 && c.spin_format != PA_SPIN_MSC32)
+    if (c.spin_format != PA_SPIN_INT8 && c.spin_format != PA_SPIN_BITS32 && c.spin_format != PA_SPIN_MSC32 &&
+        c.spin_format != PA_SPIN_REPLICA8)
         return PA_EINVAL;
     if (c.spin_format == PA_SPIN_MSC32 && !msc_L_ok(c.L)) return PA_EINVAL;
     if (c.spin_format == PA_SPIN_BITS32 && !bits_L_ok(c.L)) return PA_EINVAL;
@@ -182,6 +183,7 @@ int words_of(const pa_config& c)
     const long long N = (long long)c.L * c.L;
     if (c.spin_format == PA_SPIN_BITS32) return (int)(N / 32);
     if (c.spin_format == PA_SPIN_MSC32) return (int)N;  // per group of 32 replicas
+    if (c.spin_format == PA_SPIN_REPLICA8) return 0;    // site-major bytes, sized separately
     return (int)(((N + 15) / 16) * 4);  // bytes padded to 16, in words
 }
 
@@ -226,7 +228,8 @@ size_t footprint(const pa_config& c)
     const Sizes s = sizes_of(c);
     const size_t N1 = (size_t)s.N + 1;
     size_t b = 0;
-    b += 2 * (size_t)(c.spin_format == PA_SPIN_MSC32 ? (s.cap + 31) / 32 : s.cap) * s.words * 4;  // pop
+    if (c.spin_format == PA_SPIN_REPLICA8) b += 2 * (((size_t)s.N * (size_t)s.cap + 3) / 4) * 4;
+    else b += 2 * (size_t)(c.spin_format == PA_SPIN_MSC32 ? (s.cap + 31) / 32 : s.cap) * s.words * 4;  // pop
     b += 2 * (size_t)s.cap * 4 * 3;                 // elev, mlev, fam
     b += (size_t)s.cap * 4 * 3;                     // parent, cnt, loc
     b += 2 * (size_t)s.ntiles * 4;                  // tile sums / offsets
@@ -753,7 +756,7 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
     h.theta = cfg->theta;
     h.fmt = cfg->spin_format;
     h.gt = cfg->group_threads ? cfg->group_threads : auto_group(*cfg);
-    if (h.fmt == PA_SPIN_MSC32) h.gt = 1;  // a warp owns 32 replicas
+    if (h.fmt == PA_SPIN_MSC32 || h.fmt == PA_SPIN_REPLICA8) h.gt = 1;  // not thread groups
     if (h.fmt == PA_SPIN_BITS32 && (s.N / 64) % h.gt) return fail(PA_EINVAL);
     h.R = cfg->R;
     h.cap = s.cap;
@@ -768,9 +771,12 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
         st = dev_alloc(c, &(p), (n));             \
         if (st != PA_OK) return fail(st);         \
     } while (0)
-    const size_t pop_units = cfg->spin_format == PA_SPIN_MSC32 ? (size_t)((s.cap + 31) / 32) : (size_t)s.cap;
+    const size_t pop_words = cfg->spin_format == PA_SPIN_REPLICA8
+                                 ? ((size_t)s.N * (size_t)s.cap + 3) / 4
+                                 : (cfg->spin_format == PA_SPIN_MSC32 ? (size_t)((s.cap + 31) / 32) : (size_t)s.cap) *
+                                       (size_t)s.words;
     for (int b = 0; b < 2; b++) {
-        PA_ALLOC(h.pop[b], pop_units * s.words);
+        PA_ALLOC(h.pop[b], pop_words);
         PA_ALLOC(h.elev[b], (size_t)s.cap);
         PA_ALLOC(h.mlev[b], (size_t)s.cap);
         PA_ALLOC(h.fam[b], (size_t)s.cap);
@@ -1019,6 +1025,20 @@ pa_status pa_population(pa_ctx* c, int8_t* host_out, int64_t cap, int64_t* n)
     const long long R = c->recs[(size_t)last].R;
     const int L = c->cfg.L, N = c->N, half = L / 2;
     const long long m = std::min<long long>(cap, R);
+    if (c->h.fmt == PA_SPIN_REPLICA8) {
+        const size_t rc = (size_t)c->h.cap;
+        std::vector<uint8_t> buf((size_t)N * rc);
+        if (m > 0) PA_CUDA(cudaMemcpy(buf.data(), c->h.pop[last & 1], buf.size(), cudaMemcpyDeviceToHost));
+        for (long long r = 0; r < m; r++)
+            for (int y = 0; y < L; y++)
+                for (int x = 0; x < L; x++) {
+                    const int col = (x + y) & 1, b = y * half + (x >> 1);
+                    const int up = buf[(size_t)(col * (N / 2) + b) * rc + (size_t)r];
+                    host_out[(size_t)r * N + (size_t)y * L + x] = up ? 1 : -1;
+                }
+        *n = m;
+        return PA_OK;
+    }
     if (c->h.fmt == PA_SPIN_MSC32) {
         std::vector<uint32_t> buf((size_t)((m + 31) / 32) * (size_t)N);
         if (m > 0)

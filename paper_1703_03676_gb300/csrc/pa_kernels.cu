@@ -535,6 +535,107 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
 }
 
 
+
+// ======================================================== replica-parallel
+// The paper's generic fallback (Sec. 3 "Spin updates"): one thread per
+// replica walks its lattice site by site; byte spins stored with the replica
+// index fastest (site g of replica k at byte g * cap + k, g = c*N/2 + b), so
+// the threads of a warp touch consecutive bytes. Same random-number contract
+// as the other single-spin formats (one Philox word per attempt).
+__device__ __forceinline__ void rp_measure(const uint8_t* col, size_t cap, int L, unsigned& anti, unsigned& ups)
+{
+    const int half = L / 2, NP = L * L / 2;
+    anti = 0;
+    ups = 0;
+    for (int b = 0; b < NP; b++) {
+        const int s = col[(size_t)b * cap];
+        const int y = b / half, h = b - y * half;
+        const int up = (y == 0 ? L - 1 : y - 1) * half + h;
+        const int dn = (y == L - 1 ? 0 : y + 1) * half + h;
+        const uint8_t* o = col + (size_t)NP * cap;
+        anti += (unsigned)((o[(size_t)b * cap] != s) + (o[(size_t)nb_index_side(b, 0, L, half) * cap] != s) +
+                           (o[(size_t)up * cap] != s) + (o[(size_t)dn * cap] != s));
+        ups += (unsigned)(s + o[(size_t)b * cap]);
+    }
+}
+
+__global__ void __launch_bounds__(256) k_init_rp(const __grid_constant__ RunDev r)
+{
+    if (*r.status) return;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= r.R) return;
+    const size_t cap = (size_t)r.cap;
+    uint8_t* col = reinterpret_cast<uint8_t*>(r.pop[0]) + k;
+    const PhiloxKey key{r.key[0], r.key[1]};
+    const int N = r.N;
+    for (int gq = 0; gq < (N + 3) / 4; gq++) {
+        const uint4 x = philox10(make_uint4(0u, (unsigned)gq, kTagInit, (unsigned)k), key);
+        const unsigned xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+        for (int l = 0; l < 4; l++) {
+            const int g = 4 * gq + l;
+            if (g < N) col[(size_t)g * cap] = (uint8_t)(xs[l] < 0x80000000u);
+        }
+    }
+    unsigned anti, ups;
+    rp_measure(col, cap, r.L, anti, ups);
+    record_replica(r, 0, k, anti, ups, (uint32_t)k);
+}
+
+__global__ void __launch_bounds__(256) k_sweep_rp(const __grid_constant__ RunDev r, int step)
+{
+    if (*r.status) return;
+    const long long Ri = r.rec[step].R;
+    const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned families = 0;
+    if (k < Ri) {
+        const int cur = (step - 1) & 1, nxt = step & 1;
+        const size_t cap = (size_t)r.cap;
+        const int L = r.L, N = r.N, half = L / 2, NP = N / 2, QP = (NP + 3) / 4;
+        const uint32_t p = r.parent[k];
+        const uint8_t* src = reinterpret_cast<const uint8_t*>(r.pop[cur]) + p;
+        uint8_t* col = reinterpret_cast<uint8_t*>(r.pop[nxt]) + k;
+        for (int g = 0; g < N; g++) col[(size_t)g * cap] = src[(size_t)g * cap];
+        const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
+        const PhiloxKey key{r.key[0], r.key[1]};
+        const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
+        for (int sw = 0; sw < r.theta; sw++) {
+            const unsigned u = u0 + (unsigned)sw;
+            for (int c = 0; c < 2; c++) {
+                uint8_t* P = col + (size_t)c * NP * cap;
+                const uint8_t* O = col + (size_t)(1 - c) * NP * cap;
+                for (int q = 0; q < QP; q++) {
+                    const uint4 x = philox10(make_uint4(2u * u + (unsigned)c, (unsigned)q, kTagSweep, (unsigned)k), key);
+                    const unsigned xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                    for (int l = 0; l < 4; l++) {
+                        const int b = 4 * q + l;
+                        if (b < NP) {
+                            const int s = P[(size_t)b * cap];
+                            const int y = b / half, h = b - y * half;
+                            const int up = (y == 0 ? L - 1 : y - 1) * half + h;
+                            const int dn = (y == L - 1 ? 0 : y + 1) * half + h;
+                            const int n = (O[(size_t)b * cap] == s) + (O[(size_t)nb_index_side(b, c, L, half) * cap] == s) +
+                                          (O[(size_t)up * cap] == s) + (O[(size_t)dn * cap] == s);
+                            bool flip = n <= 2;
+                            if (n == 3) flip = xs[l] <= t4m1;
+                            if (n == 4) flip = xs[l] <= t8m1;
+                            if (flip) P[(size_t)b * cap] = (uint8_t)(s ^ 1);
+                        }
+                    }
+                }
+            }
+        }
+        unsigned anti, ups;
+        rp_measure(col, cap, L, anti, ups);
+        const uint32_t f = r.fam[cur][p];
+        record_replica(r, nxt, k, anti, ups, f);
+        families = (k == 0 || r.fam[cur][r.parent[k - 1]] != f) ? 1u : 0u;
+    }
+    families = group_sum<32>(families);
+    if ((threadIdx.x & 31) == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
+}
+
 // ======================================================== multi-spin coding
 // Asynchronous multi-spin coding (Sec. 4): replica k is bit k%32 of its
 // group's words, one word per site (plane 0 sites then plane 1, site b of a
@@ -1294,6 +1395,7 @@ const void* bytes_ptr(bool init)
 // The init / sweep kernel of a run's (format, L, threads per replica).
 const void* sweep_kernel(const RunDev& h, bool init)
 {
+    if (h.fmt == 3) return init ? (const void*)k_init_rp : (const void*)k_sweep_rp;
     if (h.fmt == 2) {
         switch (h.L) {
 #define PA_MSC_PTR(LL) \
@@ -1351,6 +1453,14 @@ cudaError_t plan_sweep(const RunDev& h, Launch* ln)
     if (!kin || !ksw) return cudaErrorInvalidConfiguration;
     size_t smem;
     int threads;
+    if (h.fmt == 3) {
+        // one thread per replica over the whole capacity, no shared memory
+        ln->sweep_threads = 256;
+        ln->sweep_smem = 0;
+        ln->sweep_blocks = (int)((h.cap + 255) / 256);
+        ln->count_blocks = h.ntiles;
+        return cudaSuccess;
+    }
     if (h.fmt == 2) {
         // one 32-replica group per CTA: its N site words and the reductions
         threads = msc_threads_of(h.L);

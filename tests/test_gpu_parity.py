@@ -23,7 +23,7 @@ if not torch.cuda.is_available():
 
 import paper_1703_03676_gb300 as eng  # noqa: E402
 
-I8, B32 = eng.SPIN_INT8, eng.SPIN_BITS32
+I8, B32, RP = eng.SPIN_INT8, eng.SPIN_BITS32, eng.SPIN_REPLICA8
 
 
 def engine_run(L, R, theta, beta_f, dbeta, seed, fmt, **kw):
@@ -56,6 +56,8 @@ CASES = [
     ("L256-bits", 256, 64, 1, 0.5, 0.25, 13, B32),
     ("L512-bits", 512, 16, 1, 1.0, 0.5, 14, B32),
     ("L10-int8", 10, 1100, 2, 0.4, 0.1, 15, I8),
+    ("L6-replica-parallel", 6, 700, 2, 0.4, 0.1, 17, RP),
+    ("L16-replica-parallel-ragged", 16, 1300, 3, 0.3, 0.05, 18, RP),
 ]
 
 CTA_CASES = [
