@@ -221,6 +221,20 @@ pa_status pa_phase_times(pa_ctx *ctx, double ms[7], int64_t launches[7]);
  * persistent CTAs). */
 pa_status pa_launch_shape(pa_ctx *ctx, int32_t *group_threads, int32_t *block_threads, int32_t *grid_blocks);
 
+/* Checkpoint at the current step boundary (Sec. 2.1 steps are independent
+ * given the population: the random numbers are counter-based). Writes the
+ * configuration, the host schedule and records, and the device state
+ * (population, levels, families, current histograms, running sums) into
+ * host_buf; *used gets the byte count. host_buf == NULL only reports the
+ * size. Synchronises. PA_EINVAL if cap is too small. */
+pa_status pa_checkpoint(pa_ctx *ctx, void *host_buf, size_t cap, size_t *used);
+
+/* Resume from a checkpoint into a context created with the same
+ * configuration (the seed, use_graph and profile may differ; the seed of
+ * the checkpoint is used). Later steps are bit-identical to an
+ * uninterrupted run. PA_EINVAL if the checkpoint does not match. */
+pa_status pa_restore(pa_ctx *ctx, const void *host_buf, size_t n);
+
 /* Device bytes a run with this configuration allocates (admission). */
 size_t pa_footprint_bytes(const pa_config *cfg);
 

@@ -103,6 +103,8 @@ SIGNATURES = [
                                       ctypes.POINTER(ctypes.c_int32)]),
     ("pa_batch_destroy", None, [_P]),
     ("pa_step_async", ctypes.c_int, [_P]),
+    ("pa_checkpoint", ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
+    ("pa_restore", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
     ("pa_create_scheduled", ctypes.c_int, [ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                            _P, ctypes.POINTER(_P)]),
     ("pa_weighted_average", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P]),
@@ -309,6 +311,20 @@ class PARun:
         _check(self._lib.pa_ln_dos(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size),
                "pa_ln_dos")
         return out
+
+    def checkpoint(self) -> bytes:
+        """Snapshot of the run at the current step boundary (pa_checkpoint)."""
+        n = ctypes.c_size_t()
+        _check(self._lib.pa_checkpoint(self._h, None, 0, ctypes.byref(n)), "pa_checkpoint")
+        buf = ctypes.create_string_buffer(n.value)
+        _check(self._lib.pa_checkpoint(self._h, buf, n.value, ctypes.byref(n)), "pa_checkpoint")
+        return buf.raw[: n.value]
+
+    def restore(self, blob: bytes):
+        """Resume from a checkpoint of a run with the same configuration."""
+        buf = ctypes.create_string_buffer(blob, len(blob))
+        _check(self._lib.pa_restore(self._h, buf, len(blob)), "pa_restore")
+        return self
 
     def mag_sums(self) -> np.ndarray:
         """Per-level sums (N+1, 5) uint64: |M|, M^2 lo/hi, M^4 lo/hi."""

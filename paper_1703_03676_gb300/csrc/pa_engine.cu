@@ -1839,3 +1839,181 @@ extern "C" pa_status pa_serve(const pa_request* reqs, int32_t n, const pa_serve_
     }
     return PA_OK;
 }
+
+// ================================================================ checkpoint
+// A step boundary is the whole state of a run: the random numbers are
+// counter-based, so the population, its levels and families, the
+// histograms, the per-step records and the host schedule determine every
+// later step. Layout: header, host vectors, then device arrays.
+namespace {
+constexpr uint64_t kCkptMagic = 0x3130334247415041ull;  // "PAGB3001"
+
+struct CkptHeader {
+    uint64_t magic;
+    uint32_t version, config_bytes;
+    pa_config cfg;
+    int64_t step, R, n_betas, n_T, n_sched, hist_steps_saved;
+    int32_t done, N;
+};
+
+size_t pop_bytes_of(const pa_ctx* c, long long R)
+{
+    switch (c->h.fmt) {
+    case PA_SPIN_MSC32: return (size_t)((R + 31) / 32) * (size_t)c->N * 4;
+    case PA_SPIN_REPLICA8: return (((size_t)c->N * (size_t)c->h.cap + 3) / 4) * 4;
+    default: return (size_t)R * (size_t)c->h.words * 4;
+    }
+}
+
+struct Writer {
+    char* p;
+    size_t cap, used;
+    bool ok;
+    void put(const void* src, size_t n)
+    {
+        if (p && used + n <= cap) std::memcpy(p + used, src, n);
+        else if (p) ok = false;
+        used += n;
+    }
+};
+}  // namespace
+
+extern "C" pa_status pa_checkpoint(pa_ctx* c, void* host_buf, size_t cap, size_t* used)
+{
+    if (!c || !used) return PA_EINVAL;
+    if (c->in_batch) return PA_ESTATE;
+    PA_TRY(pull_records(c));
+    const long long i = c->enq_step;
+    if (c->done_rows != i + 1) return PA_ESTATE;
+    const StepDev& last = c->recs[(size_t)i];
+    const long long R = last.R;
+    const size_t N1 = (size_t)c->N + 1;
+    const long long hs = c->h.hist_rec ? std::min<long long>(i + 1, c->hist_steps) : 0;
+    CkptHeader hd{};
+    hd.magic = kCkptMagic;
+    hd.version = 1;
+    hd.config_bytes = sizeof(pa_config);
+    hd.cfg = c->cfg;
+    hd.step = i;
+    hd.R = R;
+    hd.n_betas = (int64_t)c->betas.size();
+    hd.n_T = (int64_t)c->T4.size();
+    hd.n_sched = (int64_t)c->sched.size();
+    hd.hist_steps_saved = hs;
+    hd.done = c->done ? 1 : 0;
+    hd.N = c->N;
+    Writer w{(char*)host_buf, host_buf ? cap : 0, 0, true};
+    w.put(&hd, sizeof(hd));
+    w.put(c->betas.data(), 8 * c->betas.size());
+    w.put(c->deltas.data(), 8 * c->deltas.size());
+    w.put(c->T4.data(), 8 * c->T4.size());
+    w.put(c->T8.data(), 8 * c->T8.size());
+    w.put(c->sched.data(), 8 * c->sched.size());
+    w.put(c->recs.data(), sizeof(StepDev) * (size_t)(i + 1));
+    const int cur = (int)(i & 1);
+    struct Dev {
+        const void* src;
+        size_t bytes;
+    };
+    const Dev devs[] = {
+        {c->h.pop[cur], pop_bytes_of(c, R)},
+        {c->h.elev[cur], 4 * (size_t)R},
+        {c->h.mlev[cur], 4 * (size_t)R},
+        {c->h.fam[cur], 4 * (size_t)R},
+        {c->h.H[cur], 8 * N1},
+        {c->h.Hsum, 8 * N1},
+        {c->h.Msum, 40 * N1},
+        {c->h.hist_rec, 8 * N1 * (size_t)hs},
+    };
+    for (const Dev& d : devs) {
+        if (!d.bytes) continue;
+        if (w.p && w.used + d.bytes <= w.cap) {
+            PA_CUDA(cudaMemcpy(w.p + w.used, d.src, d.bytes, cudaMemcpyDeviceToHost));
+        } else if (w.p) {
+            w.ok = false;
+        }
+        w.used += d.bytes;
+    }
+    *used = w.used;
+    if (host_buf && !w.ok) return PA_EINVAL;
+    return PA_OK;
+}
+
+extern "C" pa_status pa_restore(pa_ctx* c, const void* host_buf, size_t n)
+{
+    if (!c || !host_buf || n < sizeof(CkptHeader)) return PA_EINVAL;
+    if (c->in_batch) return PA_ESTATE;
+    CkptHeader hd;
+    std::memcpy(&hd, host_buf, sizeof(hd));
+    if (hd.magic != kCkptMagic || hd.version != 1 || hd.config_bytes != sizeof(pa_config) || hd.N != c->N)
+        return PA_EINVAL;
+    pa_config a = hd.cfg, b = c->cfg;
+    a.seed = b.seed = 0;  // the seed travels with the checkpoint
+    a.use_graph = b.use_graph = 0;
+    a.profile = b.profile = 0;
+    if (std::memcmp(&a, &b, sizeof(a)) != 0) return PA_EINVAL;
+    if (hd.step < 0 || hd.step > c->max_steps || hd.R < 1 || hd.R > c->h.cap) return PA_EINVAL;
+    const long long i = hd.step, R = hd.R;
+    const size_t N1 = (size_t)c->N + 1;
+    const char* p = (const char*)host_buf + sizeof(hd);
+    const char* end = (const char*)host_buf + n;
+    auto take = [&](size_t bytes) -> const char* {
+        if ((size_t)(end - p) < bytes) return nullptr;
+        const char* q = p;
+        p += bytes;
+        return q;
+    };
+    const char* pb = take(8 * (size_t)hd.n_betas);
+    const char* pd = take(8 * (size_t)hd.n_betas);
+    const char* p4 = take(8 * (size_t)hd.n_T);
+    const char* p8 = take(8 * (size_t)hd.n_T);
+    const char* ps = take(8 * (size_t)hd.n_sched);
+    const char* pr = take(sizeof(StepDev) * (size_t)(i + 1));
+    if (!pb || !pd || !p4 || !p8 || !ps || !pr) return PA_EINVAL;
+    // device state of population i
+    PA_CUDA(cudaStreamSynchronize(c->stream));
+    const int cur = (int)(i & 1);
+    struct Dev {
+        void* dst;
+        size_t bytes;
+    };
+    const long long hs = c->h.hist_rec ? std::min<long long>(hd.hist_steps_saved, c->hist_steps) : 0;
+    if (hd.hist_steps_saved != hs) return PA_EINVAL;
+    const Dev devs[] = {
+        {c->h.pop[cur], pop_bytes_of(c, R)},
+        {c->h.elev[cur], 4 * (size_t)R},
+        {c->h.mlev[cur], 4 * (size_t)R},
+        {c->h.fam[cur], 4 * (size_t)R},
+        {c->h.H[cur], 8 * N1},
+        {c->h.Hsum, 8 * N1},
+        {c->h.Msum, 40 * N1},
+        {c->h.hist_rec, 8 * N1 * (size_t)hs},
+    };
+    for (const Dev& d : devs) {
+        if (!d.bytes) continue;
+        const char* src = take(d.bytes);
+        if (!src) return PA_EINVAL;
+        PA_CUDA(cudaMemcpy(d.dst, src, d.bytes, cudaMemcpyHostToDevice));
+    }
+    // records of steps 0..i; later ones cleared
+    PA_CUDA(cudaMemset(c->h.rec, 0, sizeof(StepDev) * (size_t)(c->max_steps + 1)));
+    PA_CUDA(cudaMemcpy(c->h.rec, pr, sizeof(StepDev) * (size_t)(i + 1), cudaMemcpyHostToDevice));
+    PA_CUDA(cudaMemset(c->h.status, 0, 16));
+    PA_CUDA(cudaMemset(c->h.work, 0, 16));
+    const unsigned key[2] = {(unsigned)(hd.cfg.seed & 0xffffffffu), (unsigned)(hd.cfg.seed >> 32)};
+    PA_CUDA(cudaMemcpy(c->d_key, key, 8, cudaMemcpyHostToDevice));
+    // host state
+    c->cfg.seed = hd.cfg.seed;
+    c->betas.assign((const double*)pb, (const double*)pb + hd.n_betas);
+    c->deltas.assign((const double*)pd, (const double*)pd + hd.n_betas);
+    c->T4.assign((const uint64_t*)p4, (const uint64_t*)p4 + hd.n_T);
+    c->T8.assign((const uint64_t*)p8, (const uint64_t*)p8 + hd.n_T);
+    c->sched.assign((const double*)ps, (const double*)ps + hd.n_sched);
+    c->recs.assign((const StepDev*)pr, (const StepDev*)pr + (i + 1));
+    c->done_rows = i + 1;
+    c->enq_step = i;
+    c->done = hd.done != 0;
+    c->failed = PA_OK;
+    if (c->adaptive && !c->done) PA_TRY(enqueue_readback(c));
+    return PA_OK;
+}
