@@ -192,6 +192,11 @@ pa_status pa_histogram(pa_ctx *ctx, int64_t step, int32_t kind, int64_t *out, in
  * for replica slot r < *n (cap is in replicas). */
 pa_status pa_population(pa_ctx *ctx, int8_t *host_out, int64_t cap, int64_t *n);
 
+/* 64-bit FNV-1a hash of the current population in the layout of
+ * pa_population (one byte per spin, 0x01 for +1 and 0xff for -1, replica
+ * after replica): a fingerprint for parity checks. */
+pa_status pa_population_hash(pa_ctx *ctx, uint64_t *out);
+
 /* Current per-replica energies, magnetisations and family ids. */
 pa_status pa_replicas(pa_ctx *ctx, int32_t *E, int32_t *M, int64_t *family, int64_t cap, int64_t *n);
 

@@ -78,6 +78,7 @@ SIGNATURES = [
     ("pa_step_info_get", ctypes.c_int, [_P, ctypes.c_int64, ctypes.POINTER(_StepInfo)]),
     ("pa_histogram", ctypes.c_int, [_P, ctypes.c_int64, ctypes.c_int32, _I64P, ctypes.c_int64]),
     ("pa_population", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int8), ctypes.c_int64, _I64P]),
+    ("pa_population_hash", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_uint64)]),
     ("pa_replicas", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32), _I64P,
                                    ctypes.c_int64, _I64P]),
     ("pa_mhr", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int64, ctypes.POINTER(_Obs)]),
@@ -292,6 +293,12 @@ class PARun:
         _check(self._lib.pa_population(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), R,
                                        ctypes.byref(got)), "pa_population")
         return out[: got.value]
+
+    def population_hash(self) -> int:
+        """FNV-1a 64 of the current population (pa_population_hash)."""
+        h = ctypes.c_uint64()
+        _check(self._lib.pa_population_hash(self._h, ctypes.byref(h)), "pa_population_hash")
+        return h.value
 
     def replicas(self):
         """(E, M, family) of the current population."""

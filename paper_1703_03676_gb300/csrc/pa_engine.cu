@@ -2017,3 +2017,23 @@ extern "C" pa_status pa_restore(pa_ctx* c, const void* host_buf, size_t n)
     if (c->adaptive && !c->done) PA_TRY(enqueue_readback(c));
     return PA_OK;
 }
+
+// 64-bit FNV-1a over the current population in natural layout (one byte
+// per spin: 0x01 for +1, 0xff for -1, replica after replica): a compact
+// fingerprint for parity checks.
+extern "C" pa_status pa_population_hash(pa_ctx* c, uint64_t* out)
+{
+    if (!c || !out) return PA_EINVAL;
+    PA_TRY(pull_records(c));
+    const long long R = c->recs[(size_t)(c->done_rows - 1)].R;
+    std::vector<int8_t> pop((size_t)R * (size_t)c->N);
+    int64_t n = 0;
+    PA_TRY(pa_population(c, pop.data(), R, &n));
+    uint64_t h = 0xcbf29ce484222325ull;
+    for (int8_t v : pop) {
+        h ^= (uint64_t)(uint8_t)v;
+        h *= 0x100000001b3ull;
+    }
+    *out = h;
+    return PA_OK;
+}

@@ -42,3 +42,12 @@ def compare_step(run, pa, i):
         assert info["kmin_prev"] == rec.kmin_prev, (i, "kmin_prev")
     np.testing.assert_array_equal(run.histogram(i, 0), rec.H_E, err_msg=f"H_E step {i}")
     np.testing.assert_array_equal(run.histogram(i, 1), rec.H_M, err_msg=f"H_M step {i}")
+
+
+def fnv1a64(pop) -> int:
+    """FNV-1a 64 over int8 +1/-1 spins (the pa_population_hash definition)."""
+    h = 0xCBF29CE484222325
+    for v in pop.astype(np.int8).ravel().view(np.uint8).tolist():
+        h ^= v
+        h = (h * 0x100000001B3) & 0xFFFFFFFFFFFFFFFF
+    return h

@@ -13,7 +13,7 @@ import math
 import numpy as np
 import pytest
 
-from tests._parity import assert_row_close, compare_step, oracle_run
+from tests._parity import assert_row_close, compare_step, fnv1a64, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -79,6 +79,7 @@ def test_run_parity(name, L, R, theta, beta_f, dbeta, seed, fmt):
         assert_row_close(rows[i], ref, f"{name} row {i}")
         compare_step(run, pa, i)
     np.testing.assert_array_equal(run.population(), pa.pop)
+    assert run.population_hash() == fnv1a64(pa.pop)
     E, M, fam = run.replicas()
     np.testing.assert_array_equal(E, pa.E)
     np.testing.assert_array_equal(M, pa.M)
