@@ -57,10 +57,14 @@ def core() -> ctypes.CDLL:
                                          ctypes.c_int64, ctypes.c_int, ctypes.c_uint64,
                                          ctypes.c_uint64, i8p]
             lib.oracle_sweep_msc.argtypes = lib.oracle_sweep.argtypes
+            lib.oracle_sweep_j.argtypes = [ctypes.c_int, ctypes.c_int64, i64p, ctypes.c_uint64, ctypes.c_int64,
+                                           ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, i8p, i8p, i8p]
+            lib.oracle_measure_j.argtypes = [ctypes.c_int, ctypes.c_int64, i8p, i8p, i8p, i64p, i64p]
             lib.oracle_measure.argtypes = [ctypes.c_int, ctypes.c_int64, i8p, i64p, i64p]
             lib.oracle_resample_words.argtypes = [ctypes.c_uint64, ctypes.c_int64, ctypes.c_int64, u32p]
             lib.oracle_philox_many.argtypes = [ctypes.c_int64, u32p, ctypes.c_uint64, u32p]
             for f in (lib.oracle_philox4x32_10, lib.oracle_init, lib.oracle_sweep, lib.oracle_sweep_msc,
+                      lib.oracle_sweep_j, lib.oracle_measure_j,
                       lib.oracle_measure, lib.oracle_resample_words, lib.oracle_philox_many):
                 f.restype = None
             _lib = lib

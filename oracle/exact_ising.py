@@ -8,7 +8,9 @@ These references pin the population-annealing oracle. The paper's model
 boundaries; the paper notes (Sec. 3) that exact results exist for it and
 uses beta_c = ln(1 + sqrt 2)/2. Three independent routes are given here:
 
-* ``brute_force`` enumerates all 2^N states of a tiny lattice (N <= 20);
+* ``brute_force`` enumerates all 2^N states of a tiny lattice (N <= 20),
+  also with +-J couplings (the disordered models the paper's method
+  targets);
 * ``transfer_matrix_lnZ`` evaluates Z = Tr T^L with the row-to-row transfer
   matrix (L <= 10);
 * ``kaufman_lnZ`` is Kaufman's (1949) closed form for the finite torus, in
@@ -32,6 +34,23 @@ def _logsumexp(a: np.ndarray) -> float:
 
 
 # ---------------------------------------------------------------- brute force
+def enumerate_states_j(L: int, Jr, Jd):
+    """E and M of all 2^N states of the +-J model: E = -sum_x,y (Jr s s_right
+    + Jd s s_down)."""
+    N = L * L
+    if N > 20:
+        raise ValueError("brute force limited to N <= 20")
+    idx = np.arange(1 << N, dtype=np.int64)
+    s = np.empty((1 << N, L, L), dtype=np.int32)
+    for y in range(L):
+        for x in range(L):
+            s[:, y, x] = ((idx >> (y * L + x)) & 1) * 2 - 1
+    Jr = np.asarray(Jr, dtype=np.int32)
+    Jd = np.asarray(Jd, dtype=np.int32)
+    E = -(Jr * s * np.roll(s, -1, axis=2)).sum(axis=(1, 2)) - (Jd * s * np.roll(s, -1, axis=1)).sum(axis=(1, 2))
+    return E.astype(np.int64), s.sum(axis=(1, 2)).astype(np.int64)
+
+
 def enumerate_states(L: int):
     """Energy and magnetisation of every one of the 2^(L*L) configurations.
 
@@ -55,10 +74,10 @@ def enumerate_states(L: int):
 class BruteForce:
     """Exact canonical averages of a tiny torus by full enumeration."""
 
-    def __init__(self, L: int):
+    def __init__(self, L: int, couplings=None):
         self.L = L
         self.N = L * L
-        E, M = enumerate_states(L)
+        E, M = enumerate_states(L) if couplings is None else enumerate_states_j(L, *couplings)
         # joint density of states g(E, M) as integer counts
         keys, counts = np.unique(np.stack([E, M], axis=1), axis=0, return_counts=True)
         self.E = keys[:, 0].astype(np.float64)

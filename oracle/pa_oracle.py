@@ -86,23 +86,37 @@ def init_spins(L: int, slots: np.ndarray, seed: int) -> np.ndarray:
 
 
 def sweep(s: np.ndarray, slots: np.ndarray, seed: int, u0: int, theta: int, T4: int, T8: int,
-          msc: bool = False) -> None:
+          msc: bool = False, couplings=None) -> None:
     """theta sweeps in place on s[r] (replica slot slots[r]); msc selects the
-    multi-spin-coded random numbers (Philox-seeded LCG per 32 replicas)."""
+    multi-spin-coded random numbers (Philox-seeded LCG per 32 replicas);
+    couplings = (Jr, Jd) int8 L x L arrays of the +-J model."""
     import ctypes
     assert s.dtype == np.int8 and s.flags.c_contiguous
     slots = np.ascontiguousarray(slots, dtype=np.int64)
     L = s.shape[1]
+    if couplings is not None:
+        assert not msc
+        Jr = np.ascontiguousarray(couplings[0], dtype=np.int8)
+        Jd = np.ascontiguousarray(couplings[1], dtype=np.int8)
+        core().oracle_sweep_j(L, slots.size, _ptr(slots, ctypes.c_int64), seed, u0, theta, T4, T8,
+                              _ptr(Jr, ctypes.c_int8), _ptr(Jd, ctypes.c_int8), _ptr(s, ctypes.c_int8))
+        return
     fn = core().oracle_sweep_msc if msc else core().oracle_sweep
     fn(L, slots.size, _ptr(slots, ctypes.c_int64), seed, u0, theta, T4, T8, _ptr(s, ctypes.c_int8))
 
 
-def measure(s: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+def measure(s: np.ndarray, couplings=None) -> tuple[np.ndarray, np.ndarray]:
     import ctypes
     s = np.ascontiguousarray(s, dtype=np.int8)
     n = s.shape[0]
     E = np.empty(n, dtype=np.int64)
     M = np.empty(n, dtype=np.int64)
+    if couplings is not None:
+        Jr = np.ascontiguousarray(couplings[0], dtype=np.int8)
+        Jd = np.ascontiguousarray(couplings[1], dtype=np.int8)
+        core().oracle_measure_j(s.shape[1], n, _ptr(s, ctypes.c_int8), _ptr(Jr, ctypes.c_int8),
+                                _ptr(Jd, ctypes.c_int8), _ptr(E, ctypes.c_int64), _ptr(M, ctypes.c_int64))
+        return E, M
     core().oracle_measure(s.shape[1], n, _ptr(s, ctypes.c_int8), _ptr(E, ctypes.c_int64),
                           _ptr(M, ctypes.c_int64))
     return E, M
@@ -259,7 +273,8 @@ class PopulationAnnealing:
 
     def __init__(self, L: int, R: int, theta: int, beta_f: float = 1.0, dbeta: float = 0.01,
                  seed: int = 1, beta0: float = 0.0, overlap: float = 0.85,
-                 capacity: int = 0, record_hist: bool = True, schedule=None, msc: bool = False):
+                 capacity: int = 0, record_hist: bool = True, schedule=None, msc: bool = False,
+                 couplings=None):
         if L < 4 or L % 2:
             raise ValueError("L must be even and >= 4")
         if beta0 != 0.0:
@@ -284,6 +299,14 @@ class PopulationAnnealing:
             self.n_fixed = int(math.floor((self.beta_f - beta0) / self.dbeta + 0.5)) if not self.adaptive else None
         self.record_hist = record_hist
         self.msc = bool(msc)  # multi-spin-coded sweeps (Sec. 4, LCG variant)
+        # +-J couplings (Jr, Jd) shared by every replica; None: ferromagnet.
+        # Levels k = (E + 2N)/4 need an even number of negative bonds.
+        self.J = None
+        if couplings is not None:
+            Jr, Jd = (np.ascontiguousarray(a, dtype=np.int8).reshape(L, L) for a in couplings)
+            if int((Jr < 0).sum() + (Jd < 0).sum()) % 2:
+                raise ValueError("the number of negative couplings must be even")
+            self.J = (Jr, Jd)
         self.step_index = 0
         self.beta = 0.0
         self.done = False
@@ -291,7 +314,7 @@ class PopulationAnnealing:
         # step 0: random configurations at beta0 = 0, measured, no sweeps
         slots = np.arange(self.R, dtype=np.int64)
         self.pop = init_spins(L, slots, self.seed)
-        self.E, self.M = measure(self.pop)
+        self.E, self.M = measure(self.pop, self.J)
         self.fam = np.arange(self.R, dtype=np.int64)
         self.sum_lnQ = 0.0
         self.Hsum = np.zeros(self.N + 1, dtype=np.int64)
@@ -384,18 +407,19 @@ class PopulationAnnealing:
                 sample = sample(R_new)
             sample = np.asarray(sample, dtype=np.int64)
             sub = np.ascontiguousarray(self.pop[parent[sample]])
-            sweep(sub, sample, self.seed, u0, self.theta, T4, T8, msc=self.msc)
+            sweep(sub, sample, self.seed, u0, self.theta, T4, T8, msc=self.msc, couplings=self.J)
             rec.sample = sample
             rec.sample_pop = sub
-            rec.sample_E, rec.sample_M = measure(sub)
+            rec.sample_E, rec.sample_M = measure(sub, self.J)
             rec.sample_fam = self.fam[parent[sample]]
             self.partial = True
             self.records.append(rec)
             return rec
         self.pop = np.ascontiguousarray(self.pop[parent])
         self.fam = self.fam[parent]
-        sweep(self.pop, np.arange(R_new, dtype=np.int64), self.seed, u0, self.theta, T4, T8, msc=self.msc)
-        self.E, self.M = measure(self.pop)
+        sweep(self.pop, np.arange(R_new, dtype=np.int64), self.seed, u0, self.theta, T4, T8, msc=self.msc,
+              couplings=self.J)
+        self.E, self.M = measure(self.pop, self.J)
         self.step_index = i
         self.beta = beta_new
         self.done = bool(final)
@@ -493,3 +517,15 @@ def weighted_average(runs_rows):
                     "betaF_per_N": bF, "S_per_N": beta * e - bF,
                     "R": sum(r.R for r in rows), "families": sum(r.families for r in rows), "weights": w})
     return out
+
+
+def random_couplings(L: int, seed: int, p_negative: float = 0.5):
+    """A +-J instance: (Jr, Jd) int8 L x L arrays, each bond -1 with
+    probability p_negative (numpy's PCG64 from `seed`), with the last down
+    bond flipped if needed so that the number of negative bonds is even."""
+    rng = np.random.default_rng(seed)
+    Jr = np.where(rng.random((L, L)) < p_negative, -1, 1).astype(np.int8)
+    Jd = np.where(rng.random((L, L)) < p_negative, -1, 1).astype(np.int8)
+    if int((Jr < 0).sum() + (Jd < 0).sum()) % 2:
+        Jd[L - 1, L - 1] = -Jd[L - 1, L - 1]
+    return Jr, Jd

@@ -107,6 +107,68 @@ void oracle_init(int L, int64_t n, const int64_t *slot, uint64_t seed, int8_t *s
  * (computed by the caller) makes Pr[x < T] = p up to 2^-32.
  * Sweep number u runs from u0 to u0 + theta - 1.
  */
+/* Couplings of the +-J model (Sec. 1: the method is for disordered systems
+ * too): Jr[y*L+x] couples (x,y) to (x+1,y), Jd[y*L+x] couples it to
+ * (x,y+1); NULL means the ferromagnet (all +1). A neighbour is "aligned"
+ * when J s_i s_j = +1, so dE = 4 n - 8 as before. */
+static int jr(const int8_t *Jr, int L, int x, int y) { return Jr ? Jr[y * L + x] : 1; }
+static int jd(const int8_t *Jd, int L, int x, int y) { return Jd ? Jd[y * L + x] : 1; }
+
+static int aligned_j(const int8_t *S, const int8_t *Jr, const int8_t *Jd, int L, int x, int y)
+{
+    int si = S[y * L + x];
+    int xr = (x + 1) % L, xl = (x + L - 1) % L, yd = (y + 1) % L, yu = (y + L - 1) % L;
+    return (jr(Jr, L, x, y) * si * S[y * L + xr] == 1) + (jr(Jr, L, xl, y) * si * S[y * L + xl] == 1) +
+           (jd(Jd, L, x, y) * si * S[yd * L + x] == 1) + (jd(Jd, L, x, yu) * si * S[yu * L + x] == 1);
+}
+
+void oracle_sweep_j(int L, int64_t n, const int64_t *slot, uint64_t seed, int64_t u0, int theta,
+                    uint64_t T4, uint64_t T8, const int8_t *Jr, const int8_t *Jd, int8_t *s)
+{
+    const int N = L * L, half = L / 2;
+    for (int64_t r = 0; r < n; r++) {
+        int8_t *S = s + (size_t)r * N;
+        uint32_t k = (uint32_t)slot[r];
+        for (int sw = 0; sw < theta; sw++) {
+            uint32_t u = (uint32_t)(u0 + sw);
+            for (int c = 0; c < 2; c++) {
+                for (int y = 0; y < L; y++)
+                    for (int x = 0; x < L; x++) {
+                        if (((x + y) & 1) != c)
+                            continue;
+                        int aligned = aligned_j(S, Jr, Jd, L, x, y);
+                        int flip = 1;
+                        if (aligned > 2) {
+                            uint32_t b = (uint32_t)(y * half + (x >> 1));
+                            uint32_t w = stream_word(seed, 2u * u + (uint32_t)c, b >> 2, 1u, k, b & 3u);
+                            flip = ((uint64_t)w < ((aligned == 3) ? T4 : T8));
+                        }
+                        if (flip)
+                            S[y * L + x] = (int8_t)(-S[y * L + x]);
+                    }
+            }
+        }
+    }
+}
+
+void oracle_measure_j(int L, int64_t n, const int8_t *s, const int8_t *Jr, const int8_t *Jd,
+                      int64_t *E, int64_t *M)
+{
+    const int N = L * L;
+    for (int64_t r = 0; r < n; r++) {
+        const int8_t *S = s + (size_t)r * N;
+        int64_t e = 0, m = 0;
+        for (int y = 0; y < L; y++)
+            for (int x = 0; x < L; x++) {
+                int si = S[y * L + x];
+                e -= si * (jr(Jr, L, x, y) * S[y * L + (x + 1) % L] + jd(Jd, L, x, y) * S[((y + 1) % L) * L + x]);
+                m += si;
+            }
+        E[r] = e;
+        M[r] = m;
+    }
+}
+
 void oracle_sweep(int L, int64_t n, const int64_t *slot, uint64_t seed, int64_t u0,
                   int theta, uint64_t T4, uint64_t T8, int8_t *s)
 {
