@@ -120,6 +120,18 @@ typedef struct {
  * Errors: PA_EINVAL (bad config), PA_ENOMEM, PA_ECUDA. */
 pa_status pa_create(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
 
+/* Create a run of the +-J (Edwards-Anderson) model: quenched couplings
+ * shared by every replica, H = -sum_{x,y} (Jr[y L + x] s(x,y) s(x+1,y) +
+ * Jd[y L + x] s(x,y) s(x,y+1)) with every J = +1 or -1 (host arrays of
+ * L*L int8 each; all +1 is the ferromagnet). The paper's method applies
+ * unchanged (Sec. 1, Sec. 6: disordered systems): a neighbour is aligned
+ * when J s_i s_j = +1, so dE = 4n - 8 and the acceptance rule, Q and the
+ * resampling are as for the ferromagnet. The number of negative couplings
+ * must be even (then (E + 2N)/4 is an integer). PA_SPIN_BITS32 and
+ * PA_SPIN_INT8 only. */
+pa_status pa_create_couplings(const pa_config *cfg, const int8_t *Jr, const int8_t *Jd, void *cuda_stream,
+                              pa_ctx **out);
+
 /* Create a run that follows a given schedule beta_1 < ... < beta_n (host
  * array betas[n], 0 < beta_i <= 50), with step i using
  * delta_i = beta_i - beta_{i-1} in Q and tau_hat. Sec. 2.3: with M runs the

@@ -106,6 +106,7 @@ SIGNATURES = [
     ("pa_step_async", ctypes.c_int, [_P]),
     ("pa_checkpoint", ctypes.c_int, [_P, _P, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]),
     ("pa_restore", ctypes.c_int, [_P, _P, ctypes.c_size_t]),
+    ("pa_create_couplings", ctypes.c_int, [ctypes.POINTER(_Config), _P, _P, _P, ctypes.POINTER(_P)]),
     ("pa_create_scheduled", ctypes.c_int, [ctypes.POINTER(_Config), ctypes.POINTER(ctypes.c_double), ctypes.c_int64,
                                            _P, ctypes.POINTER(_P)]),
     ("pa_weighted_average", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P]),
@@ -191,14 +192,23 @@ def footprint_bytes(cfg: PAConfig) -> int:
 class PARun:
     """One population-annealing run on the GPU (a pa_ctx)."""
 
-    def __init__(self, cfg: PAConfig, stream=None, schedule=None):
+    def __init__(self, cfg: PAConfig, stream=None, schedule=None, couplings=None):
         """schedule: optional increasing betas beta_1..beta_n to follow
-        (pa_create_scheduled), e.g. the row betas of an adaptive first run."""
+        (pa_create_scheduled), e.g. the row betas of an adaptive first run.
+        couplings: optional (Jr, Jd) int8 L x L arrays of +-1 (pa_create_couplings)."""
         self.cfg = cfg
         self._lib = lib()
         self._h = ctypes.c_void_p()
         c = cfg._c()
-        if schedule is None:
+        if couplings is not None:
+            assert schedule is None
+            Jr = np.ascontiguousarray(couplings[0], dtype=np.int8).ravel()
+            Jd = np.ascontiguousarray(couplings[1], dtype=np.int8).ravel()
+            self._J = (Jr, Jd)
+            _check(self._lib.pa_create_couplings(ctypes.byref(c), ctypes.c_void_p(Jr.ctypes.data),
+                                                 ctypes.c_void_p(Jd.ctypes.data), _stream_handle(stream),
+                                                 ctypes.byref(self._h)), "pa_create_couplings")
+        elif schedule is None:
             _check(self._lib.pa_create(ctypes.byref(c), _stream_handle(stream), ctypes.byref(self._h)), "pa_create")
         else:
             b = np.ascontiguousarray(schedule, dtype=np.float64)

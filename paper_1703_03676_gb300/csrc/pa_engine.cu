@@ -722,11 +722,63 @@ size_t pa_footprint_bytes(const pa_config* cfg)
     return footprint(*cfg);
 }
 
+namespace {
+pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr, const int8_t* Jd, pa_ctx** out);
+}
+
 pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
+{
+    return create_impl(cfg, cuda_stream, nullptr, nullptr, out);
+}
+
+pa_status pa_create_couplings(const pa_config* cfg, const int8_t* Jr, const int8_t* Jd, void* cuda_stream,
+                              pa_ctx** out)
+{
+    if (!Jr || !Jd) return PA_EINVAL;
+    return create_impl(cfg, cuda_stream, Jr, Jd, out);
+}
+
+}  // extern "C"
+
+namespace {
+
+// +-J couplings as the kernels read them: for colour c and plane site b at
+// (x, y), the bonds to its neighbours in the order same-h, row, up, down
+// (same-h is the left bond when x is odd, the right bond when x is even).
+void bond_tables(int L, const int8_t* Jr, const int8_t* Jd, std::vector<uint32_t>& masks,
+                 std::vector<uint8_t>& bytes)
+{
+    const int N = L * L, HB = L / 2, NP = N / 2, WP = N / 64;
+    bytes.assign((size_t)8 * NP, 0);
+    masks.assign((size_t)8 * (WP > 0 ? WP : 1), 0u);
+    for (int c = 0; c < 2; c++)
+        for (int b = 0; b < NP; b++) {
+            const int y = b / HB, h = b % HB, x = 2 * h + ((c + y) & 1);
+            const int right = Jr[y * L + x] < 0, left = Jr[y * L + (x + L - 1) % L] < 0;
+            const int down = Jd[y * L + x] < 0, up = Jd[((y + L - 1) % L) * L + x] < 0;
+            const int dir[4] = {(x & 1) ? left : right, (x & 1) ? right : left, up, down};
+            for (int d = 0; d < 4; d++) {
+                bytes[(size_t)(d * 2 + c) * NP + b] = (uint8_t)dir[d];
+                if (WP > 0 && dir[d]) masks[(size_t)(d * 2 + c) * WP + (b >> 5)] |= 1u << (b & 31);
+            }
+        }
+}
+
+pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr, const int8_t* Jd, pa_ctx** out)
 {
     if (!cfg || !out) return PA_EINVAL;
     *out = nullptr;
     PA_TRY(validate(*cfg));
+    if (Jr) {
+        if (cfg->spin_format != PA_SPIN_BITS32 && cfg->spin_format != PA_SPIN_INT8) return PA_EINVAL;
+        long long neg = 0;
+        const long long N = (long long)cfg->L * cfg->L;
+        for (long long i = 0; i < N; i++) {
+            if ((Jr[i] != 1 && Jr[i] != -1) || (Jd[i] != 1 && Jd[i] != -1)) return PA_EINVAL;
+            neg += (Jr[i] < 0) + (Jd[i] < 0);
+        }
+        if (neg & 1) return PA_EINVAL;  // (E + 2N)/4 must be an integer
+    }
     pa_ctx* c = new (std::nothrow) pa_ctx();
     if (!c) return PA_ENOMEM;
     c->cfg = *cfg;
@@ -799,6 +851,24 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
     PA_ALLOC(h.work, 4);
     PA_ALLOC(c->d_key, 4);
     h.key = c->d_key;
+    if (Jr) {
+        std::vector<uint32_t> masks;
+        std::vector<uint8_t> bytes;
+        bond_tables(cfg->L, Jr, Jd, masks, bytes);
+        if (cfg->spin_format == PA_SPIN_BITS32) {
+            uint32_t* d = nullptr;
+            PA_ALLOC(d, masks.size());
+            if (cudaMemcpy(d, masks.data(), masks.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(PA_ECUDA);
+            h.bonds = d;
+        } else {
+            uint8_t* d = nullptr;
+            PA_ALLOC(d, bytes.size());
+            if (cudaMemcpy(d, bytes.data(), bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+                return fail(PA_ECUDA);
+            h.bonds8 = d;
+        }
+    }
 #undef PA_ALLOC
     // staging for adaptive uploads (level weights + thresholds)
     c->h_stage_bytes = N1 * sizeof(double) + 64;
@@ -838,6 +908,10 @@ pa_status pa_create(const pa_config* cfg, void* cuda_stream, pa_ctx** out)
     *out = c;
     return PA_OK;
 }
+
+}  // namespace
+
+extern "C" {
 
 pa_status pa_create_scheduled(const pa_config* cfg, const double* betas, int64_t n, void* cuda_stream,
                               pa_ctx** out)

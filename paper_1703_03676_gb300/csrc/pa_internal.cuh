@@ -18,6 +18,8 @@
 //   Hsum        running sum of energy histograms (Sec. 2.4).
 //   Msum        per energy level, over all steps: sum |M|, sum M^2, sum M^4
 //               (the last two as 128-bit lo/hi), for reweighting magnetisations.
+//   bonds       +-J couplings as masks per neighbour direction (same-h, row,
+//               up, down) and colour; null for the ferromagnet.
 //   tw          level weights t[d] = exp(-4 delta d) (host-computed).
 //   F, U        copy tables per energy level: floor(tau_hat), ceil(frac 2^32).
 //   thr         per step: T4 - 1 and T8 - 1 (uint32).
@@ -75,6 +77,8 @@ struct RunDev {
     uint32_t* H[2];
     unsigned long long* Hsum;
     unsigned long long* Msum;  // per energy level: sum |M|, sum M^2 (lo, hi), sum M^4 (lo, hi)
+    const uint32_t* bonds;    // +-J model, bit-packed: masks [dir][colour][word], bit set = J < 0
+    const uint8_t* bonds8;    // +-J model, byte spins: [dir][colour][site], 1 = J < 0
     double* tw;
     uint32_t* F;
     unsigned long long* U;

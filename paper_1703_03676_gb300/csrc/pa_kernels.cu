@@ -170,8 +170,23 @@ __device__ __forceinline__ void copy_words(uint32_t* __restrict__ dst, const uin
 }
 
 // anti-parallel bonds and up spins of the replica in shared memory
+// +-J model: a neighbour word seen through the couplings (bit flipped where
+// J < 0), so "disagree" means an unsatisfied bond in every formula below
+template <int L>
+__device__ __forceinline__ void apply_bonds(const uint32_t* __restrict__ bonds, int c, int w, uint32_t& same,
+                                            uint32_t& side, uint32_t& up, uint32_t& down)
+{
+    constexpr int WP = Geo<L>::WP;
+    const uint32_t* B = bonds + c * WP + w;
+    same ^= __ldg(B);
+    side ^= __ldg(B + 2 * WP);
+    up ^= __ldg(B + 4 * WP);
+    down ^= __ldg(B + 6 * WP);
+}
+
 template <int L, int G>
-__device__ __forceinline__ void measure_bits(const uint32_t* sp, int gl, unsigned& anti, unsigned& ups)
+__device__ __forceinline__ void measure_bits(const uint32_t* sp, int gl, unsigned& anti, unsigned& ups,
+                                             const uint32_t* __restrict__ bonds)
 {
     using Gm = Geo<L>;
     anti = 0;
@@ -179,6 +194,7 @@ __device__ __forceinline__ void measure_bits(const uint32_t* sp, int gl, unsigne
     for (int w = gl; w < Gm::WP; w += G) {
         uint32_t same, side, up, down;
         neighbours<L>(sp + Gm::WP, 0, w, same, side, up, down);
+        if (bonds) apply_bonds<L>(bonds, 0, w, same, side, up, down);
         const uint32_t s = sp[w];
         anti += __popc(s ^ same) + __popc(s ^ side) + __popc(s ^ up) + __popc(s ^ down);
         ups += __popc(s) + __popc(sp[Gm::WP + w]);
@@ -258,6 +274,7 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
     const PhiloxKey key{r.key[0], r.key[1]};
     const int theta = r.theta;
     const unsigned u0 = (unsigned)(step - 1) * (unsigned)theta;
+    const uint32_t* __restrict__ bonds = r.bonds;
     uint32_t p = 0;
     if (active) {
         p = r.parent[k];
@@ -277,6 +294,7 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
                     const int w = gl + m * G;
                     uint32_t same, side, up, down;
                     neighbours<L>(O, c, w, same, side, up, down);
+                    if (bonds) apply_bonds<L>(bonds, c, w, same, side, up, down);
                     P[w] = metropolis_word(P[w], same, side, up, down, 8u * (unsigned)w, (unsigned)k, c2, t4m1,
                                            t8m1, key);
                 }
@@ -285,7 +303,7 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
         }
     }
     unsigned anti = 0, ups = 0;
-    if (active) measure_bits<L, G>(sp, gl, anti, ups);
+    if (active) measure_bits<L, G>(sp, gl, anti, ups, bonds);
     anti = Gr::sum(anti, red);
     ups = Gr::sum(ups, red);
     if (active) {
@@ -324,7 +342,7 @@ __device__ __forceinline__ void bits_group_init(const RunDev& r, long long k, bo
     }
     Gr::sync();
     unsigned anti = 0, ups = 0;
-    if (active) measure_bits<L, G>(sp, gl, anti, ups);
+    if (active) measure_bits<L, G>(sp, gl, anti, ups, r.bonds);
     anti = Gr::sum(anti, red);
     ups = Gr::sum(ups, red);
     if (active) {
@@ -389,8 +407,15 @@ __device__ __forceinline__ int nb_index_side(int b, int c, int L, int half)
     return y * half + h2;
 }
 
+// bond byte (1: J < 0) of direction dir for site b of plane c, or 0
+__device__ __forceinline__ int bond8(const uint8_t* __restrict__ bonds8, int dir, int c, int NP, int b)
+{
+    return bonds8 ? (int)__ldg(bonds8 + ((size_t)(dir * 2 + c) * NP + b)) : 0;
+}
+
 template <int G>
-__device__ __forceinline__ void measure_bytes(const uint8_t* sp, int L, int gl, unsigned& anti, unsigned& ups)
+__device__ __forceinline__ void measure_bytes(const uint8_t* sp, int L, int gl, unsigned& anti, unsigned& ups,
+                                              const uint8_t* __restrict__ bonds8)
 {
     const int N = L * L, half = L / 2, NP = N / 2;
     const uint8_t* o = sp + NP;
@@ -401,7 +426,9 @@ __device__ __forceinline__ void measure_bytes(const uint8_t* sp, int L, int gl, 
         const int y = b / half, h = b - y * half;
         const int up = ((y == 0 ? L - 1 : y - 1)) * half + h;
         const int dn = ((y == L - 1 ? 0 : y + 1)) * half + h;
-        anti += (unsigned)((o[b] != s) + (o[nb_index_side(b, 0, L, half)] != s) + (o[up] != s) + (o[dn] != s));
+        anti += (unsigned)(((o[b] ^ bond8(bonds8, 0, 0, NP, b)) != s) +
+                           ((o[nb_index_side(b, 0, L, half)] ^ bond8(bonds8, 1, 0, NP, b)) != s) +
+                           ((o[up] ^ bond8(bonds8, 2, 0, NP, b)) != s) + ((o[dn] ^ bond8(bonds8, 3, 0, NP, b)) != s));
         ups += (unsigned)(s + o[b]);
     }
 }
@@ -439,7 +466,7 @@ __global__ void __launch_bounds__(256) k_init_bytes(const __grid_constant__ RunD
         (void)NP;
         __syncwarp();
         unsigned anti = 0, ups = 0;
-        if (active) measure_bytes<G>(sp, r.L, gl, anti, ups);
+        if (active) measure_bytes<G>(sp, r.L, gl, anti, ups, r.bonds8);
         anti = group_sum<G>(anti);
         ups = group_sum<G>(ups);
         if (active) {
@@ -501,8 +528,11 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
                                 const int y = b / half, h = b - y * half;
                                 const int up = (y == 0 ? L - 1 : y - 1) * half + h;
                                 const int dn = (y == L - 1 ? 0 : y + 1) * half + h;
-                                const int n = (O[b] == s) + (O[nb_index_side(b, c, L, half)] == s) + (O[up] == s) +
-                                              (O[dn] == s);
+                                const uint8_t* B8 = r.bonds8;
+                                const int n = ((O[b] ^ bond8(B8, 0, c, NP, b)) == s) +
+                                              ((O[nb_index_side(b, c, L, half)] ^ bond8(B8, 1, c, NP, b)) == s) +
+                                              ((O[up] ^ bond8(B8, 2, c, NP, b)) == s) +
+                                              ((O[dn] ^ bond8(B8, 3, c, NP, b)) == s);
                                 bool flip = n <= 2;
                                 if (n == 3) flip = xs[l] <= t4m1;
                                 if (n == 4) flip = xs[l] <= t8m1;
@@ -515,7 +545,7 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
             }
         }
         unsigned anti = 0, ups = 0;
-        if (active) measure_bytes<G>(sp, L, gl, anti, ups);
+        if (active) measure_bytes<G>(sp, L, gl, anti, ups, r.bonds8);
         anti = group_sum<G>(anti);
         ups = group_sum<G>(ups);
         if (active) {
