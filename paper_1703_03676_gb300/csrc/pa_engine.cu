@@ -818,6 +818,7 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     h.record_hist = cfg->record_histograms ? 1 : 0;
     h.hist_steps = (int)s.hist_steps;
     h.nsteps = (int)s.steps;
+    h.unit = 1u;
     const size_t N1 = (size_t)s.N + 1;
     pa_status st = PA_OK;
 #define PA_ALLOC(p, n)                            \

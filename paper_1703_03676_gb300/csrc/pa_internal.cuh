@@ -64,7 +64,7 @@ struct RunDev {
     int record_hist;
     int hist_steps;           // steps with a slot in hist_rec
     int nsteps;               // last step of a fixed schedule (batched runs stop there)
-    int pad1;
+    unsigned unit;            // always 1; a run-time multiplier for the accept-bit insert
     uint32_t* pop[2];
     int32_t* elev[2];
     int32_t* mlev[2];

@@ -86,6 +86,44 @@ __device__ __forceinline__ void neighbours(const uint32_t* __restrict__ O, int c
     }
 }
 
+// Sets bit T of acc when x <= thr. The 32 accept bits of a word are
+// disjoint, so the insert can be an addition: a predicated multiply-add by
+// the run-time constant unit (always 1) issues on the FMA pipe, which the
+// update leaves less busy than the integer/logic pipe the threshold select
+// and compare occupy (a compile-time 1 would be folded back into a logic op).
+template <int T>
+__device__ __forceinline__ uint32_t accept_bit(uint32_t acc, uint32_t x, uint32_t thr, uint32_t unit)
+{
+    asm("{\n\t.reg .pred p;\n\tsetp.le.u32 p, %1, %2;\n\t@p mad.lo.u32 %0, %3, %4, %0;\n\t}"
+        : "+r"(acc)
+        : "r"(x), "r"(thr), "r"(unit), "n"(1u << T));
+    return acc;
+}
+
+// site T compares against T8-1 when none of its neighbours disagrees, else T4-1
+template <int T>
+__device__ __forceinline__ uint32_t site_threshold(uint32_t eq0, uint32_t t4m1, uint32_t t8m1)
+{
+    return ((eq0 >> T) & 1u) ? t8m1 : t4m1;
+}
+
+// the accept bits of sites 4q .. 4q+3 from Philox block q, then blocks q+1 .. 7
+template <int Q>
+__device__ __forceinline__ uint32_t accept_blocks(uint32_t acc, uint32_t eq0, unsigned c0, unsigned k, unsigned c2,
+                                                  uint32_t t4m1, uint32_t t8m1, uint32_t unit, PhiloxKey key)
+{
+    if constexpr (Q == 8) {
+        return acc;
+    } else {
+        const uint4 x = philox10(make_uint4(c2, c0 + Q, kTagSweep, k), key);
+        acc = accept_bit<4 * Q + 0>(acc, x.x, site_threshold<4 * Q + 0>(eq0, t4m1, t8m1), unit);
+        acc = accept_bit<4 * Q + 1>(acc, x.y, site_threshold<4 * Q + 1>(eq0, t4m1, t8m1), unit);
+        acc = accept_bit<4 * Q + 2>(acc, x.z, site_threshold<4 * Q + 2>(eq0, t4m1, t8m1), unit);
+        acc = accept_bit<4 * Q + 3>(acc, x.w, site_threshold<4 * Q + 3>(eq0, t4m1, t8m1), unit);
+        return accept_blocks<Q + 1>(acc, eq0, c0, k, c2, t4m1, t8m1, unit, key);
+    }
+}
+
 // One Metropolis update of the 32 sites of word s (all of one colour).
 // A site with n aligned neighbours flips with certainty if n <= 2 (dE <= 0),
 // with x <= T4-1 if n = 3 and x <= T8-1 if n = 4, x the SWEEP word of the
@@ -96,25 +134,13 @@ __device__ __forceinline__ void neighbours(const uint32_t* __restrict__ O, int c
 // once; each site is then compared once, against the threshold its n selects.
 __device__ __forceinline__ uint32_t metropolis_word(uint32_t s, uint32_t same, uint32_t side, uint32_t up,
                                                     uint32_t down, unsigned c0, unsigned k, unsigned c2,
-                                                    uint32_t t4m1, uint32_t t8m1, PhiloxKey key)
+                                                    uint32_t t4m1, uint32_t t8m1, uint32_t unit, PhiloxKey key)
 {
     const uint32_t d1 = s ^ same, d2 = s ^ side, d3 = s ^ up, d4 = s ^ down;
     const uint32_t a = d1 ^ d2, b = d1 & d2, cc = d3 ^ d4, e = d3 & d4;
     const uint32_t ge2 = b | e | (a & cc);
     const uint32_t eq0 = ~(d1 | d2 | d3 | d4);
-    uint32_t acc = 0;
-#pragma unroll
-    for (int q = 0; q < 8; q++) {
-        const uint4 x = philox10(make_uint4(c2, c0 + q, kTagSweep, k), key);
-        const uint32_t xs[4] = {x.x, x.y, x.z, x.w};
-#pragma unroll
-        for (int l = 0; l < 4; l++) {
-            const int t = 4 * q + l;
-            const uint32_t thr = ((eq0 >> t) & 1u) ? t8m1 : t4m1;
-            acc |= (uint32_t)(xs[l] <= thr) << t;
-        }
-    }
-    return s ^ (ge2 | acc);
+    return s ^ (ge2 | accept_blocks<0>(0u, eq0, c0, k, c2, t4m1, t8m1, unit, key));
 }
 
 // ======================================================== shared epilogue
@@ -296,7 +322,7 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
                     neighbours<L>(O, c, w, same, side, up, down);
                     if (bonds) apply_bonds<L>(bonds, c, w, same, side, up, down);
                     P[w] = metropolis_word(P[w], same, side, up, down, 8u * (unsigned)w, (unsigned)k, c2, t4m1,
-                                           t8m1, key);
+                                           t8m1, r.unit, key);
                 }
             }
             Gr::sync();
@@ -727,22 +753,29 @@ __device__ __forceinline__ void msc_measure(const uint32_t* sp, int lane, unsign
     }
 }
 
+// accept bits of replicas J .. 31: LCG value j+1 of the site's seed
+template <int J>
+__device__ __forceinline__ uint32_t msc_accept(uint32_t acc, uint32_t eq0, unsigned seed, uint32_t t4m1,
+                                               uint32_t t8m1, uint32_t unit)
+{
+    if constexpr (J == 32) {
+        return acc;
+    } else {
+        const unsigned xj = c_lcg.a[J + 1] * seed + c_lcg.c[J + 1];
+        acc = accept_bit<J>(acc, xj, site_threshold<J>(eq0, t4m1, t8m1), unit);
+        return msc_accept<J + 1>(acc, eq0, seed, t4m1, t8m1, unit);
+    }
+}
+
 // the 32 replicas' Metropolis update of site word s with neighbour words
 __device__ __forceinline__ uint32_t msc_update(uint32_t s, uint32_t n1, uint32_t n2, uint32_t n3, uint32_t n4,
-                                               unsigned seed, uint32_t t4m1, uint32_t t8m1)
+                                               unsigned seed, uint32_t t4m1, uint32_t t8m1, uint32_t unit)
 {
     const uint32_t d1 = s ^ n1, d2 = s ^ n2, d3 = s ^ n3, d4 = s ^ n4;
     const uint32_t a = d1 ^ d2, bb = d1 & d2, cc = d3 ^ d4, e = d3 & d4;
     const uint32_t ge2 = bb | e | (a & cc);
     const uint32_t eq0 = ~(d1 | d2 | d3 | d4);
-    uint32_t acc = 0;
-#pragma unroll
-    for (int j = 0; j < 32; j++) {
-        const unsigned xj = c_lcg.a[j + 1] * seed + c_lcg.c[j + 1];
-        const uint32_t thr = ((eq0 >> j) & 1u) ? t8m1 : t4m1;
-        acc |= (uint32_t)(xj <= thr) << j;
-    }
-    return s ^ (ge2 | acc);
+    return s ^ (ge2 | msc_accept<0>(0u, eq0, seed, t4m1, t8m1, unit));
 }
 
 // Warps per 32-replica group: enough that each thread updates one to four
@@ -886,7 +919,7 @@ __global__ void __launch_bounds__(32 * msc_warps<L>()) k_sweep_msc(const __grid_
                             const int h = h0 + l, b = b0 + l;
                             const int h2 = xodd ? (h + 1 == HALF ? 0 : h + 1) : (h == 0 ? HALF - 1 : h - 1);
                             P[b] = msc_update(P[b], O[b], O[y * HALF + h2], O[rup + h], O[rdn + h], seeds[l], t4m1,
-                                              t8m1);
+                                              t8m1, r.unit);
                         }
                     } else {
 #pragma unroll
@@ -897,7 +930,7 @@ __global__ void __launch_bounds__(32 * msc_warps<L>()) k_sweep_msc(const __grid_
                                 const int up = (y == 0 ? L - 1 : y - 1) * HALF + h;
                                 const int dn = (y == L - 1 ? 0 : y + 1) * HALF + h;
                                 P[b] = msc_update(P[b], O[b], O[msc_side<L>(b, c)], O[up], O[dn], seeds[l], t4m1,
-                                                  t8m1);
+                                                  t8m1, r.unit);
                             }
                         }
                     }
