@@ -6,18 +6,20 @@ serves the tests, the golden-value script and ``__graft_entry__.smoke``.
 These references pin the population-annealing oracle. The paper's model
 (Sec. 3, Eq. hamiltonian) is H = -J sum_<ij> s_i s_j with J = 1 and periodic
 boundaries; the paper notes (Sec. 3) that exact results exist for it and
-uses beta_c = ln(1 + sqrt 2)/2. Three independent routes are given here:
+uses beta_c = ln(1 + sqrt 2)/2. Four independent routes are given here:
 
 * ``brute_force`` enumerates all 2^N states of a tiny lattice (N <= 20),
   also with +-J couplings (the disordered models the paper's method
   targets);
 * ``transfer_matrix_lnZ`` evaluates Z = Tr T^L with the row-to-row transfer
   matrix (L <= 10);
+* ``transfer_matrix_dos`` counts the exact integer density of states g(E)
+  of tori up to 6 x 6 (2^36 states) with the same row transfer;
 * ``kaufman_lnZ`` is Kaufman's (1949) closed form for the finite torus, in
   the four-product form also used by Beale (1996).
 
-The tests check the three against each other before any of them is used as a
-pin for the oracle.
+The tests check them against each other and against closed-form state
+counts before any of them is used as a pin for the oracle.
 """
 from __future__ import annotations
 
@@ -146,6 +148,53 @@ def transfer_matrix_lnZ(L: int, beta: float) -> float:
     ratio = lam / lmax
     s = float(np.sum(ratio ** L))
     return L * math.log(lmax) + math.log(s)
+
+
+def transfer_matrix_dos(L: int) -> dict[int, int]:
+    """Exact integer density of states g(E) of the L x L torus (L <= 6) by
+    counting row sequences with the transfer matrix.
+
+    Rows are states a in [0, 2^L) (bit x set = spin +1). Appending row b
+    after row a adds dE(a, b) = -sum_x b_x b_{x+1} - sum_x a_x b_x. For every
+    first row a0 the counts n[a0, b, E] of row sequences a0 .. b are carried
+    row by row; closing the torus after L rows keeps b = a0. All counts stay
+    below 2^(L*L) <= 2^36 < 2^53, so float64 matrix products are exact.
+    """
+    if not 2 <= L <= 6:
+        raise ValueError("transfer-matrix density of states limited to 2 <= L <= 6")
+    N = L * L
+    n_rows = 1 << L
+    idx = np.arange(n_rows)
+    rows = np.array([[1 if (i >> x) & 1 else -1 for x in range(L)] for i in idx], dtype=np.int64)
+    h = -(rows * np.roll(rows, -1, axis=1)).sum(axis=1)       # in-row bonds of b
+    v = -(rows @ rows.T)                                      # bonds between rows a and b
+    dE = v + h[None, :]                                       # [a, b]
+    # energies in steps of 2 (dE is even); index i <-> E = 2 i - 2N
+    n_e = 2 * N + 1
+    cnt = np.zeros((n_rows, n_rows, n_e), dtype=np.float64)   # [a0, b, E index]
+    cnt[idx, idx, N] = 1.0                                    # zero rows: E = 0
+    for _ in range(L):
+        nxt = np.zeros_like(cnt)
+        by_e = cnt.transpose(0, 2, 1)                         # [a0, E index, b]
+        for d in np.unique(dE):
+            Md = (dE == d).astype(np.float64)                 # [b, b'] pairs adding energy d
+            moved = (by_e @ Md).transpose(0, 2, 1)            # [a0, b', E index]
+            shift = int(d) // 2
+            if shift >= 0:
+                nxt[:, :, shift:] += moved[:, :, :n_e - shift]
+            else:
+                nxt[:, :, :n_e + shift] += moved[:, :, -shift:]
+        cnt = nxt
+    # the L appended rows are rows 1..L; closing the torus needs row L == row 0
+    closed = cnt[idx, idx, :].sum(axis=0)
+    if float(closed.max()) >= 2.0 ** 53:
+        raise ArithmeticError("count exceeds exact float64 range")
+    out: dict[int, int] = {}
+    for i in range(n_e):
+        c = int(round(float(closed[i])))
+        if c:
+            out[2 * i - 2 * N] = c
+    return out
 
 
 # ------------------------------------------------------------ Kaufman (1949)

@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 from oracle.exact_ising import (BETA_C, BruteForce, kaufman_lnZ, kaufman_observables,
-                                transfer_matrix_lnZ)
+                                transfer_matrix_dos, transfer_matrix_lnZ)
 
 BETAS = [0.0, 0.05, 0.2, 0.4, BETA_C, 0.5, 0.8, 1.0, 1.5]
 
@@ -44,6 +44,39 @@ def test_bruteforce_counts():
     assert -28 not in dos
     assert dos[-24] == 2 * 16
     assert all((e + 32) % 4 == 0 for e in dos)
+
+
+def test_transfer_matrix_dos_equals_enumeration_L4():
+    assert transfer_matrix_dos(4) == BruteForce(4).energy_dos()
+
+
+def test_transfer_matrix_dos_low_energy_counts_L6():
+    """Counts fixed by hand: from the two ground states (E = -2N) a flipped
+    cluster costs 2 per broken bond. One spin breaks 4 bonds, an adjacent
+    pair 6 (2N pairs); 8 broken bonds come from two non-adjacent spins
+    (N(N-1)/2 - 2N), straight (2N) and bent (4N) triples and 2 x 2 squares
+    (N). Flipping every spin of one sublattice maps E to -E, and the
+    level spacing is 4."""
+    g = transfer_matrix_dos(6)
+    N = 36
+    assert sum(g.values()) == 2 ** N
+    assert g[-2 * N] == 2
+    assert -2 * N + 4 not in g
+    assert g[-2 * N + 8] == 2 * N
+    assert g[-2 * N + 12] == 2 * 2 * N
+    assert g[-2 * N + 16] == 2 * (N * (N - 1) // 2 - 2 * N + 2 * N + 4 * N + N)
+    assert all(g[e] == g[-e] for e in g)
+    assert all((e + 2 * N) % 4 == 0 for e in g)
+
+
+@pytest.mark.parametrize("L", [4, 6])
+@pytest.mark.parametrize("beta", [0.1, 0.3, BETA_C, 0.7, 1.2])
+def test_transfer_matrix_dos_lnZ_vs_kaufman(L, beta):
+    g = transfer_matrix_dos(L)
+    lw = np.array([math.log(c) - beta * e for e, c in g.items()])
+    m = lw.max()
+    lnZ = m + math.log(float(np.exp(lw - m).sum()))
+    assert lnZ == pytest.approx(kaufman_lnZ(L, beta), rel=1e-12)
 
 
 def test_beta_zero_values():
