@@ -318,6 +318,16 @@ def run_engine(args):
             roofline["rng_ceiling_words_per_ns"] = eng.measure_rng_peak(2048, stream)
         except Exception as e:  # measurement only
             roofline["rng_ceiling_words_per_ns"] = f"unavailable: {e}"
+        try:
+            # measured issue rates of the instruction classes behind the derived peaks
+            mp = {"wide_mul": eng.measure_pipe_peak(eng.PIPE_WIDE_MUL, 16384, stream),
+                  "lop3": eng.measure_pipe_peak(eng.PIPE_LOP3, 16384, stream),
+                  "imad": eng.measure_pipe_peak(eng.PIPE_IMAD, 16384, stream)}
+            roofline["measured_pipe_peaks_gops"] = mp
+            roofline["frac_of_measured_wide_mul"] = achieved / mp["wide_mul"]
+            roofline["alu_pipe"]["frac_of_measured_lop3"] = ALU_OPS_PER_ATTEMPT * apn / mp["lop3"]
+        except Exception as e:  # measurement only
+            roofline["measured_pipe_peaks_gops"] = f"unavailable: {e}"
 
     # end to end through the public API with host buffers
     e2e = None

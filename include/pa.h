@@ -400,6 +400,22 @@ pa_status pa_resample_noalloc(const int32_t *dev_levels, int64_t n_old, const ui
 pa_status pa_measure_rng_peak(int64_t blocks_per_thread, uint32_t *dev_sink, void *cuda_stream,
                               double *words_per_ns);
 
+/* Measured issue rate of one integer instruction class over the whole
+ * device, the denominators behind the sweep's roofline: every thread of a
+ * 152 x 2048-thread grid (SM count x 2048) runs eight independent dependency
+ * chains for `iters` iterations (rounded down to a multiple of 4, >= 4) of
+ *   pipe 0: 32x32->64 product by a constant, halves XORed (the
+ *           Philox4x32-10 round, Sec. 3; the multiplies are counted),
+ *   pipe 1: three-input logic op (the Philox XOR, the bit-sliced neighbour
+ *           count), three per chain and iteration,
+ *   pipe 2: 32-bit multiply-add (the accept-bit insert; the LCG of Sec. 4).
+ * *lane_ops_per_ns gets instructions x threads / elapsed ns of the second of
+ * two launches (the first warms up). `dev_sink` is a device buffer of >= 4
+ * bytes per thread. Synchronous on `cuda_stream`; PA_EINVAL for a bad pipe
+ * or iteration count. */
+pa_status pa_measure_pipe_peak(int pipe, int64_t iters, uint32_t *dev_sink, void *cuda_stream,
+                               double *lane_ops_per_ns);
+
 #ifdef __cplusplus
 }
 #endif

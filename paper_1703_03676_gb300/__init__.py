@@ -112,6 +112,7 @@ SIGNATURES = [
     ("pa_weighted_average", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P]),
     ("pa_serve", ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
     ("pa_measure_rng_peak", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    ("pa_measure_pipe_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     ("pa_resample", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64, _P,
                                    ctypes.c_int64, _I64P, _P]),
     ("pa_resample_noalloc", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.c_uint64,
@@ -532,6 +533,24 @@ def measure_rng_peak(blocks_per_thread: int = 4096, stream=None) -> float:
     out = ctypes.c_double()
     _check(lib().pa_measure_rng_peak(blocks_per_thread, ctypes.c_void_p(sink.data_ptr()), _stream_handle(stream),
                                      ctypes.byref(out)), "pa_measure_rng_peak")
+    return out.value
+
+
+PIPE_WIDE_MUL, PIPE_LOP3, PIPE_IMAD = 0, 1, 2
+
+
+def measure_pipe_peak(pipe: int, iters: int = 4096, stream=None) -> float:
+    """Measured lane instructions per ns (Gop/s) of one integer instruction
+    class over the whole device: PIPE_WIDE_MUL (32x32->64 product by a
+    constant, halves XORed, as in a Philox round),
+    PIPE_LOP3 (three-input logic) or PIPE_IMAD (32-bit multiply-add)."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    sink = torch.empty(sms * 2048, dtype=torch.int32, device="cuda")
+    torch.cuda.synchronize()
+    out = ctypes.c_double()
+    _check(lib().pa_measure_pipe_peak(pipe, iters, ctypes.c_void_p(sink.data_ptr()), _stream_handle(stream),
+                                      ctypes.byref(out)), "pa_measure_pipe_peak")
     return out.value
 
 

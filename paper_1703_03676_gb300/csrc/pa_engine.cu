@@ -1473,6 +1473,32 @@ pa_status pa_measure_rng_peak(int64_t blocks_per_thread, uint32_t* sink, void* s
     return PA_OK;
 }
 
+pa_status pa_measure_pipe_peak(int pipe, int64_t iters, uint32_t* sink, void* stream, double* lane_ops_per_ns)
+{
+    if (pipe < 0 || pipe > 2 || iters < 4 || !sink || !lane_ops_per_ns) return PA_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    PA_CUDA(cudaGetDevice(&dev));
+    PA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int threads = 256, grid = sms * 8;  // 2048 resident threads per SM
+    const long long it = iters & ~3ll;
+    cudaEvent_t a, b;
+    PA_CUDA(cudaEventCreate(&a));
+    PA_CUDA(cudaEventCreate(&b));
+    PA_CUDA(pa::launch_pipe_peak(pipe, it, sink, grid, threads, s));  // warm-up
+    PA_CUDA(cudaEventRecord(a, s));
+    PA_CUDA(pa::launch_pipe_peak(pipe, it, sink, grid, threads, s));
+    PA_CUDA(cudaEventRecord(b, s));
+    PA_CUDA(cudaEventSynchronize(b));
+    float ms = 0.f;
+    PA_CUDA(cudaEventElapsedTime(&ms, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    const double per_iter = pipe == 1 ? 24.0 : 8.0;  // instructions per thread per iteration
+    *lane_ops_per_ns = per_iter * (double)it * (double)grid * threads / ((double)ms * 1e6);
+    return PA_OK;
+}
+
 }  // extern "C"
 
 // ================================================================== batches

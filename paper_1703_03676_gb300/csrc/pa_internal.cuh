@@ -171,6 +171,7 @@ cudaError_t launch_resample(const ResampleArgs& a, int tiles, cudaStream_t s);
 cudaError_t launch_sweep(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s);
 cudaError_t launch_stats(const RunDev* d_run, const RunDev& h, int step, cudaStream_t s);
 cudaError_t launch_rng_peak(long long blocks, uint32_t* sink, int grid, int threads, cudaStream_t s);
+cudaError_t launch_pipe_peak(int pipe, long long iters, uint32_t* sink, int grid, int threads, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint32_t* out, cudaStream_t s);
 
 struct BatchLaunch {
