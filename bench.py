@@ -41,7 +41,16 @@ if ROOT not in sys.path:
 METRIC = "spin-flip attempts/ns (batched vs single-run, bit-exact); p50/p99 run latency"
 UNIT = "flips/ns"
 WL = dict(L=64, R=20000, theta=100, beta_f=1.0, dbeta=0.005)
-WORKLOAD = "plain PA, 2D Ising L=64 periodic, R=20000, theta=100, beta 0->1 dbeta=0.005 (200 steps), bit-packed spins"
+DEFAULT_WL = dict(WL)
+
+
+def workload_label():
+    n = int(round(WL["beta_f"] / WL["dbeta"]))
+    return (f"plain PA, 2D Ising L={WL['L']} periodic, R={WL['R']}, theta={WL['theta']}, beta 0->1 "
+            f"dbeta={WL['dbeta']:g} ({n} steps), bit-packed spins")
+
+
+WORKLOAD = workload_label()
 # paper, program summary: 17 s on a Tesla K80 for this workload with multi-spin
 # coding (151 s single-spin); attempts = 4096 * 100 * sum R_i ~ 1.64e12
 PAPER_K80_MSC_FLIPS_PER_NS = 4096 * 100 * 200 * 20000 / 17.0 / 1e9
@@ -223,7 +232,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "sample_replicas": R_s},
+            "data": "synthetic", "config": {"workload": workload_label(), "sample_replicas": R_s},
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -246,7 +255,8 @@ def run_engine(args):
     fmt = {"bits": eng.SPIN_BITS32, "msc": eng.SPIN_MSC32, "int8": eng.SPIN_INT8,
            "replica": eng.SPIN_REPLICA8}[args.format]
     cfg = eng.PAConfig(L=L, R=WL["R"], theta=theta, beta_f=WL["beta_f"], dbeta=WL["dbeta"], seed=seed_of(0),
-                       spin_format=fmt, use_graph=True, profile=args.profile)
+                       spin_format=fmt, use_graph=True, profile=args.profile,
+                       group_threads=args.group_threads or 0)
     run = eng.PARun(cfg, stream=stream)
     n_steps = int(round(WL["beta_f"] / WL["dbeta"]))
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device=dev)  # > L2 (126 MB)
@@ -303,9 +313,12 @@ def run_engine(args):
         mul_peak = sm * 32 * clk_max * 1e6 / 1e9  # Gop/s, wide multiplies
         alu_peak = sm * 64 * clk_max * 1e6 / 1e9  # Gop/s, ALU pipe
         achieved = MUL_OPS_PER_ATTEMPT * apn
+        default_wl = WL == DEFAULT_WL
+        shape = run.launch_shape()
+        gt = shape["group_threads"]
         roofline = {"bound": "alu", "achieved": achieved, "peak": mul_peak, "unit": "Gop/s",
-                    "frac": achieved / mul_peak, "traffic": profiled_traffic(),
-                    "kernel": "k_sweep_bits<64,32>",
+                    "frac": achieved / mul_peak, "traffic": profiled_traffic() if default_wl else None,
+                    "kernel": f"k_sweep_bits<{L},{gt}>", "launch": shape,
                     "ops": "lane-varying 32x32->64 multiplies of Philox4x32-10, 4 per attempt",
                     "peak_note": "FMA-heavy pipe: SMs x 32 wide multiplies/clk x max SM clock (derived)",
                     "alu_pipe": {"achieved": ALU_OPS_PER_ATTEMPT * apn, "peak": alu_peak,
@@ -360,11 +373,13 @@ def run_engine(args):
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-                "scaling": "weak", "vs_baseline": value / PAPER_K80_MSC_FLIPS_PER_NS, "dtype": "u32",
-                "data": "synthetic",
-                "config": {"workload": WORKLOAD if args.format == "bits" else WORKLOAD.replace(
+                "scaling": "weak",
+                "vs_baseline": value / PAPER_K80_MSC_FLIPS_PER_NS if WL == DEFAULT_WL else None,
+                "dtype": "u32", "data": "synthetic",
+                "config": {"workload": workload_label() if args.format == "bits" else workload_label().replace(
                                "bit-packed spins", f"{args.format} spins"),
                            "seeds": "2+step (+100000*rank)", "spin_format": args.format,
+                           "group_threads": args.group_threads or "auto",
                            "l2": "flushed between timed steps (256 MB write)",
                            "baseline_ref": "paper K80 multi-spin-coded run, 17 s for this workload",
                            "parallelism": f"independent runs x{ws}"},
@@ -488,6 +503,12 @@ def main():
     ap.add_argument("--format", choices=["bits", "msc", "int8", "replica"], default="bits",
                     help="spin format of the default workload: bits (Philox per attempt, the reference contract), "
                          "msc (the paper's multi-spin coding with a Philox-seeded LCG), int8")
+    ap.add_argument("--L", type=int, default=None, help="override the default workload's lattice edge")
+    ap.add_argument("--R", type=int, default=None, help="override the default workload's population")
+    ap.add_argument("--theta", type=int, default=None, help="override the default workload's sweeps per step")
+    ap.add_argument("--dbeta", type=float, default=None, help="override the default workload's step size")
+    ap.add_argument("--group-threads", type=int, default=None,
+                    help="threads per replica of the bit-packed sweep (default: chosen by the engine)")
     ap.add_argument("--c4-steps", type=int, default=200)
     ap.add_argument("--serve-n", type=int, default=48)
     ap.add_argument("--serve-rdiv", type=int, default=50)
@@ -503,6 +524,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
+    for k in ("L", "R", "theta", "dbeta"):  # labelled variants of the default workload
+        if getattr(args, k) is not None:
+            WL[k] = getattr(args, k)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batched":
