@@ -268,14 +268,17 @@ const char *pa_last_error_message(void);
 /* ---- batches of independent runs ---------------------------------------
  * Many independent fixed-schedule runs (spec batching; Sec. 2.2 notes
  * that independent runs combine by free-energy weights) stepped together:
- * every phase of a temperature step is one launch for all runs and the
- * sweep is one persistent kernel whose warps take (run, replica batch) work
- * items from a single queue ordered by descending work per replica. The
- * whole schedule is one CUDA graph, captured on the first launch and reused
- * after pa_batch_reset. Each run's results are those of the same pa_config
- * run alone, bit for bit. Runs must use fixed steps (dbeta > 0), bit-packed
- * spins and L <= 256; group_threads == 0 picks the threads per replica by a
- * timed probe per L (cached per process). */
+ * every phase of a temperature step is one launch for all runs. The sweep
+ * is two persistent kernels over one queue of work items: one replica per
+ * CTA of the runs with group_threads 256 (L = 128, 256, 512), then
+ * (run, replica batch) items of the warp-group runs, each part ordered by
+ * descending work per replica. The whole schedule is one
+ * CUDA graph, captured on the first launch and reused after pa_batch_reset.
+ * Each run's results are those of the same pa_config run alone, bit for
+ * bit. Runs must use fixed steps (dbeta > 0), bit-packed spins and
+ * L <= 512 (L = 512: group_threads 256 only); group_threads == 0 picks the
+ * threads per replica by a timed probe per L (cached per process), and an
+ * unsupported group_threads gives PA_EINVAL. */
 typedef struct pa_batch pa_batch;
 
 /* Create n runs (their beta0 populations are generated). Errors as pa_create. */
@@ -298,7 +301,8 @@ pa_status pa_batch_get(pa_batch *b, int32_t i, pa_ctx **out);
  * any of the configs): [0] tables, [1] counts, [2] scan, [3] parent,
  * [4] plan + sweep, [5] stats. */
 pa_status pa_batch_phase_times(pa_batch *b, double ms[7], int64_t launches[7]);
-/* Threads per replica used for run i and the persistent sweep grid size. */
+/* Threads per replica used for run i and the persistent grid size of the
+ * sweep kernel that runs it (CTA-group or warp-group kernel). */
 pa_status pa_batch_shape(pa_batch *b, int32_t i, int32_t *group_threads, int32_t *sweep_blocks);
 void pa_batch_destroy(pa_batch *b);
 

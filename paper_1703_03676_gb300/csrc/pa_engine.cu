@@ -1532,10 +1532,10 @@ namespace {
 std::mutex g_tune_mu;
 std::map<long long, int> g_tuned;
 
-int batch_candidates(int L, int out[4])
+int batch_candidates(int L, int out[8])
 {
     int n = 0;
-    for (int g : {1, 2, 4, 8, 16, 32})
+    for (int g : {1, 2, 4, 8, 16, 32, 256})
         if (pa::batch_supports(L, g)) out[n++] = g;
     return n;
 }
@@ -1554,17 +1554,20 @@ pa_status tune_group(int L, void* stream, int* out)
             return PA_OK;
         }
     }
-    int cand[4];
+    int cand[8];
     const int nc = batch_candidates(L, cand);
     if (nc == 0) return PA_EINVAL;
+    // one population for every candidate (the same work), four rounds of the
+    // smallest group's persistent warps (16 warps per SM)
+    const long long R_probe = std::max(2048ll, 4ll * sms * 16 * (32 / std::min(cand[0], 32)));
     int best = cand[0];
     double best_ms = 1e300;
     for (int i = 0; i < nc && nc > 1; i++) {
         pa_config pc;
         pa_config_default(&pc);
         pc.L = L;
-        pc.R = std::max(2048ll, 4ll * 152 * (32 / cand[i]) * 8);
-        pc.theta = 4;
+        pc.R = R_probe;
+        pc.theta = 20;
         pc.beta_f = 0.02;
         pc.dbeta = 0.01;
         pc.spin_format = PA_SPIN_BITS32;
@@ -1684,7 +1687,7 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
     for (int i = 0; i < n; i++) {
         const pa_config& c = cfgs[i];
         PA_TRY(validate(c));
-        if (!(c.dbeta > 0.0) || c.spin_format != PA_SPIN_BITS32 || c.L > 256) return PA_EINVAL;  // bit-packed only
+        if (!(c.dbeta > 0.0) || c.spin_format != PA_SPIN_BITS32 || c.L > 512) return PA_EINVAL;  // bit-packed only
         if (c.group_threads && !pa::batch_supports(c.L, c.group_threads)) return PA_EINVAL;
     }
     pa_batch* b = new (std::nothrow) pa_batch();
@@ -1702,7 +1705,7 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
     }
     b->profile = false;
     std::vector<RunDev> hr((size_t)n);
-    int warp_words = 0;
+    int warp_words = 0, cta_words = 0, n_cta = 0;
     for (int i = 0; i < n; i++) {
         pa_config c = cfgs[i];
         if (c.profile) b->profile = true;
@@ -1719,12 +1722,20 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
         b->runs.push_back(m);
         hr[(size_t)i] = m->h;
         b->max_steps = std::max(b->max_steps, (int)m->n_fixed);
-        warp_words = std::max(warp_words, (32 / m->h.gt) * m->h.words);
+        if (m->h.gt > 32) {
+            cta_words = std::max(cta_words, m->h.words);
+            n_cta++;
+        } else {
+            warp_words = std::max(warp_words, (32 / m->h.gt) * m->h.words);
+        }
     }
-    // queue order: descending work per replica (theta * N)
+    // queue order: runs with CTA-wide groups first (the sweep's CTA phase),
+    // then descending work per replica (theta * N)
     std::vector<int> order((size_t)n), tile_run, tile_first((size_t)n);
     for (int i = 0; i < n; i++) order[(size_t)i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const bool cx = hr[(size_t)x].gt > 32, cy = hr[(size_t)y].gt > 32;
+        if (cx != cy) return cx;
         return (long long)hr[(size_t)x].theta * hr[(size_t)x].N > (long long)hr[(size_t)y].theta * hr[(size_t)y].N;
     });
     for (int i = 0; i < n; i++) {
@@ -1759,7 +1770,9 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
     b->bd.item_off = d_off;
     b->bd.work = d_work;
     b->bd.nruns = n;
+    b->bd.n_cta = n_cta;
     b->bd.warp_words = warp_words;
+    b->bd.cta_words = cta_words;
     b->ln.tiles = (int)tile_run.size();
     if (pa::plan_batch(b->bd, &b->ln) != cudaSuccess) {
         cudaGetLastError();
@@ -1832,7 +1845,7 @@ pa_status pa_batch_shape(pa_batch* b, int32_t i, int32_t* group_threads, int32_t
 {
     if (!b || i < 0 || i >= (int32_t)b->runs.size()) return PA_EINVAL;
     if (group_threads) *group_threads = b->runs[(size_t)i]->h.gt;
-    if (sweep_blocks) *sweep_blocks = b->ln.sweep_blocks;
+    if (sweep_blocks) *sweep_blocks = b->runs[(size_t)i]->h.gt > 32 ? b->ln.cta_blocks : b->ln.sweep_blocks;
     return PA_OK;
 }
 

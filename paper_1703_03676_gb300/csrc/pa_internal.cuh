@@ -148,9 +148,11 @@ struct BatchDev {
     const int* tile_run;      // copy-count tile -> run
     const int* tile_first;    // first copy-count tile of each run
     long long* item_off;      // nruns + 1 offsets of each run's work items (queue order)
-    unsigned* work;           // queue counter of the sweep
+    unsigned* work;           // queue counters of the sweep: [0] warp-group items, [1] CTA-group items
     int nruns;
-    int warp_words;           // shared-memory words per warp in the sweep
+    int n_cta;                // runs at the front of `order` whose replicas take a whole CTA
+    int warp_words;           // shared-memory words per warp in the sweep (warp-group runs)
+    int cta_words;            // shared-memory words of one replica of the CTA-group runs
 };
 
 // ---------------------------------------------------------------- launches
@@ -176,8 +178,10 @@ cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint3
 
 struct BatchLaunch {
     int tiles;                // copy-count tiles over all runs
-    int sweep_blocks;         // persistent sweep CTAs (256 threads)
+    int sweep_blocks;         // persistent CTAs (256 threads) of the warp-group sweep
     size_t sweep_smem;
+    int cta_blocks;           // persistent CTAs of the CTA-group sweep
+    size_t cta_smem;
 };
 cudaError_t plan_batch(const BatchDev& b, BatchLaunch* ln);
 cudaError_t launch_batch_step(const BatchDev& b, const BatchLaunch& ln, int step, cudaStream_t s, int phase,

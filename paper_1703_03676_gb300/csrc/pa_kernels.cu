@@ -18,6 +18,7 @@
 // at step i leaves rows 0..i-1 intact and the rest of a captured graph inert.
 #include "pa_internal.cuh"
 
+#include <algorithm>
 #include <cstdio>
 
 namespace pa {
@@ -89,8 +90,9 @@ __device__ __forceinline__ void neighbours(const uint32_t* __restrict__ O, int c
 // Sets bit T of acc when x <= thr. The 32 accept bits of a word are
 // disjoint, so the insert can be an addition: a predicated multiply-add by
 // the run-time constant unit (always 1) issues on the FMA pipe, which the
-// update leaves less busy than the integer/logic pipe the threshold select
-// and compare occupy (a compile-time 1 would be folded back into a logic op).
+// update leaves less busy than the integer/logic pipe the compares and
+// neighbour logic occupy (a compile-time 1 would be folded back into a
+// logic op).
 template <int T>
 __device__ __forceinline__ uint32_t accept_bit(uint32_t acc, uint32_t x, uint32_t thr, uint32_t unit)
 {
@@ -100,27 +102,23 @@ __device__ __forceinline__ uint32_t accept_bit(uint32_t acc, uint32_t x, uint32_
     return acc;
 }
 
-// site T compares against T8-1 when none of its neighbours disagrees, else T4-1
-template <int T>
-__device__ __forceinline__ uint32_t site_threshold(uint32_t eq0, uint32_t t4m1, uint32_t t8m1)
-{
-    return ((eq0 >> T) & 1u) ? t8m1 : t4m1;
-}
-
-// the accept bits of sites 4q .. 4q+3 from Philox block q, then blocks q+1 .. 7
+// Bits 4q .. 4q+3 of acc4 (x <= T4-1) and acc8 (x <= T8-1) from Philox
+// block q, then blocks q+1 .. 7
 template <int Q>
-__device__ __forceinline__ uint32_t accept_blocks(uint32_t acc, uint32_t eq0, unsigned c0, unsigned k, unsigned c2,
-                                                  uint32_t t4m1, uint32_t t8m1, uint32_t unit, PhiloxKey key)
+__device__ __forceinline__ void accept_blocks(uint32_t& acc4, uint32_t& acc8, unsigned c0, unsigned k, unsigned c2,
+                                              uint32_t t4m1, uint32_t t8m1, uint32_t unit, PhiloxKey key)
 {
-    if constexpr (Q == 8) {
-        return acc;
-    } else {
+    if constexpr (Q < 8) {
         const uint4 x = philox10(make_uint4(c2, c0 + Q, kTagSweep, k), key);
-        acc = accept_bit<4 * Q + 0>(acc, x.x, site_threshold<4 * Q + 0>(eq0, t4m1, t8m1), unit);
-        acc = accept_bit<4 * Q + 1>(acc, x.y, site_threshold<4 * Q + 1>(eq0, t4m1, t8m1), unit);
-        acc = accept_bit<4 * Q + 2>(acc, x.z, site_threshold<4 * Q + 2>(eq0, t4m1, t8m1), unit);
-        acc = accept_bit<4 * Q + 3>(acc, x.w, site_threshold<4 * Q + 3>(eq0, t4m1, t8m1), unit);
-        return accept_blocks<Q + 1>(acc, eq0, c0, k, c2, t4m1, t8m1, unit, key);
+        acc4 = accept_bit<4 * Q + 0>(acc4, x.x, t4m1, unit);
+        acc8 = accept_bit<4 * Q + 0>(acc8, x.x, t8m1, unit);
+        acc4 = accept_bit<4 * Q + 1>(acc4, x.y, t4m1, unit);
+        acc8 = accept_bit<4 * Q + 1>(acc8, x.y, t8m1, unit);
+        acc4 = accept_bit<4 * Q + 2>(acc4, x.z, t4m1, unit);
+        acc8 = accept_bit<4 * Q + 2>(acc8, x.z, t8m1, unit);
+        acc4 = accept_bit<4 * Q + 3>(acc4, x.w, t4m1, unit);
+        acc8 = accept_bit<4 * Q + 3>(acc8, x.w, t8m1, unit);
+        accept_blocks<Q + 1>(acc4, acc8, c0, k, c2, t4m1, t8m1, unit, key);
     }
 }
 
@@ -131,7 +129,9 @@ __device__ __forceinline__ uint32_t accept_blocks(uint32_t acc, uint32_t eq0, un
 // between the lanes of a warp, so the first-round products are warp-uniform.
 // Bit-sliced counting of the disagreeing neighbours d1..d4 gives "at least
 // two disagree" (n <= 2) and "none disagrees" (n = 4) for all 32 sites at
-// once; each site is then compared once, against the threshold its n selects.
+// once. Each site's word is compared with both thresholds into two words of
+// accept bits, and the count picks between them for all 32 sites with two
+// logic ops: cheaper than selecting a threshold per site.
 __device__ __forceinline__ uint32_t metropolis_word(uint32_t s, uint32_t same, uint32_t side, uint32_t up,
                                                     uint32_t down, unsigned c0, unsigned k, unsigned c2,
                                                     uint32_t t4m1, uint32_t t8m1, uint32_t unit, PhiloxKey key)
@@ -140,7 +140,9 @@ __device__ __forceinline__ uint32_t metropolis_word(uint32_t s, uint32_t same, u
     const uint32_t a = d1 ^ d2, b = d1 & d2, cc = d3 ^ d4, e = d3 & d4;
     const uint32_t ge2 = b | e | (a & cc);
     const uint32_t eq0 = ~(d1 | d2 | d3 | d4);
-    return s ^ (ge2 | accept_blocks<0>(0u, eq0, c0, k, c2, t4m1, t8m1, unit, key));
+    uint32_t acc4 = 0, acc8 = 0;
+    accept_blocks<0>(acc4, acc8, c0, k, c2, t4m1, t8m1, unit, key);
+    return s ^ (ge2 | (acc4 & ~eq0) | (acc8 & eq0));
 }
 
 // ======================================================== shared epilogue
@@ -753,17 +755,17 @@ __device__ __forceinline__ void msc_measure(const uint32_t* sp, int lane, unsign
     }
 }
 
-// accept bits of replicas J .. 31: LCG value j+1 of the site's seed
+// accept bits of replicas J .. 31 against both thresholds: LCG value j+1 of
+// the site's seed
 template <int J>
-__device__ __forceinline__ uint32_t msc_accept(uint32_t acc, uint32_t eq0, unsigned seed, uint32_t t4m1,
-                                               uint32_t t8m1, uint32_t unit)
+__device__ __forceinline__ void msc_accept(uint32_t& acc4, uint32_t& acc8, unsigned seed, uint32_t t4m1,
+                                           uint32_t t8m1, uint32_t unit)
 {
-    if constexpr (J == 32) {
-        return acc;
-    } else {
+    if constexpr (J < 32) {
         const unsigned xj = c_lcg.a[J + 1] * seed + c_lcg.c[J + 1];
-        acc = accept_bit<J>(acc, xj, site_threshold<J>(eq0, t4m1, t8m1), unit);
-        return msc_accept<J + 1>(acc, eq0, seed, t4m1, t8m1, unit);
+        acc4 = accept_bit<J>(acc4, xj, t4m1, unit);
+        acc8 = accept_bit<J>(acc8, xj, t8m1, unit);
+        msc_accept<J + 1>(acc4, acc8, seed, t4m1, t8m1, unit);
     }
 }
 
@@ -775,7 +777,9 @@ __device__ __forceinline__ uint32_t msc_update(uint32_t s, uint32_t n1, uint32_t
     const uint32_t a = d1 ^ d2, bb = d1 & d2, cc = d3 ^ d4, e = d3 & d4;
     const uint32_t ge2 = bb | e | (a & cc);
     const uint32_t eq0 = ~(d1 | d2 | d3 | d4);
-    return s ^ (ge2 | msc_accept<0>(0u, eq0, seed, t4m1, t8m1, unit));
+    uint32_t acc4 = 0, acc8 = 0;
+    msc_accept<0>(acc4, acc8, seed, t4m1, t8m1, unit);
+    return s ^ (ge2 | (acc4 & ~eq0) | (acc8 & eq0));
 }
 
 // Warps per 32-replica group: enough that each thread updates one to four
@@ -1328,8 +1332,10 @@ __global__ void __launch_bounds__(kOneCta) k_stats_batch(const __grid_constant__
 }
 
 // ======================================================== batched sweep
-// Work items of step `step`: ceil(R_i / (replicas per warp)) per live run,
-// laid out in queue order; the sweep's warps take items from one counter.
+// Work items of step `step`, laid out in queue order: one per replica of a
+// run with CTA-wide groups (those come first), ceil(R_i / (replicas per
+// warp)) per run with warp groups. Each of the two sweep kernels takes its
+// part of the items from its own counter.
 __global__ void k_plan(const __grid_constant__ BatchDev b, int step)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -1338,12 +1344,13 @@ __global__ void k_plan(const __grid_constant__ BatchDev b, int step)
         b.item_off[q] = acc;
         const RunDev& r = b.runs[b.order[q]];
         if (*r.status == 0 && step <= r.nsteps) {
-            const int per = 32 / r.gt;
+            const int per = r.gt > 32 ? 1 : 32 / r.gt;
             acc += (r.rec[step].R + per - 1) / per;
         }
     }
     b.item_off[b.nruns] = acc;
-    *b.work = 0u;
+    b.work[0] = 0u;  // warp-group items
+    b.work[1] = 0u;  // CTA-group items
 }
 
 template <int L, int G>
@@ -1360,31 +1367,82 @@ __device__ __forceinline__ void batch_item(const RunDev& r, int step, long long 
     if (lane == 0 && fam) atomicAdd(&r.rec[step].fam, (unsigned long long)fam);
 }
 
-// (L, G) pairs a batched sweep can run: warp groups dividing the plane
-#define PA_BATCH_SHAPES(X) X(8, 1) X(16, 2) X(16, 4) X(32, 8) X(32, 16) X(64, 16) X(64, 32) X(128, 32) X(256, 32)
+// one replica of a run with CTA-wide groups, taken by the whole CTA
+template <int L>
+__device__ __forceinline__ void batch_item_cta(const RunDev& r, int step, long long k, uint32_t* sp, unsigned* red)
+{
+    unsigned fam = 0;
+    bits_group_step<L, 256>(r, step, k, k < r.rec[step].R, sp, (int)threadIdx.x, red, fam);
+    if (threadIdx.x == 0 && fam) atomicAdd(&r.rec[step].fam, (unsigned long long)fam);
+}
 
+// (L, G) pairs a batched sweep can run: warp groups dividing the plane, and
+// one replica per 256-thread CTA for L >= 128
+#define PA_BATCH_SHAPES(X) X(8, 1) X(16, 2) X(16, 4) X(32, 8) X(32, 16) X(64, 16) X(64, 32) X(128, 32) X(256, 32)
+#define PA_BATCH_CTA_SIZES(X) X(128) X(256) X(512)
+
+// largest q in [0, n) with off[q] <= it
+__device__ __forceinline__ int batch_run_of(const long long* off, int n, long long it)
+{
+    int lo = 0, hi = n;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (off[mid] <= it) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// Persistent CTAs over the items of the CTA-group runs (the first n_cta
+// runs of the queue, items [0, item_off[n_cta])): one replica at a time,
+// colour phases separated by __syncthreads. Its own counter (work[1]).
+__global__ void __launch_bounds__(256) k_sweep_batch_cta(const __grid_constant__ BatchDev b, int step)
+{
+    extern __shared__ uint32_t smem[];
+    __shared__ long long s_off[kMaxBatchRuns + 1];
+    __shared__ unsigned s_red[256 / 32];
+    __shared__ unsigned s_item;
+    for (int i = threadIdx.x; i <= b.n_cta; i += blockDim.x) s_off[i] = b.item_off[i];
+    __syncthreads();
+    const long long end = s_off[b.n_cta];
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(b.work + 1, 1u);
+        __syncthreads();
+        const long long it = s_item;
+        __syncthreads();
+        if (it >= end) break;
+        const int q = batch_run_of(s_off, b.n_cta, it);
+        const RunDev& r = b.runs[b.order[q]];
+        const long long k = it - s_off[q];
+        switch (r.L) {
+#define PA_BATCH_CTA_CASE(LL) \
+    case LL: batch_item_cta<LL>(r, step, k, smem, s_red); break;
+            PA_BATCH_CTA_SIZES(PA_BATCH_CTA_CASE)
+#undef PA_BATCH_CTA_CASE
+        default: break;
+        }
+    }
+}
+
+// Persistent warps over the items of the warp-group runs (items
+// [item_off[n_cta], item_off[nruns])), taken one per warp from work[0].
 __global__ void __launch_bounds__(256) k_sweep_batch(const __grid_constant__ BatchDev b, int step)
 {
     extern __shared__ uint32_t smem[];
     __shared__ long long s_off[kMaxBatchRuns + 1];
     for (int i = threadIdx.x; i <= b.nruns; i += blockDim.x) s_off[i] = b.item_off[i];
     __syncthreads();
-    const long long total = s_off[b.nruns];
+    const long long total = s_off[b.nruns], first = s_off[b.n_cta];
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     uint32_t* wsm = smem + warp * b.warp_words;
     for (;;) {
-        unsigned it = 0;
-        if (lane == 0) it = atomicAdd(b.work, 1u);
-        it = __shfl_sync(0xffffffffu, it, 0);
-        if ((long long)it >= total) break;
-        int lo = 0, hi = b.nruns;  // largest q with s_off[q] <= it
-        while (hi - lo > 1) {
-            const int mid = (lo + hi) >> 1;
-            if (s_off[mid] <= (long long)it) lo = mid;
-            else hi = mid;
-        }
-        const RunDev& r = b.runs[b.order[lo]];
-        const long long item = (long long)it - s_off[lo];
+        unsigned v = 0;
+        if (lane == 0) v = atomicAdd(b.work, 1u);
+        const long long it = first + (long long)__shfl_sync(0xffffffffu, v, 0);
+        if (it >= total) break;
+        const int q = batch_run_of(s_off, b.nruns, it);
+        const RunDev& r = b.runs[b.order[q]];
+        const long long item = it - s_off[q];
         switch (r.L * 64 + r.gt) {
 #define PA_BATCH_CASE(LL, GG) \
     case LL * 64 + GG: batch_item<LL, GG>(r, step, item, wsm); break;
@@ -1628,6 +1686,15 @@ cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint3
 
 bool batch_supports(int L, int gt)
 {
+    if (gt == 256) {
+        switch (L) {
+#define PA_BATCH_CTA_OK(LL) case LL:
+            PA_BATCH_CTA_SIZES(PA_BATCH_CTA_OK)
+#undef PA_BATCH_CTA_OK
+            return true;
+        default: return false;
+        }
+    }
     switch (L * 64 + gt) {
 #define PA_BATCH_OK(LL, GG) case LL * 64 + GG:
         PA_BATCH_SHAPES(PA_BATCH_OK)
@@ -1644,8 +1711,10 @@ cudaError_t plan_batch(const BatchDev& b, BatchLaunch* ln)
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
-    const size_t smem = (size_t)8 * b.warp_words * 4;
-    if (smem + (kMaxBatchRuns + 1) * 8 > (size_t)max_optin) return cudaErrorInvalidConfiguration;
+    const size_t fixed = (kMaxBatchRuns + 1) * 8 + 64;  // static shared memory of both kernels
+    // warp-group kernel
+    const size_t smem = (size_t)std::max(8 * b.warp_words, 1) * 4;
+    if (smem + fixed > (size_t)max_optin) return cudaErrorInvalidConfiguration;
     if ((e = cudaFuncSetAttribute((const void*)k_sweep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
         cudaSuccess)
         return e;
@@ -1653,6 +1722,17 @@ cudaError_t plan_batch(const BatchDev& b, BatchLaunch* ln)
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     ln->sweep_blocks = sms * per_sm;
     ln->sweep_smem = smem;
+    // CTA-group kernel
+    const size_t csmem = (size_t)std::max(b.cta_words, 1) * 4;
+    if (csmem + fixed > (size_t)max_optin) return cudaErrorInvalidConfiguration;
+    if ((e = cudaFuncSetAttribute((const void*)k_sweep_batch_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)csmem)) != cudaSuccess)
+        return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_batch_cta, 256, csmem)) != cudaSuccess)
+        return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    ln->cta_blocks = sms * per_sm;
+    ln->cta_smem = csmem;
     return cudaSuccess;
 }
 
@@ -1669,7 +1749,11 @@ cudaError_t launch_batch_step(const BatchDev& b, const BatchLaunch& ln, int step
     case 4:
         k_plan<<<1, 32, 0, s>>>(b, step);
         if (cudaPeekAtLastError() != cudaSuccess) break;
-        k_sweep_batch<<<ln.sweep_blocks, 256, ln.sweep_smem, s>>>(b, step);
+        if (b.n_cta > 0) {
+            k_sweep_batch_cta<<<ln.cta_blocks, 256, ln.cta_smem, s>>>(b, step);
+            if (cudaPeekAtLastError() != cudaSuccess) break;
+        }
+        if (b.n_cta < b.nruns) k_sweep_batch<<<ln.sweep_blocks, 256, ln.sweep_smem, s>>>(b, step);
         break;
     case 5: k_stats_batch<<<b.nruns, kOneCta, 0, s>>>(b, step); break;
     default: return cudaErrorInvalidValue;

@@ -1,7 +1,7 @@
 """Batched runs (pa_batch_*): every run of a batch gives the same results as
 the same configuration run alone, bit for bit, whatever the threads per
-replica chosen for it, after a reset with new seeds, and when another run
-of the batch fails."""
+replica chosen for it (warp groups or one replica per CTA), after a reset
+with new seeds, and when another run of the batch fails."""
 import numpy as np
 import pytest
 
@@ -77,6 +77,39 @@ def test_batch_group_shapes_do_not_change_results():
     b.run()
     check_same(b, refs)
     b.close()
+
+
+def test_batch_cta_groups_mixed_with_warp_groups():
+    """Runs with one replica per 256-thread CTA (L >= 128, including L = 512,
+    which has no warp-group shape) are taken first by whole CTAs, the rest
+    by warps, in the same launch; every run is bit-identical to itself run
+    alone."""
+    mix = [(128, 300, 2, 0.2, 0.1, 111), (64, 900, 2, 0.2, 0.1, 112), (512, 24, 1, 0.2, 0.1, 113),
+           (16, 700, 3, 0.3, 0.1, 114), (256, 60, 1, 0.3, 0.15, 115), (32, 400, 2, 0.2, 0.1, 116)]
+    shapes = {128: 256, 64: 32, 512: 256, 16: 4, 256: 256, 32: 16}
+    refs = [alone(cfg(*m)) for m in mix]
+    b = eng.PABatch([cfg(*m, group_threads=shapes[m[0]]) for m in mix])
+    for i, m in enumerate(mix):
+        assert b.shape(i)["group_threads"] == shapes[m[0]]
+    b.run()
+    check_same(b, refs)
+    b.close()
+
+
+def test_batch_of_cta_group_runs_only():
+    mix = [(128, 200, 2, 0.2, 0.1, 121), (256, 30, 1, 0.2, 0.1, 122), (128, 77, 3, 0.3, 0.1, 123)]
+    refs = [alone(cfg(*m)) for m in mix]
+    b = eng.PABatch([cfg(*m, group_threads=256) for m in mix])
+    b.run()
+    check_same(b, refs)
+    b.close()
+
+
+def test_batch_rejects_unsupported_group_shape():
+    with pytest.raises(eng.PAError):
+        eng.PABatch([cfg(64, 100, 1, 0.1, 0.1, 1, group_threads=256)])
+    with pytest.raises(eng.PAError):
+        eng.PABatch([cfg(512, 10, 1, 0.1, 0.1, 1, group_threads=32)])
 
 
 def test_batch_reset_with_new_seeds():
