@@ -58,6 +58,11 @@ CASES = [
     ("L10-int8", 10, 1100, 2, 0.4, 0.1, 15, I8),
     ("L6-replica-parallel", 6, 700, 2, 0.4, 0.1, 17, RP),
     ("L16-replica-parallel-ragged", 16, 1300, 3, 0.3, 0.05, 18, RP),
+    # degenerate populations: one replica (one level, tau = 1: resampling is
+    # the identity) and two
+    ("R1-bits", 16, 1, 3, 0.5, 0.1, 21, B32),
+    ("R1-int8", 6, 1, 2, 0.4, 0.2, 23, I8),
+    ("R2-bits", 8, 2, 2, 0.6, 0.2, 22, B32),
 ]
 
 CTA_CASES = [

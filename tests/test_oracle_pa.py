@@ -60,6 +60,19 @@ def test_identity_resampling_at_zero_step():
     assert S == 1000.0 and np.all(F == 1) and np.all(U == 0)
 
 
+def test_single_replica_population_is_kept():
+    """R = 1: one occupied level, S = t[0] = 1 and tau_hat = R t / S = 1
+    exactly, so every step copies the one replica once (Eq. tau with
+    R_{i-1} = R = 1); the population never grows, dies or splits."""
+    pa = PopulationAnnealing(16, 1, 3, beta_f=0.5, dbeta=0.1, seed=21)
+    pa.run()
+    assert [r.R for r in pa.rows] == [1] * 6
+    assert all(r.families == 1 for r in pa.rows)
+    # Eq. Q with one replica: Q_i = exp(-dbeta E_{i-1}) exactly
+    for prev, r in zip(pa.rows[:-1], pa.rows[1:]):
+        assert r.lnQ == pytest.approx(-0.1 * prev.e * 256, rel=1e-12, abs=1e-12)
+
+
 def test_copy_number_law():
     """r_j in {floor, floor+1} with Pr[floor+1] = frac(tau_hat): check the
     empirical frequency over many independent resampling streams."""
