@@ -61,6 +61,9 @@ PAPER_K80_MSC_FLIPS_PER_NS = 4096 * 100 * 200 * 20000 / 17.0 / 1e9
 #    first-round products are the same for all lanes of a warp, leaving 16
 #    lane-varying multiplies and 18 XORs, i.e. 4 and 4.5 per attempt;
 #  - one threshold comparison and ~0.5 logic ops (15 LOP3 per 32-site word).
+#    (The kernel compares each word with both thresholds and lets the
+#    neighbour count pick, two compares per site: cheaper than selecting the
+#    threshold; the count here is the algorithmic one.)
 # A wide multiply occupies the FMA-heavy pipe for 4 cycles per warp (32 lanes
 # per SM per clock, measured: the Philox-only kernel reaches 84% of it); LOP3
 # and compares go to the ALU pipe (64 lanes per SM per clock).
