@@ -10,7 +10,7 @@ uses beta_c = ln(1 + sqrt 2)/2. Four independent routes are given here:
 
 * ``brute_force`` enumerates all 2^N states of a tiny lattice (N <= 20),
   also with +-J couplings (the disordered models the paper's method
-  targets);
+  targets) and for the simple cubic 2 x 2 x 2 torus;
 * ``transfer_matrix_lnZ`` evaluates Z = Tr T^L with the row-to-row transfer
   matrix (L <= 10);
 * ``transfer_matrix_dos`` counts the exact integer density of states g(E)
@@ -53,6 +53,23 @@ def enumerate_states_j(L: int, Jr, Jd):
     return E.astype(np.int64), s.sum(axis=(1, 2)).astype(np.int64)
 
 
+def enumerate_states3(L: int):
+    """E and M of all 2^(L^3) states of the simple cubic L x L x L torus:
+    E = -sum over every site's +x, +y and +z bond (for L = 2 the +x and -x
+    neighbours coincide, so each such pair carries two bonds)."""
+    N = L ** 3
+    if N > 20:
+        raise ValueError("brute force limited to N <= 20")
+    idx = np.arange(1 << N, dtype=np.int64)
+    s = np.empty((1 << N, L, L, L), dtype=np.int32)  # [state, z, y, x]
+    for z in range(L):
+        for y in range(L):
+            for x in range(L):
+                s[:, z, y, x] = ((idx >> ((z * L + y) * L + x)) & 1) * 2 - 1
+    E = -(s * (np.roll(s, -1, axis=3) + np.roll(s, -1, axis=2) + np.roll(s, -1, axis=1))).sum(axis=(1, 2, 3))
+    return E.astype(np.int64), s.sum(axis=(1, 2, 3)).astype(np.int64)
+
+
 def enumerate_states(L: int):
     """Energy and magnetisation of every one of the 2^(L*L) configurations.
 
@@ -74,12 +91,16 @@ def enumerate_states(L: int):
 
 
 class BruteForce:
-    """Exact canonical averages of a tiny torus by full enumeration."""
+    """Exact canonical averages of a tiny torus by full enumeration (square
+    lattice, or simple cubic with dim = 3)."""
 
-    def __init__(self, L: int, couplings=None):
+    def __init__(self, L: int, couplings=None, dim: int = 2):
         self.L = L
-        self.N = L * L
-        E, M = enumerate_states(L) if couplings is None else enumerate_states_j(L, *couplings)
+        self.N = L ** dim
+        if dim == 3:
+            E, M = enumerate_states3(L)
+        else:
+            E, M = enumerate_states(L) if couplings is None else enumerate_states_j(L, *couplings)
         # joint density of states g(E, M) as integer counts
         keys, counts = np.unique(np.stack([E, M], axis=1), axis=0, return_counts=True)
         self.E = keys[:, 0].astype(np.float64)

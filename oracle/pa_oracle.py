@@ -1,4 +1,5 @@
-"""Population annealing for the 2D Ising model: the oracle's step logic.
+"""Population annealing for the Ising model (square lattice; also the simple
+cubic one): the oracle's step logic.
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
@@ -14,6 +15,9 @@ estimate of the density of states (Eq. MHReq1).
 Readings where the paper is silent (each listed in the design notes):
 
 * Energy level k = (E + 2N)/4 in [0, N]; magnetisation level m = (M + N)/2.
+  On the simple cubic lattice (dim = 3) k = (E + 3N)/4 in [0, 3N/2], and a
+  flip with all six neighbours aligned (dE = 12) needs x < ceil(exp(-12 beta)
+  2^32).
 * No sweeps at beta0: the random start is already in equilibrium there
   (Sec. 2.1); row 0 is emitted with ln Q_0 = 0.
 * Fixed schedule: n = round((beta_f - beta0)/dbeta) steps with
@@ -77,23 +81,31 @@ def philox_many(ctr: np.ndarray, seed: int) -> np.ndarray:
     return out
 
 
-def init_spins(L: int, slots: np.ndarray, seed: int) -> np.ndarray:
+def init_spins(L: int, slots: np.ndarray, seed: int, dim: int = 2) -> np.ndarray:
     import ctypes
     slots = np.ascontiguousarray(slots, dtype=np.int64)
-    s = np.empty((slots.size, L, L), dtype=np.int8)
-    core().oracle_init(L, slots.size, _ptr(slots, ctypes.c_int64), seed, _ptr(s, ctypes.c_int8))
+    s = np.empty((slots.size,) + (L,) * dim, dtype=np.int8)
+    fn = core().oracle_init3 if dim == 3 else core().oracle_init
+    fn(L, slots.size, _ptr(slots, ctypes.c_int64), seed, _ptr(s, ctypes.c_int8))
     return s
 
 
 def sweep(s: np.ndarray, slots: np.ndarray, seed: int, u0: int, theta: int, T4: int, T8: int,
-          msc: bool = False, couplings=None) -> None:
+          msc: bool = False, couplings=None, T12: int | None = None) -> None:
     """theta sweeps in place on s[r] (replica slot slots[r]); msc selects the
     multi-spin-coded random numbers (Philox-seeded LCG per 32 replicas);
-    couplings = (Jr, Jd) int8 L x L arrays of the +-J model."""
+    couplings = (Jr, Jd) int8 L x L arrays of the +-J model. A 3D population
+    (s of shape (n, L, L, L)) needs T12 for flips with all six neighbours
+    aligned."""
     import ctypes
     assert s.dtype == np.int8 and s.flags.c_contiguous
     slots = np.ascontiguousarray(slots, dtype=np.int64)
     L = s.shape[1]
+    if s.ndim == 4:
+        assert not msc and couplings is None and T12 is not None
+        core().oracle_sweep3(L, slots.size, _ptr(slots, ctypes.c_int64), seed, u0, theta, T4, T8, T12,
+                             _ptr(s, ctypes.c_int8))
+        return
     if couplings is not None:
         assert not msc
         Jr = np.ascontiguousarray(couplings[0], dtype=np.int8)
@@ -111,6 +123,11 @@ def measure(s: np.ndarray, couplings=None) -> tuple[np.ndarray, np.ndarray]:
     n = s.shape[0]
     E = np.empty(n, dtype=np.int64)
     M = np.empty(n, dtype=np.int64)
+    if s.ndim == 4:
+        assert couplings is None
+        core().oracle_measure3(s.shape[1], n, _ptr(s, ctypes.c_int8), _ptr(E, ctypes.c_int64),
+                               _ptr(M, ctypes.c_int64))
+        return E, M
     if couplings is not None:
         Jr = np.ascontiguousarray(couplings[0], dtype=np.int8)
         Jd = np.ascontiguousarray(couplings[1], dtype=np.int8)
@@ -135,10 +152,11 @@ def metropolis_threshold(beta: float, dE: int) -> int:
     return int(math.ceil(math.ldexp(math.exp(-float(dE) * beta), 32)))
 
 
-def pad_size(N: int) -> int:
-    """Smallest power of two >= N + 1 (the number of energy levels)."""
+def pad_size(K: int) -> int:
+    """Smallest power of two >= K + 1, the number of energy levels (K, the
+    highest level, is N in 2D and 3N/2 in 3D)."""
     P = 1
-    while P < N + 1:
+    while P < K + 1:
         P *= 2
     return P
 
@@ -160,10 +178,10 @@ def level_weights(delta: float, ndiff: int) -> np.ndarray:
     return np.array([math.exp(-(f * float(d))) for d in range(ndiff)], dtype=np.float64)
 
 
-def normaliser_S(H: np.ndarray, kmin: int, kmax: int, t: np.ndarray, N: int) -> float:
+def normaliser_S(H: np.ndarray, kmin: int, kmax: int, t: np.ndarray, K: int) -> float:
     """S = sum_k H[k] t[k - kmin] by the fixed pairwise tree (Eq. Q up to the
-    factor exp(-dbeta E_min) / R_{i-1})."""
-    T = np.zeros(pad_size(N), dtype=np.float64)
+    factor exp(-dbeta E_min) / R_{i-1}); K is the highest energy level."""
+    T = np.zeros(pad_size(K), dtype=np.float64)
     T[kmin:kmax + 1] = H[kmin:kmax + 1].astype(np.float64) * t[: kmax - kmin + 1]
     return pairwise_sum(T)
 
@@ -177,27 +195,27 @@ def copy_tables(R: int, t: np.ndarray, S: float):
     return tau, F.astype(np.int64), U.astype(np.int64)
 
 
-def overlap_alpha(H: np.ndarray, kmin: int, kmax: int, R: int, R_prev: int, delta: float, N: int) -> float:
+def overlap_alpha(H: np.ndarray, kmin: int, kmax: int, R: int, R_prev: int, delta: float, K: int) -> float:
     """Histogram overlap of Sec. 2.3: (1/R_{i-1}) sum_j min(1, tau_hat_j),
-    evaluated over levels in ascending order."""
+    evaluated over levels in ascending order (K: the highest energy level)."""
     t = level_weights(delta, kmax - kmin + 1)
-    S = normaliser_S(H, kmin, kmax, t, N)
+    S = normaliser_S(H, kmin, kmax, t, K)
     acc = 0.0
     for k in range(kmin, kmax + 1):
         acc += float(H[k]) * min(1.0, (float(R) * float(t[k - kmin])) / S)
     return acc / float(R_prev)
 
 
-def choose_delta(H, kmin, kmax, R, R_prev, beta, beta_f, target, N):
+def choose_delta(H, kmin, kmax, R, R_prev, beta, beta_f, target, K):
     """Adaptive step (Sec. 2.3): largest delta found by 60 bisection steps
     with alpha(delta) >= target; the whole remaining interval if it passes."""
     dmax = beta_f - beta
-    if overlap_alpha(H, kmin, kmax, R, R_prev, dmax, N) >= target:
+    if overlap_alpha(H, kmin, kmax, R, R_prev, dmax, K) >= target:
         return dmax, True
     lo, hi = 0.0, dmax
     for _ in range(60):
         mid = 0.5 * (lo + hi)
-        if overlap_alpha(H, kmin, kmax, R, R_prev, mid, N) >= target:
+        if overlap_alpha(H, kmin, kmax, R, R_prev, mid, K) >= target:
             lo = mid
         else:
             hi = mid
@@ -217,6 +235,7 @@ class StepRecord:
     lnQ: float = 0.0
     T4: int = 0
     T8: int = 0
+    T12: int = 0                    # 3D only (six aligned neighbours)
     H_E: np.ndarray | None = None   # histogram of this step's population
     H_M: np.ndarray | None = None
     counts: np.ndarray | None = None  # r_j of the previous population
@@ -269,19 +288,28 @@ def make_row(beta: float, N: int, R: int, sums, sum_lnQ: float, lnQ: float, fami
 
 
 class PopulationAnnealing:
-    """One PA run of the 2D Ising model, step by step (Sec. 2.1)."""
+    """One PA run of the Ising model, step by step (Sec. 2.1): the square
+    lattice (dim = 2, Sec. 3) or the simple cubic one (dim = 3). Energy
+    levels are k = (E + dim N)/4 = 0 .. dim N/2."""
 
     def __init__(self, L: int, R: int, theta: int, beta_f: float = 1.0, dbeta: float = 0.01,
                  seed: int = 1, beta0: float = 0.0, overlap: float = 0.85,
                  capacity: int = 0, record_hist: bool = True, schedule=None, msc: bool = False,
-                 couplings=None):
-        if L < 4 or L % 2:
-            raise ValueError("L must be even and >= 4")
+                 couplings=None, dim: int = 2):
+        if dim not in (2, 3):
+            raise ValueError("dim must be 2 or 3")
+        if L % 2 or L < (4 if dim == 2 else 2):
+            raise ValueError("L must be even and >= 4 (>= 2 in 3D)")
+        if dim == 3 and (msc or couplings is not None):
+            raise ValueError("the 3D model has plain Philox sweeps and J = 1")
         if beta0 != 0.0:
             raise ValueError("beta0 must be 0 (Z_beta0 = 2^N is known only there)")
         if R < 1 or theta < 1 or not (beta_f > beta0):
             raise ValueError("bad R, theta or beta_f")
-        self.L, self.N, self.R, self.theta = L, L * L, int(R), int(theta)
+        self.dim = dim
+        self.L, self.N, self.R, self.theta = L, L ** dim, int(R), int(theta)
+        self.eoff = dim * self.N          # E_k = 4 k - eoff
+        self.nl = dim * self.N // 2 + 1   # energy levels
         self.seed = int(seed)
         self.beta_f = float(beta_f)
         self.dbeta = float(dbeta)
@@ -313,28 +341,28 @@ class PopulationAnnealing:
         self.partial = False
         # step 0: random configurations at beta0 = 0, measured, no sweeps
         slots = np.arange(self.R, dtype=np.int64)
-        self.pop = init_spins(L, slots, self.seed)
+        self.pop = init_spins(L, slots, self.seed, dim)
         self.E, self.M = measure(self.pop, self.J)
         self.fam = np.arange(self.R, dtype=np.int64)
         self.sum_lnQ = 0.0
-        self.Hsum = np.zeros(self.N + 1, dtype=np.int64)
+        self.Hsum = np.zeros(self.nl, dtype=np.int64)
         # per energy level, summed over every measured replica of every step:
         # sum |M|, sum M^2, sum M^4 (Python ints, exact)
-        self.Msums = [[0, 0, 0] for _ in range(self.N + 1)]
+        self.Msums = [[0, 0, 0] for _ in range(self.nl)]
         self.records: list[StepRecord] = []
         self.rows: list[Row] = []
         self._measure_and_record(StepRecord(step=0, beta=0.0, delta=0.0, R=self.R, R_prev=self.R))
 
     # -- helpers
     def levels(self) -> np.ndarray:
-        return (self.E + 2 * self.N) // 4
+        return (self.E + self.eoff) // 4
 
     def mlevels(self) -> np.ndarray:
         return (self.M + self.N) // 2
 
     def _measure_and_record(self, rec: StepRecord):
         N = self.N
-        H_E = np.bincount(self.levels(), minlength=N + 1).astype(np.int64)
+        H_E = np.bincount(self.levels(), minlength=self.nl).astype(np.int64)
         H_M = np.bincount(self.mlevels(), minlength=N + 1).astype(np.int64)
         self.Hsum += H_E
         for k, m in zip(self.levels().tolist(), self.M.tolist()):
@@ -365,7 +393,8 @@ class PopulationAnnealing:
         i = self.step_index + 1
         R_prev = self.E.size
         lv = self.levels()
-        H = np.bincount(lv, minlength=N + 1).astype(np.int64)
+        K = self.nl - 1
+        H = np.bincount(lv, minlength=self.nl).astype(np.int64)
         occ = np.nonzero(H)[0]
         kmin, kmax = int(occ[0]), int(occ[-1])
         if self.schedule is not None:
@@ -373,7 +402,7 @@ class PopulationAnnealing:
             delta = beta_new - self.beta
             final = i == self.n_fixed
         elif self.adaptive:
-            delta, final = choose_delta(H, kmin, kmax, R, R_prev, self.beta, self.beta_f, self.overlap, N)
+            delta, final = choose_delta(H, kmin, kmax, R, R_prev, self.beta, self.beta_f, self.overlap, K)
             if delta <= 0.0:
                 raise OracleError("stalled", "adaptive step found no positive delta")
             beta_new = self.beta_f if final else self.beta + delta
@@ -383,7 +412,7 @@ class PopulationAnnealing:
             final = i == self.n_fixed
         # Eq. Q with the E_min shift, and the copy numbers of Eq. resampling-factors
         t = level_weights(delta, kmax - kmin + 1)
-        S = normaliser_S(H, kmin, kmax, t, N)
+        S = normaliser_S(H, kmin, kmax, t, K)
         _, F, U = copy_tables(R, t, S)
         x = resample_words(self.seed, i, R_prev).astype(np.int64)
         d = lv - kmin
@@ -394,12 +423,13 @@ class PopulationAnnealing:
         if R_new == 0:
             raise OracleError("extinct", f"population died out at step {i}")
         parent = np.repeat(np.arange(R_prev, dtype=np.int64), r)
-        E_min = -2 * N + 4 * kmin
+        E_min = -self.eoff + 4 * kmin
         lnQ = (math.log(S) - math.log(float(R_prev))) - delta * float(E_min)
         T4 = metropolis_threshold(beta_new, 4)
         T8 = metropolis_threshold(beta_new, 8)
+        T12 = metropolis_threshold(beta_new, 12) if self.dim == 3 else None
         rec = StepRecord(step=i, beta=beta_new, delta=delta, R=R_new, R_prev=R_prev, kmin_prev=kmin,
-                         S=S, lnQ=lnQ, T4=T4, T8=T8, counts=r if self.record_hist else None)
+                         S=S, lnQ=lnQ, T4=T4, T8=T8, T12=T12 or 0, counts=r if self.record_hist else None)
         rec.parent = parent
         u0 = (i - 1) * self.theta
         if sample is not None:
@@ -407,7 +437,7 @@ class PopulationAnnealing:
                 sample = sample(R_new)
             sample = np.asarray(sample, dtype=np.int64)
             sub = np.ascontiguousarray(self.pop[parent[sample]])
-            sweep(sub, sample, self.seed, u0, self.theta, T4, T8, msc=self.msc, couplings=self.J)
+            sweep(sub, sample, self.seed, u0, self.theta, T4, T8, msc=self.msc, couplings=self.J, T12=T12)
             rec.sample = sample
             rec.sample_pop = sub
             rec.sample_E, rec.sample_M = measure(sub, self.J)
@@ -418,7 +448,7 @@ class PopulationAnnealing:
         self.pop = np.ascontiguousarray(self.pop[parent])
         self.fam = self.fam[parent]
         sweep(self.pop, np.arange(R_new, dtype=np.int64), self.seed, u0, self.theta, T4, T8, msc=self.msc,
-              couplings=self.J)
+              couplings=self.J, T12=T12)
         self.E, self.M = measure(self.pop, self.J)
         self.step_index = i
         self.beta = beta_new
@@ -437,12 +467,12 @@ class PopulationAnnealing:
         ln Omega_k = ln Hsum_k - LSE_i(ln R_i + beta_i F_i - beta_i E_k),
         beta_i F_i = -(N ln 2 + sum_{l<=i} ln Q_l)."""
         N = self.N
-        E_k = (-2 * N + 4 * np.arange(N + 1)).astype(np.float64)
+        E_k = (-self.eoff + 4 * np.arange(self.nl)).astype(np.float64)
         betas = np.array([r.beta for r in self.rows])
         lnR = np.log(np.array([float(r.R) for r in self.rows]))
         bF = np.array([r.betaF_per_N for r in self.rows]) * N
-        out = np.full(N + 1, -np.inf)
-        for k in range(N + 1):
+        out = np.full(self.nl, -np.inf)
+        for k in range(self.nl):
             if self.Hsum[k] > 0:
                 a = lnR + bF - betas * E_k[k]
                 m = a.max()

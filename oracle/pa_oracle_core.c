@@ -32,6 +32,11 @@
  * where c = (x+y)&1 is the checkerboard colour of site (x, y),
  * b = y*(L/2) + (x>>1) its index within the colour, k the replica slot,
  * u the global sweep number, i the temperature step and j the old slot.
+ *
+ * The three-dimensional model (the simple cubic L x L x L torus, one of the
+ * other models the paper's conclusion names for the method) uses the same
+ * streams with c = (x+y+z)&1 and b = (z*L + y)*(L/2) + (x>>1), spins stored
+ * as s[(z*L + y)*L + x].
  */
 #include <stdint.h>
 #include <stddef.h>
@@ -293,4 +298,94 @@ void oracle_philox_many(int64_t n, const uint32_t *ctr, uint64_t seed, uint32_t 
     uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
     for (int64_t r = 0; r < n; r++)
         oracle_philox4x32_10(ctr + 4 * r, key, out + 4 * r);
+}
+
+/* ------------------------------------------------------------------ 3D
+ * Simple cubic L x L x L torus, H = -sum over the 3N bonds (each site's +x,
+ * +y and +z neighbour). A flip changes the energy by dE = 2 s_i sum_nb s_j =
+ * 4 n - 12 with n the number of the six neighbours aligned with s_i:
+ * always accepted for n <= 3, with probability exp(-4 beta), exp(-8 beta),
+ * exp(-12 beta) for n = 4, 5, 6, i.e. iff the SWEEP word is < T4, T8, T12.
+ * L = 2 is allowed here: the +x and -x neighbours are then the same site,
+ * counted twice, consistently in the energy and in dE.
+ */
+static int site3(int L, int x, int y, int z)
+{
+    return (z * L + y) * L + x;
+}
+
+void oracle_init3(int L, int64_t n, const int64_t *slot, uint64_t seed, int8_t *s)
+{
+    const int N = L * L * L, half = L / 2;
+    for (int64_t r = 0; r < n; r++) {
+        int8_t *S = s + (size_t)r * N;
+        uint32_t k = (uint32_t)slot[r];
+        for (int z = 0; z < L; z++)
+            for (int y = 0; y < L; y++)
+                for (int x = 0; x < L; x++) {
+                    uint32_t c = (uint32_t)((x + y + z) & 1);
+                    uint32_t b = (uint32_t)((z * L + y) * half + (x >> 1));
+                    uint32_t g = c * (uint32_t)(N / 2) + b;
+                    uint32_t w = stream_word(seed, 0u, g >> 2, 0u, k, g & 3u);
+                    S[site3(L, x, y, z)] = (w < 0x80000000u) ? 1 : -1;
+                }
+    }
+}
+
+void oracle_sweep3(int L, int64_t n, const int64_t *slot, uint64_t seed, int64_t u0, int theta, uint64_t T4,
+                   uint64_t T8, uint64_t T12, int8_t *s)
+{
+    const int N = L * L * L, half = L / 2;
+    for (int64_t r = 0; r < n; r++) {
+        int8_t *S = s + (size_t)r * N;
+        uint32_t k = (uint32_t)slot[r];
+        for (int sw = 0; sw < theta; sw++) {
+            uint32_t u = (uint32_t)(u0 + sw);
+            for (int c = 0; c < 2; c++) {
+                for (int z = 0; z < L; z++)
+                    for (int y = 0; y < L; y++)
+                        for (int x = 0; x < L; x++) {
+                            if (((x + y + z) & 1) != c)
+                                continue;
+                            int si = S[site3(L, x, y, z)];
+                            int aligned = (S[site3(L, (x + 1) % L, y, z)] == si) +
+                                          (S[site3(L, (x + L - 1) % L, y, z)] == si) +
+                                          (S[site3(L, x, (y + 1) % L, z)] == si) +
+                                          (S[site3(L, x, (y + L - 1) % L, z)] == si) +
+                                          (S[site3(L, x, y, (z + 1) % L)] == si) +
+                                          (S[site3(L, x, y, (z + L - 1) % L)] == si);
+                            int flip;
+                            if (aligned <= 3) {
+                                flip = 1;  /* dE <= 0 */
+                            } else {
+                                uint32_t b = (uint32_t)((z * L + y) * half + (x >> 1));
+                                uint32_t w = stream_word(seed, 2u * u + (uint32_t)c, b >> 2, 1u, k, b & 3u);
+                                uint64_t T = (aligned == 4) ? T4 : (aligned == 5) ? T8 : T12;
+                                flip = ((uint64_t)w < T);
+                            }
+                            if (flip)
+                                S[site3(L, x, y, z)] = (int8_t)(-si);
+                        }
+            }
+        }
+    }
+}
+
+void oracle_measure3(int L, int64_t n, const int8_t *s, int64_t *E, int64_t *M)
+{
+    const int N = L * L * L;
+    for (int64_t r = 0; r < n; r++) {
+        const int8_t *S = s + (size_t)r * N;
+        int64_t e = 0, m = 0;
+        for (int z = 0; z < L; z++)
+            for (int y = 0; y < L; y++)
+                for (int x = 0; x < L; x++) {
+                    int si = S[site3(L, x, y, z)];
+                    e -= si * (S[site3(L, (x + 1) % L, y, z)] + S[site3(L, x, (y + 1) % L, z)] +
+                               S[site3(L, x, y, (z + 1) % L)]);
+                    m += si;
+                }
+        E[r] = e;
+        M[r] = m;
+    }
 }
