@@ -89,7 +89,15 @@ typedef struct {
     int32_t use_graph;      /* != 0: pa_run captures the fixed schedule as one
                                CUDA graph                                       */
     int32_t profile;        /* != 0: time every kernel phase with CUDA events     */
-    int32_t reserved[3];    /* must be 0                                          */
+    int32_t dim;            /* 0 or 2: the L x L square lattice (Sec. 3); 3: the
+                               L x L x L simple cubic lattice, N = L^3, with
+                               PA_SPIN_BITS32 and L in {8, 16, 32, 64} only
+                               (one of the further models the paper's
+                               conclusion names; energy levels k = (E + 3N)/4
+                               = 0 .. 3N/2, so every histogram has 3N/2 + 1
+                               entries; magnetisation levels use the first
+                               N + 1)                                           */
+    int32_t reserved[2];    /* must be 0                                          */
 } pa_config;
 
 /* One output row (Sec. 3 "Further optimization and parameters": beta, e, C,
@@ -192,16 +200,20 @@ pa_status pa_observables(pa_ctx *ctx, pa_obs *rows, int64_t cap, int64_t *n_rows
 /* Step bookkeeping of completed step `step` (0 <= step < rows). */
 pa_status pa_step_info_get(pa_ctx *ctx, int64_t step, pa_step_info *out);
 
-/* Histogram over levels 0..N (N = L*L) into host `out` (cap >= N + 1):
- * PA_HIST_E: energy levels k = (E + 2N)/4 of step `step`;
- * PA_HIST_M: magnetisation levels m = (M + N)/2 of step `step`;
+/* Histogram of nlev entries into host `out` (cap >= nlev), where nlev =
+ * N + 1 on the square lattice (N = L*L) and 3N/2 + 1 on the simple cubic
+ * one (N = L^3):
+ * PA_HIST_E: energy levels k = (E + dim N)/4 of step `step`;
+ * PA_HIST_M: magnetisation levels m = (M + N)/2 of step `step` (entries
+ * above N are 0);
  * PA_HIST_ESUM: sum of the energy histograms of steps 0..last (Sec. 2.4;
  * `step` ignored). Per-step kinds need record_histograms, else PA_ESTATE
  * (the latest step is always available). */
 pa_status pa_histogram(pa_ctx *ctx, int64_t step, int32_t kind, int64_t *out, int64_t cap);
 
-/* Current population in natural layout: host_out[r*L*L + y*L + x] = +1 / -1
- * for replica slot r < *n (cap is in replicas). */
+/* Current population in natural layout: host_out[r*N + y*L + x] = +1 / -1
+ * (simple cubic: host_out[r*N + (z*L + y)*L + x]) for replica slot r < *n
+ * (cap is in replicas). */
 pa_status pa_population(pa_ctx *ctx, int8_t *host_out, int64_t cap, int64_t *n);
 
 /* 64-bit FNV-1a hash of the current population in the layout of
@@ -223,10 +235,11 @@ pa_status pa_mhr(pa_ctx *ctx, const double *betas, int64_t n, pa_obs *out);
 /* The per-level magnetisation sums behind pa_mhr, over all measured replicas
  * of all completed steps: out[5k + 0] = sum |M|, out[5k + 1..2] = sum M^2
  * (low, high 64 bits), out[5k + 3..4] = sum M^4 (low, high), for energy
- * levels k = 0..N (cap >= 5 (N + 1)). */
+ * levels k = 0..nlev-1 (cap >= 5 nlev; nlev as for pa_histogram). */
 pa_status pa_mag_sums(pa_ctx *ctx, uint64_t *out, int64_t cap);
 
-/* ln Omega(E_k) for k = 0..N from Eq. MHReq1 (-inf where never visited). */
+/* ln Omega(E_k), E_k = 4k - dim N, for k = 0..nlev-1 from Eq. MHReq1 (-inf
+ * where never visited; cap >= nlev as for pa_histogram). */
 pa_status pa_ln_dos(pa_ctx *ctx, double *out, int64_t cap);
 
 /* Accumulated device time in ms of each kernel phase (needs profile != 0):
@@ -275,8 +288,8 @@ const char *pa_last_error_message(void);
  * descending work per replica. The whole schedule is one
  * CUDA graph, captured on the first launch and reused after pa_batch_reset.
  * Each run's results are those of the same pa_config run alone, bit for
- * bit. Runs must use fixed steps (dbeta > 0), bit-packed spins and
- * L <= 512 (L = 512: group_threads 256 only); group_threads == 0 picks the
+ * bit. Runs must use fixed steps (dbeta > 0), bit-packed spins on the
+ * square lattice and L <= 512 (L = 512: group_threads 256 only); group_threads == 0 picks the
  * threads per replica by a timed probe per L (cached per process), and an
  * unsupported group_threads gives PA_EINVAL. */
 typedef struct pa_batch pa_batch;

@@ -41,7 +41,7 @@ class _Config(ctypes.Structure):
                 ("overlap", ctypes.c_double), ("seed", ctypes.c_uint64), ("spin_format", ctypes.c_int32),
                 ("record_histograms", ctypes.c_int32), ("capacity", ctypes.c_int64),
                 ("group_threads", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 3)]
+                ("dim", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
 
 
 class _Obs(ctypes.Structure):
@@ -170,6 +170,17 @@ class PAConfig:
     group_threads: int = 0
     use_graph: bool = True
     profile: bool = False
+    dim: int = 2                 # 3: the L x L x L simple cubic lattice (bit-packed, L in 8..64)
+
+    @property
+    def n_sites(self) -> int:
+        return self.L ** (3 if self.dim == 3 else 2)
+
+    @property
+    def nlev(self) -> int:
+        """Entries of every histogram: energy levels k = (E + dim N)/4."""
+        d = 3 if self.dim == 3 else 2
+        return d * self.n_sites // 2 + 1
 
     def _c(self) -> _Config:
         c = _Config()
@@ -182,6 +193,7 @@ class PAConfig:
         c.group_threads = self.group_threads
         c.use_graph = int(bool(self.use_graph))
         c.profile = int(bool(self.profile))
+        c.dim = self.dim
         return c
 
 
@@ -216,7 +228,7 @@ class PARun:
             _check(self._lib.pa_create_scheduled(ctypes.byref(c), b.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
                                                  b.size, _stream_handle(stream), ctypes.byref(self._h)),
                    "pa_create_scheduled")
-        self.N = cfg.L * cfg.L
+        self.N = cfg.n_sites
 
     # -- lifecycle
     def close(self):
@@ -291,7 +303,7 @@ class PARun:
         return {f: getattr(s, f) for f, _ in _StepInfo._fields_ if f != "pad"}
 
     def histogram(self, step: int, kind: int = HIST_E) -> np.ndarray:
-        out = np.zeros(self.N + 1, dtype=np.int64)
+        out = np.zeros(self.cfg.nlev, dtype=np.int64)
         _check(self._lib.pa_histogram(self._h, step, kind, out.ctypes.data_as(_I64P), out.size), "pa_histogram")
         return out
 
@@ -299,7 +311,7 @@ class PARun:
         """Current population as int8 +1/-1 of shape (R_i, L, L)."""
         n = self.num_rows()
         R = self.step_info(n - 1)["R"]
-        out = np.zeros((R, self.cfg.L, self.cfg.L), dtype=np.int8)
+        out = np.zeros((R,) + (self.cfg.L,) * (3 if self.cfg.dim == 3 else 2), dtype=np.int8)
         got = ctypes.c_int64()
         _check(self._lib.pa_population(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), R,
                                        ctypes.byref(got)), "pa_population")
@@ -325,7 +337,7 @@ class PARun:
         return E[: got.value], M[: got.value], F[: got.value]
 
     def ln_dos(self) -> np.ndarray:
-        out = np.zeros(self.N + 1, dtype=np.float64)
+        out = np.zeros(self.cfg.nlev, dtype=np.float64)
         _check(self._lib.pa_ln_dos(self._h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), out.size),
                "pa_ln_dos")
         return out
@@ -346,9 +358,9 @@ class PARun:
 
     def mag_sums(self) -> np.ndarray:
         """Per-level sums (N+1, 5) uint64: |M|, M^2 lo/hi, M^4 lo/hi."""
-        out = np.zeros((self.N + 1) * 5, dtype=np.uint64)
+        out = np.zeros(self.cfg.nlev * 5, dtype=np.uint64)
         _check(self._lib.pa_mag_sums(self._h, ctypes.c_void_p(out.ctypes.data), out.size), "pa_mag_sums")
-        return out.reshape(self.N + 1, 5)
+        return out.reshape(self.cfg.nlev, 5)
 
     def mhr(self, betas) -> np.ndarray:
         b = np.ascontiguousarray(betas, dtype=np.float64)
@@ -409,7 +421,7 @@ def serve(requests, hbm_budget: int = 0, max_active: int = 8, time_scale: float 
         for i, (t, c) in enumerate(requests):
             if ctxs[i]:
                 r = PARun.__new__(PARun)
-                r.cfg, r._lib, r._h, r.N = c, lib(), ctypes.c_void_p(ctxs[i]), c.L * c.L
+                r.cfg, r._lib, r._h, r.N = c, lib(), ctypes.c_void_p(ctxs[i]), c.n_sites
                 runs.append(r)
             else:
                 runs.append(None)
@@ -444,7 +456,7 @@ class _BorrowedRun(PARun):
         self.cfg = cfg
         self._lib = lib()
         self._h = handle
-        self.N = cfg.L * cfg.L
+        self.N = cfg.n_sites
 
     def close(self):
         self._h = ctypes.c_void_p()

@@ -140,6 +140,13 @@ bool bits_L_ok(int L)
     return L == 8 || L == 16 || L == 32 || L == 64 || L == 128 || L == 256 || L == 512;
 }
 
+// simple cubic lattice, bit-packed: one L x L layer of a colour plane fills
+// whole words (L^2 / 64 >= 1), a replica fits one CTA's shared memory
+bool bits3_L_ok(int L)
+{
+    return L == 8 || L == 16 || L == 32 || L == 64;
+}
+
 bool msc_L_ok(int L)
 {
     switch (L) {
@@ -169,8 +176,21 @@ pa_status validate(const pa_config& c)
     if (c.capacity < 0 || (c.capacity > 0 && c.capacity < c.R)) return PA_EINVAL;
     if (c.group_threads < 0 || (c.group_threads & (c.group_threads - 1))) return PA_EINVAL;
     if (c.group_threads > 32 && !(c.group_threads == 256 && c.spin_format == PA_SPIN_BITS32)) return PA_EINVAL;
-    if (c.reserved[0] || c.reserved[1] || c.reserved[2]) return PA_EINVAL;
+    if (c.reserved[0] || c.reserved[1]) return PA_EINVAL;
+    if (c.dim != 0 && c.dim != 2 && c.dim != 3) return PA_EINVAL;
+    if (c.dim == 3 && (c.spin_format != PA_SPIN_BITS32 || !bits3_L_ok(c.L))) return PA_EINVAL;
     return PA_OK;
+}
+
+int dim_of(const pa_config& c)
+{
+    return c.dim == 3 ? 3 : 2;
+}
+
+// sites of the L x L torus, or of the L x L x L one (dim 3)
+long long sites_of(const pa_config& c)
+{
+    return dim_of(c) == 3 ? (long long)c.L * c.L * c.L : (long long)c.L * c.L;
 }
 
 long long capacity_of(const pa_config& c)
@@ -180,7 +200,7 @@ long long capacity_of(const pa_config& c)
 
 int words_of(const pa_config& c)
 {
-    const long long N = (long long)c.L * c.L;
+    const long long N = sites_of(c);
     if (c.spin_format == PA_SPIN_BITS32) return (int)(N / 32);
     if (c.spin_format == PA_SPIN_MSC32) return (int)N;  // per group of 32 replicas
     if (c.spin_format == PA_SPIN_REPLICA8) return 0;    // site-major bytes, sized separately
@@ -191,7 +211,7 @@ int words_of(const pa_config& c)
 // the plane's words (bit-packed) or the Philox blocks per plane (bytes)
 int auto_group(const pa_config& c)
 {
-    const long long N = (long long)c.L * c.L;
+    const long long N = sites_of(c);
     if (c.spin_format == PA_SPIN_BITS32) {
         const long long wp = N / 64;
         // L >= 128: one replica per 256-thread CTA (measured faster than warp
@@ -210,12 +230,14 @@ int auto_group(const pa_config& c)
 struct Sizes {
     long long cap, ntiles, steps, hist_steps;
     int N, words;
+    int nlev;  // energy levels k = (E + dim N)/4 = 0 .. dim N/2; also the length of each histogram
 };
 
 Sizes sizes_of(const pa_config& c)
 {
     Sizes s{};
-    s.N = c.L * c.L;
+    s.N = (int)sites_of(c);
+    s.nlev = dim_of(c) * s.N / 2 + 1;
     s.cap = capacity_of(c);
     s.ntiles = (s.cap + pa::kTile - 1) / pa::kTile;
     s.words = words_of(c);
@@ -228,7 +250,7 @@ Sizes sizes_of(const pa_config& c)
 size_t footprint(const pa_config& c)
 {
     const Sizes s = sizes_of(c);
-    const size_t N1 = (size_t)s.N + 1;
+    const size_t N1 = (size_t)s.nlev;
     size_t b = 0;
     if (c.spin_format == PA_SPIN_REPLICA8) b += 2 * (((size_t)s.N * (size_t)s.cap + 3) / 4) * 4;
     else b += 2 * (size_t)(c.spin_format == PA_SPIN_MSC32 ? (s.cap + 31) / 32 : s.cap) * s.words * 4;  // pop
@@ -238,7 +260,7 @@ size_t footprint(const pa_config& c)
     b += 2 * 2 * N1 * 4;                            // H
     b += N1 * 8 * 3 + N1 * 4;                       // Hsum, tw, U, F
     b += N1 * 8 * 5;                                // magnetisation sums per level
-    b += 2 * (size_t)(s.steps + 1) * 4;             // thresholds
+    b += (size_t)(dim_of(c) == 3 ? 3 : 2) * (size_t)(s.steps + 1) * 4;  // thresholds
     b += (size_t)(s.steps + 1) * sizeof(StepDev);   // records
     b += (size_t)s.hist_steps * 2 * N1 * 4;         // recorded histograms
     b += 64;                                        // status + work
@@ -418,9 +440,9 @@ pa_status enqueue_step(pa_ctx* c, bool wait = true)
         const uint32_t* hr = (const uint32_t*)((const char*)c->h_down + sizeof(StepDev) + 16);
         const int kmin = pr.kmin, kmax = pr.kmax;
         const int nl = kmax - kmin + 1;
-        std::vector<long long> H((size_t)c->N + 1, 0);
+        std::vector<long long> H((size_t)c->h.nlev, 0);
         for (int k = kmin; k <= kmax; k++) H[(size_t)k] = hr[(size_t)k];
-        const long long P = pad_pow2(c->N + 1);
+        const long long P = pad_pow2(c->h.nlev);
         const double bprev = c->betas[(size_t)(i - 1)];
         const double dmax = c->cfg.beta_f - bprev;
         const double target = c->cfg.overlap;
@@ -458,6 +480,11 @@ pa_status enqueue_step(pa_ctx* c, bool wait = true)
         PA_CUDA(cudaMemcpyAsync(c->h.tw, st, sizeof(double) * (size_t)nl, cudaMemcpyHostToDevice, c->stream));
         PA_CUDA(cudaMemcpyAsync(c->h.thr + 2 * i, st + sizeof(double) * (size_t)nl, sizeof(thr),
                                 cudaMemcpyHostToDevice, c->stream));
+        if (c->h.thr12) {
+            uint32_t* t12 = (uint32_t*)(st + sizeof(double) * (size_t)nl + sizeof(thr));
+            *t12 = (uint32_t)(threshold(beta, 12.0) - 1);
+            PA_CUDA(cudaMemcpyAsync(c->h.thr12 + i, t12, 4, cudaMemcpyHostToDevice, c->stream));
+        }
         c->T4.push_back(t4);
         c->T8.push_back(t8);
     }
@@ -478,7 +505,7 @@ pa_status enqueue_readback(pa_ctx* c)
     char* d = (char*)c->h_down;
     PA_CUDA(cudaMemcpyAsync(d, c->h.rec + i, sizeof(StepDev), cudaMemcpyDeviceToHost, c->stream));
     PA_CUDA(cudaMemcpyAsync(d + sizeof(StepDev), c->h.status, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
-    PA_CUDA(cudaMemcpyAsync(d + sizeof(StepDev) + 16, c->h.H[i & 1], sizeof(uint32_t) * ((size_t)c->N + 1),
+    PA_CUDA(cudaMemcpyAsync(d + sizeof(StepDev) + 16, c->h.H[i & 1], sizeof(uint32_t) * (size_t)c->h.nlev,
                             cudaMemcpyDeviceToHost, c->stream));
     PA_CUDA(cudaEventRecord(c->ev_ready, c->stream));
     return PA_OK;
@@ -510,7 +537,7 @@ double lnQ_of(const pa_ctx* c, long long i)
 {
     if (i == 0) return 0.0;
     const StepDev& r = c->recs[(size_t)i];
-    const double Emin = (double)(-2ll * c->N + 4ll * r.kmin_prev);
+    const double Emin = (double)(-c->h.eoff + 4ll * r.kmin_prev);
     return (std::log(r.S) - std::log((double)r.R_prev)) - c->deltas[(size_t)i] * Emin;
 }
 
@@ -530,7 +557,7 @@ void all_rows(const pa_ctx* c, std::vector<pa_obs>& rows)
 pa_status reset_run(pa_ctx* c, uint64_t seed)
 {
     RunDev& h = c->h;
-    const size_t N1 = (size_t)c->N + 1;
+    const size_t N1 = (size_t)h.nlev;
     PA_CUDA(cudaStreamSynchronize(c->stream));
     if (c->cfg.profile) PA_TRY(prof_collect(c));
     unsigned* key = (unsigned*)c->h_stage;  // pinned; idle after the sync
@@ -774,6 +801,7 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     if (Jr) {
         if (cfg->spin_format != PA_SPIN_BITS32 && cfg->spin_format != PA_SPIN_INT8) return PA_EINVAL;
         long long neg = 0;
+        if (dim_of(*cfg) != 2) return PA_EINVAL;  // +-J bonds: square lattice only
         const long long N = (long long)cfg->L * cfg->L;
         for (long long i = 0; i < N; i++) {
             if ((Jr[i] != 1 && Jr[i] != -1) || (Jd[i] != 1 && Jd[i] != -1)) return PA_EINVAL;
@@ -819,7 +847,10 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     h.hist_steps = (int)s.hist_steps;
     h.nsteps = (int)s.steps;
     h.unit = 1u;
-    const size_t N1 = (size_t)s.N + 1;
+    h.dim = dim_of(*cfg);
+    h.nlev = s.nlev;
+    h.eoff = (long long)h.dim * s.N;
+    const size_t N1 = (size_t)s.nlev;
     pa_status st = PA_OK;
 #define PA_ALLOC(p, n)                            \
     do {                                          \
@@ -848,6 +879,7 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     PA_ALLOC(h.F, N1);
     PA_ALLOC(h.U, N1);
     PA_ALLOC(h.thr, 2 * (size_t)(s.steps + 1));
+    if (h.dim == 3) PA_ALLOC(h.thr12, (size_t)(s.steps + 1));
     PA_ALLOC(h.rec, (size_t)(s.steps + 1));
     if (s.hist_steps) PA_ALLOC(h.hist_rec, (size_t)s.hist_steps * 2 * N1);
     PA_ALLOC(h.status, 4);
@@ -884,19 +916,21 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     c->T8.push_back(1ull << 32);
     if (!c->adaptive) {
         // all thresholds and the (fixed) level weights up front
-        std::vector<uint32_t> thr(2 * (size_t)(s.steps + 1), 0xffffffffu);
+        std::vector<uint32_t> thr(2 * (size_t)(s.steps + 1), 0xffffffffu), thr12((size_t)(s.steps + 1), 0xffffffffu);
         for (long long i = 1; i <= s.steps; i++) {
             const double beta = 0.0 + (double)i * cfg->dbeta;
             const uint64_t t4 = threshold(beta, 4.0), t8 = threshold(beta, 8.0);
             thr[2 * (size_t)i] = (uint32_t)(t4 - 1);
             thr[2 * (size_t)i + 1] = (uint32_t)(t8 - 1);
+            thr12[(size_t)i] = (uint32_t)(threshold(beta, 12.0) - 1);
             c->T4.push_back(t4);
             c->T8.push_back(t8);
         }
         std::vector<double> w;
         level_weights(cfg->dbeta, (int)N1, w);
         if (cudaMemcpy(h.thr, thr.data(), thr.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
-            cudaMemcpy(h.tw, w.data(), N1 * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+            cudaMemcpy(h.tw, w.data(), N1 * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
+            (h.thr12 && cudaMemcpy(h.thr12, thr12.data(), thr12.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess))
             return fail(PA_ECUDA);
     }
     if (pa::plan_sweep(h, &c->ln) != cudaSuccess) {
@@ -1072,9 +1106,9 @@ pa_status pa_step_info_get(pa_ctx* c, int64_t step, pa_step_info* out)
 
 pa_status pa_histogram(pa_ctx* c, int64_t step, int32_t kind, int64_t* out, int64_t cap)
 {
-    if (!c || !out || cap < c->N + 1) return PA_EINVAL;
+    if (!c || !out || cap < c->h.nlev) return PA_EINVAL;
     pull_records(c);
-    const size_t N1 = (size_t)c->N + 1;
+    const size_t N1 = (size_t)c->h.nlev;
     if (kind == PA_HIST_ESUM) {
         std::vector<unsigned long long> t(N1);
         PA_CUDA(cudaMemcpy(t.data(), c->h.Hsum, N1 * 8, cudaMemcpyDeviceToHost));
@@ -1135,17 +1169,19 @@ pa_status pa_population(pa_ctx* c, int8_t* host_out, int64_t cap, int64_t* n)
     std::vector<uint32_t> buf((size_t)m * c->h.words);
     if (m > 0)
         PA_CUDA(cudaMemcpy(buf.data(), c->h.pop[last & 1], buf.size() * 4, cudaMemcpyDeviceToHost));
+    const int layers = c->h.dim == 3 ? L : 1;  // z-layers of the simple cubic lattice
     for (long long r = 0; r < m; r++) {
         const uint32_t* w = buf.data() + (size_t)r * c->h.words;
         const uint8_t* bytes = (const uint8_t*)w;
-        for (int y = 0; y < L; y++)
-            for (int x = 0; x < L; x++) {
-                const int col = (x + y) & 1, b = y * half + (x >> 1);
-                int up;
-                if (c->h.fmt == PA_SPIN_BITS32) up = (w[col * (N / 64) + (b >> 5)] >> (b & 31)) & 1u;
-                else up = bytes[col * (N / 2) + b];
-                host_out[(size_t)r * N + (size_t)y * L + x] = up ? 1 : -1;
-            }
+        for (int z = 0; z < layers; z++)
+            for (int y = 0; y < L; y++)
+                for (int x = 0; x < L; x++) {
+                    const int col = (x + y + z) & 1, b = (z * L + y) * half + (x >> 1);
+                    int up;
+                    if (c->h.fmt == PA_SPIN_BITS32) up = (w[col * (N / 64) + (b >> 5)] >> (b & 31)) & 1u;
+                    else up = bytes[col * (N / 2) + b];
+                    host_out[(size_t)r * N + ((size_t)z * L + y) * L + x] = up ? 1 : -1;
+                }
     }
     *n = m;
     return PA_OK;
@@ -1167,7 +1203,7 @@ pa_status pa_replicas(pa_ctx* c, int32_t* E, int32_t* M, int64_t* family, int64_
         PA_CUDA(cudaMemcpy(fv.data(), c->h.fam[last & 1], (size_t)m * 4, cudaMemcpyDeviceToHost));
     }
     for (long long r = 0; r < m; r++) {
-        if (E) E[r] = 4 * ev[(size_t)r] - 2 * c->N;
+        if (E) E[r] = (int32_t)(4ll * ev[(size_t)r] - c->h.eoff);
         if (M) M[r] = 2 * mv[(size_t)r] - c->N;
         if (family) family[r] = fv[(size_t)r];
     }
@@ -1181,10 +1217,10 @@ pa_status pa_replicas(pa_ctx* c, int32_t* E, int32_t* M, int64_t* family, int64_
 // exact beta = 0 sample) included.
 pa_status pa_ln_dos(pa_ctx* c, double* out, int64_t cap)
 {
-    if (!c || !out || cap < c->N + 1) return PA_EINVAL;
+    if (!c || !out || cap < c->h.nlev) return PA_EINVAL;
     pa_status st = pull_records(c);
     if (st != PA_OK && st != PA_ECAPACITY && st != PA_EEXTINCT) return st;
-    const size_t N1 = (size_t)c->N + 1;
+    const size_t N1 = (size_t)c->h.nlev;
     std::vector<unsigned long long> hs(N1);
     PA_CUDA(cudaMemcpy(hs.data(), c->h.Hsum, N1 * 8, cudaMemcpyDeviceToHost));
     std::vector<pa_obs> rows;
@@ -1202,7 +1238,7 @@ pa_status pa_ln_dos(pa_ctx* c, double* out, int64_t cap)
             out[k] = -INFINITY;
             continue;
         }
-        const double Ek = (double)(-2ll * c->N + 4ll * (long long)k);
+        const double Ek = (double)(-c->h.eoff + 4ll * (long long)k);
         double m = -INFINITY;
         for (size_t i = 0; i < nr; i++) {
             a[i] = lnR[i] + bF[i] - b[i] * Ek;
@@ -1217,10 +1253,10 @@ pa_status pa_ln_dos(pa_ctx* c, double* out, int64_t cap)
 
 pa_status pa_mag_sums(pa_ctx* c, uint64_t* out, int64_t cap)
 {
-    if (!c || !out || cap < 5 * ((int64_t)c->N + 1)) return PA_EINVAL;
+    if (!c || !out || cap < 5 * (int64_t)c->h.nlev) return PA_EINVAL;
     pa_status st = pull_records(c);
     if (st != PA_OK && st != PA_ECAPACITY && st != PA_EEXTINCT) return st;
-    PA_CUDA(cudaMemcpy(out, c->h.Msum, 5 * ((size_t)c->N + 1) * 8, cudaMemcpyDeviceToHost));
+    PA_CUDA(cudaMemcpy(out, c->h.Msum, 5 * (size_t)c->h.nlev * 8, cudaMemcpyDeviceToHost));
     return PA_OK;
 }
 
@@ -1230,7 +1266,7 @@ pa_status pa_mag_sums(pa_ctx* c, uint64_t* out, int64_t cap)
 pa_status pa_mhr(pa_ctx* c, const double* betas, int64_t n, pa_obs* out)
 {
     if (!c || (n > 0 && (!betas || !out))) return PA_EINVAL;
-    const size_t N1 = (size_t)c->N + 1;
+    const size_t N1 = (size_t)c->h.nlev;
     std::vector<double> lno(N1);
     PA_TRY(pa_ln_dos(c, lno.data(), (int64_t)N1));
     std::vector<unsigned long long> hs(N1), ms(5 * N1);
@@ -1252,13 +1288,13 @@ pa_status pa_mhr(pa_ctx* c, const double* betas, int64_t n, pa_obs* out)
         double m = -INFINITY;
         for (size_t k = 0; k < N1; k++) {
             if (!std::isfinite(lno[k])) continue;
-            const double Ek = (double)(-2ll * c->N + 4ll * (long long)k);
+            const double Ek = (double)(-c->h.eoff + 4ll * (long long)k);
             m = std::max(m, lno[k] - beta * Ek);
         }
         double Z = 0.0, e1 = 0.0, e2 = 0.0, a1 = 0.0, a2 = 0.0, a4 = 0.0;
         for (size_t k = 0; k < N1; k++) {
             if (!std::isfinite(lno[k])) continue;
-            const double Ek = (double)(-2ll * c->N + 4ll * (long long)k);
+            const double Ek = (double)(-c->h.eoff + 4ll * (long long)k);
             const double w = std::exp(lno[k] - beta * Ek - m);
             Z += w;
             e1 += w * Ek;
@@ -1687,7 +1723,8 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
     for (int i = 0; i < n; i++) {
         const pa_config& c = cfgs[i];
         PA_TRY(validate(c));
-        if (!(c.dbeta > 0.0) || c.spin_format != PA_SPIN_BITS32 || c.L > 512) return PA_EINVAL;  // bit-packed only
+        if (!(c.dbeta > 0.0) || c.spin_format != PA_SPIN_BITS32 || c.L > 512 || dim_of(c) != 2)
+            return PA_EINVAL;  // bit-packed square lattices only
         if (c.group_threads && !pa::batch_supports(c.L, c.group_threads)) return PA_EINVAL;
     }
     pa_batch* b = new (std::nothrow) pa_batch();
@@ -2003,7 +2040,7 @@ extern "C" pa_status pa_checkpoint(pa_ctx* c, void* host_buf, size_t cap, size_t
     if (c->done_rows != i + 1) return PA_ESTATE;
     const StepDev& last = c->recs[(size_t)i];
     const long long R = last.R;
-    const size_t N1 = (size_t)c->N + 1;
+    const size_t N1 = (size_t)c->h.nlev;
     const long long hs = c->h.hist_rec ? std::min<long long>(i + 1, c->hist_steps) : 0;
     CkptHeader hd{};
     hd.magic = kCkptMagic;
@@ -2070,7 +2107,7 @@ extern "C" pa_status pa_restore(pa_ctx* c, const void* host_buf, size_t n)
     if (std::memcmp(&a, &b, sizeof(a)) != 0) return PA_EINVAL;
     if (hd.step < 0 || hd.step > c->max_steps || hd.R < 1 || hd.R > c->h.cap) return PA_EINVAL;
     const long long i = hd.step, R = hd.R;
-    const size_t N1 = (size_t)c->N + 1;
+    const size_t N1 = (size_t)c->h.nlev;
     const char* p = (const char*)host_buf + sizeof(hd);
     const char* end = (const char*)host_buf + n;
     auto take = [&](size_t bytes) -> const char* {

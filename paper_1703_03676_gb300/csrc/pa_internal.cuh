@@ -65,6 +65,9 @@ struct RunDev {
     int hist_steps;           // steps with a slot in hist_rec
     int nsteps;               // last step of a fixed schedule (batched runs stop there)
     unsigned unit;            // always 1; a run-time multiplier for the accept-bit insert
+    int dim;                  // 2: L x L square lattice; 3: L x L x L simple cubic (N = L^dim)
+    int nlev;                 // energy levels k = (E + eoff)/4 = 0 .. dim N/2, and the length of each histogram
+    long long eoff;           // dim * N: E_k = 4 k - eoff
     uint32_t* pop[2];
     int32_t* elev[2];
     int32_t* mlev[2];
@@ -74,7 +77,7 @@ struct RunDev {
     uint32_t* loc;
     uint32_t* tile_sum;
     uint32_t* tile_off;
-    uint32_t* H[2];
+    uint32_t* H[2];           // energy histogram (nlev) then magnetisation histogram (nlev, N + 1 used)
     unsigned long long* Hsum;
     unsigned long long* Msum;  // per energy level: sum |M|, sum M^2 (lo, hi), sum M^4 (lo, hi)
     const uint32_t* bonds;    // +-J model, bit-packed: masks [dir][colour][word], bit set = J < 0
@@ -82,7 +85,8 @@ struct RunDev {
     double* tw;
     uint32_t* F;
     unsigned long long* U;
-    uint32_t* thr;
+    uint32_t* thr;            // per step: T4 - 1, T8 - 1
+    uint32_t* thr12;          // per step: T12 - 1 (simple cubic lattice only, else null)
     StepDev* rec;
     uint32_t* hist_rec;       // (steps) x 2 x (N+1) when record_hist
     int* status;

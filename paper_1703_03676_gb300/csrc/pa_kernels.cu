@@ -87,6 +87,33 @@ __device__ __forceinline__ void neighbours(const uint32_t* __restrict__ O, int c
     }
 }
 
+// Word counts of a bit-packed replica: the L x L square lattice (D = 2) or
+// the L x L x L simple cubic one (D = 3). Layer z of a simple cubic colour
+// plane is laid out like a square-lattice plane (WPL words).
+template <int L, int D>
+struct Lat {
+    static constexpr int N = D == 3 ? L * L * L : L * L;
+    static constexpr int WP = N / 64;       // words per colour plane
+    static constexpr int WORDS = N / 32;    // words per replica
+    static constexpr int WPL = L * L / 64;  // words per colour plane and layer
+};
+
+// The six neighbour words of word w of plane c on the simple cubic lattice.
+// Within layer z the sites of colour c have x = c + z + y (mod 2), so the
+// in-layer neighbours are the square lattice's for colour (c + z) & 1; the
+// other two are the same word of layers z - 1 and z + 1.
+template <int L>
+__device__ __forceinline__ void neighbours3(const uint32_t* __restrict__ O, int c, int w, uint32_t& same,
+                                            uint32_t& side, uint32_t& up, uint32_t& down, uint32_t& zup,
+                                            uint32_t& zdn)
+{
+    constexpr int WPL = Lat<L, 3>::WPL;
+    const int z = w / WPL, wl = w - z * WPL;
+    neighbours<L>(O + z * WPL, (c + z) & 1, wl, same, side, up, down);
+    zup = O[(z == 0 ? L - 1 : z - 1) * WPL + wl];
+    zdn = O[(z == L - 1 ? 0 : z + 1) * WPL + wl];
+}
+
 // Sets bit T of acc when x <= thr. The 32 accept bits of a word are
 // disjoint, so the insert can be an addition: a predicated multiply-add by
 // the run-time constant unit (always 1) issues on the FMA pipe, which the
@@ -145,6 +172,55 @@ __device__ __forceinline__ uint32_t metropolis_word(uint32_t s, uint32_t same, u
     return s ^ (ge2 | (acc4 & ~eq0) | (acc8 & eq0));
 }
 
+// Bits 4q .. 4q+3 of acc4, acc8 and acc12 (x <= T4-1, T8-1, T12-1) from
+// Philox block q, then blocks q+1 .. 7
+template <int Q>
+__device__ __forceinline__ void accept_blocks3(uint32_t& acc4, uint32_t& acc8, uint32_t& acc12, unsigned c0,
+                                               unsigned k, unsigned c2, uint32_t t4m1, uint32_t t8m1,
+                                               uint32_t t12m1, uint32_t unit, PhiloxKey key)
+{
+    if constexpr (Q < 8) {
+        const uint4 x = philox10(make_uint4(c2, c0 + Q, kTagSweep, k), key);
+        acc4 = accept_bit<4 * Q + 0>(acc4, x.x, t4m1, unit);
+        acc8 = accept_bit<4 * Q + 0>(acc8, x.x, t8m1, unit);
+        acc12 = accept_bit<4 * Q + 0>(acc12, x.x, t12m1, unit);
+        acc4 = accept_bit<4 * Q + 1>(acc4, x.y, t4m1, unit);
+        acc8 = accept_bit<4 * Q + 1>(acc8, x.y, t8m1, unit);
+        acc12 = accept_bit<4 * Q + 1>(acc12, x.y, t12m1, unit);
+        acc4 = accept_bit<4 * Q + 2>(acc4, x.z, t4m1, unit);
+        acc8 = accept_bit<4 * Q + 2>(acc8, x.z, t8m1, unit);
+        acc12 = accept_bit<4 * Q + 2>(acc12, x.z, t12m1, unit);
+        acc4 = accept_bit<4 * Q + 3>(acc4, x.w, t4m1, unit);
+        acc8 = accept_bit<4 * Q + 3>(acc8, x.w, t8m1, unit);
+        acc12 = accept_bit<4 * Q + 3>(acc12, x.w, t12m1, unit);
+        accept_blocks3<Q + 1>(acc4, acc8, acc12, c0, k, c2, t4m1, t8m1, t12m1, unit, key);
+    }
+}
+
+// One Metropolis update of the 32 sites of word s on the simple cubic
+// lattice: with n of the six neighbours aligned, dE = 4n - 12, so a site
+// flips with certainty if at most 3 neighbours agree (3 or more disagree),
+// else iff x <= T4-1, T8-1, T12-1 for 2, 1, 0 disagreeing neighbours; x is
+// the SWEEP word of the site, as on the square lattice. The disagreeing
+// neighbours are counted bit-sliced (two full adders of three, then the
+// carries), 4 b2 + 2 b1 + b0.
+__device__ __forceinline__ uint32_t metropolis_word3(uint32_t s, uint32_t n1, uint32_t n2, uint32_t n3,
+                                                     uint32_t n4, uint32_t n5, uint32_t n6, unsigned c0,
+                                                     unsigned k, unsigned c2, uint32_t t4m1, uint32_t t8m1,
+                                                     uint32_t t12m1, uint32_t unit, PhiloxKey key)
+{
+    const uint32_t d1 = s ^ n1, d2 = s ^ n2, d3 = s ^ n3, d4 = s ^ n4, d5 = s ^ n5, d6 = s ^ n6;
+    const uint32_t sa = d1 ^ d2 ^ d3, ca = (d1 & d2) | (d3 & (d1 ^ d2));
+    const uint32_t sb = d4 ^ d5 ^ d6, cb = (d4 & d5) | (d6 & (d4 ^ d5));
+    const uint32_t b0 = sa ^ sb, k0 = sa & sb;
+    const uint32_t b1 = ca ^ cb ^ k0, b2 = (ca & cb) | (k0 & (ca ^ cb));
+    const uint32_t ge3 = b2 | (b1 & b0);
+    const uint32_t eq2 = ~b2 & b1 & ~b0, eq1 = ~b2 & ~b1 & b0, eq0 = ~(b2 | b1 | b0);
+    uint32_t acc4 = 0, acc8 = 0, acc12 = 0;
+    accept_blocks3<0>(acc4, acc8, acc12, c0, k, c2, t4m1, t8m1, t12m1, unit, key);
+    return s ^ (ge3 | (acc4 & eq2) | (acc8 & eq1) | (acc12 & eq0));
+}
+
 // ======================================================== shared epilogue
 // 128-bit unsigned accumulation (lo, hi) with an explicit carry: integer
 // addition is associative, so the total does not depend on the order.
@@ -161,12 +237,12 @@ __device__ __forceinline__ void atomic_add_u128(unsigned long long* lohi, unsign
 __device__ __forceinline__ void record_replica(const RunDev& r, int nxt, long long k, unsigned anti, unsigned ups,
                                                uint32_t family)
 {
-    const int kl = (int)(anti >> 1);  // (E + 2N)/4 with E = 2*anti - 2N
+    const int kl = (int)(anti >> 1);  // (E + dim N)/4 with E = 2*anti - dim N
     r.elev[nxt][k] = kl;
     r.mlev[nxt][k] = (int)ups;        // (M + N)/2 = number of up spins
     r.fam[nxt][k] = family;
     atomicAdd(&r.H[nxt][kl], 1u);
-    atomicAdd(&r.H[nxt][r.N + 1 + ups], 1u);
+    atomicAdd(&r.H[nxt][r.nlev + ups], 1u);
     const long long M = 2ll * (long long)ups - r.N;
     const unsigned long long aM = (unsigned long long)(M < 0 ? -M : M);
     const unsigned long long M2 = aM * aM;
@@ -212,19 +288,26 @@ __device__ __forceinline__ void apply_bonds(const uint32_t* __restrict__ bonds, 
     down ^= __ldg(B + 6 * WP);
 }
 
-template <int L, int G>
+template <int L, int G, int D = 2>
 __device__ __forceinline__ void measure_bits(const uint32_t* sp, int gl, unsigned& anti, unsigned& ups,
                                              const uint32_t* __restrict__ bonds)
 {
-    using Gm = Geo<L>;
+    using Gm = Lat<L, D>;
     anti = 0;
     ups = 0;
     for (int w = gl; w < Gm::WP; w += G) {
-        uint32_t same, side, up, down;
-        neighbours<L>(sp + Gm::WP, 0, w, same, side, up, down);
-        if (bonds) apply_bonds<L>(bonds, 0, w, same, side, up, down);
         const uint32_t s = sp[w];
-        anti += __popc(s ^ same) + __popc(s ^ side) + __popc(s ^ up) + __popc(s ^ down);
+        if constexpr (D == 3) {
+            uint32_t same, side, up, down, zup, zdn;
+            neighbours3<L>(sp + Gm::WP, 0, w, same, side, up, down, zup, zdn);
+            anti += __popc(s ^ same) + __popc(s ^ side) + __popc(s ^ up) + __popc(s ^ down) + __popc(s ^ zup) +
+                    __popc(s ^ zdn);
+        } else {
+            uint32_t same, side, up, down;
+            neighbours<L>(sp + Gm::WP, 0, w, same, side, up, down);
+            if (bonds) apply_bonds<L>(bonds, 0, w, same, side, up, down);
+            anti += __popc(s ^ same) + __popc(s ^ side) + __popc(s ^ up) + __popc(s ^ down);
+        }
         ups += __popc(s) + __popc(sp[Gm::WP + w]);
     }
 }
@@ -289,16 +372,18 @@ struct Group {
 // One temperature step of the replica in new slot k (gather of its parent,
 // theta sweeps, measurement, write-back). Every thread of the group calls
 // this, active or not (inactive groups only take part in the syncs).
-template <int L, int G>
+template <int L, int G, int D = 2>
 __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long long k, bool active,
                                                 uint32_t* sp, int gl, unsigned* red, unsigned& families)
 {
-    using Gm = Geo<L>;
+    using Gm = Lat<L, D>;
     using Gr = Group<G>;
     constexpr int WPT = Gm::WP / G;  // words per thread per plane
     static_assert(Gm::WP % G == 0, "group must divide the plane");
     const int cur = (step - 1) & 1, nxt = step & 1;
     const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
+    uint32_t t12m1 = 0;
+    if constexpr (D == 3) t12m1 = r.thr12[step];
     const PhiloxKey key{r.key[0], r.key[1]};
     const int theta = r.theta;
     const unsigned u0 = (unsigned)(step - 1) * (unsigned)theta;
@@ -320,18 +405,25 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
 #pragma unroll 2
                 for (int m = 0; m < WPT; m++) {
                     const int w = gl + m * G;
-                    uint32_t same, side, up, down;
-                    neighbours<L>(O, c, w, same, side, up, down);
-                    if (bonds) apply_bonds<L>(bonds, c, w, same, side, up, down);
-                    P[w] = metropolis_word(P[w], same, side, up, down, 8u * (unsigned)w, (unsigned)k, c2, t4m1,
-                                           t8m1, r.unit, key);
+                    if constexpr (D == 3) {
+                        uint32_t same, side, up, down, zup, zdn;
+                        neighbours3<L>(O, c, w, same, side, up, down, zup, zdn);
+                        P[w] = metropolis_word3(P[w], same, side, up, down, zup, zdn, 8u * (unsigned)w,
+                                                (unsigned)k, c2, t4m1, t8m1, t12m1, r.unit, key);
+                    } else {
+                        uint32_t same, side, up, down;
+                        neighbours<L>(O, c, w, same, side, up, down);
+                        if (bonds) apply_bonds<L>(bonds, c, w, same, side, up, down);
+                        P[w] = metropolis_word(P[w], same, side, up, down, 8u * (unsigned)w, (unsigned)k, c2,
+                                               t4m1, t8m1, r.unit, key);
+                    }
                 }
             }
             Gr::sync();
         }
     }
     unsigned anti = 0, ups = 0;
-    if (active) measure_bits<L, G>(sp, gl, anti, ups, bonds);
+    if (active) measure_bits<L, G, D>(sp, gl, anti, ups, bonds);
     anti = Gr::sum(anti, red);
     ups = Gr::sum(ups, red);
     if (active) {
@@ -347,11 +439,11 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
 
 // Initial spins of replica k (INIT stream: site g = c*N/2 + b, counter
 // (0, g>>2, 0, k), spin up iff x < 2^31), measured and written to pop[0].
-template <int L, int G>
+template <int L, int G, int D = 2>
 __device__ __forceinline__ void bits_group_init(const RunDev& r, long long k, bool active, uint32_t* sp, int gl,
                                                 unsigned* red)
 {
-    using Gm = Geo<L>;
+    using Gm = Lat<L, D>;
     using Gr = Group<G>;
     const PhiloxKey key{r.key[0], r.key[1]};
     if (active) {
@@ -370,7 +462,7 @@ __device__ __forceinline__ void bits_group_init(const RunDev& r, long long k, bo
     }
     Gr::sync();
     unsigned anti = 0, ups = 0;
-    if (active) measure_bits<L, G>(sp, gl, anti, ups, r.bonds);
+    if (active) measure_bits<L, G, D>(sp, gl, anti, ups, r.bonds);
     anti = Gr::sum(anti, red);
     ups = Gr::sum(ups, red);
     if (active) {
@@ -383,10 +475,10 @@ __device__ __forceinline__ void bits_group_init(const RunDev& r, long long k, bo
 // ======================================================== bit-packed kernels
 // Persistent: each group repeatedly takes the next replica of the run's
 // work counter, so the tail of a step is at most one replica's work.
-template <int L, int G>
+template <int L, int G, int D = 2>
 __global__ void __launch_bounds__(256) k_init_bits(const __grid_constant__ RunDev r)
 {
-    using Gm = Geo<L>;
+    using Gm = Lat<L, D>;
     using Gr = Group<G>;
     extern __shared__ uint32_t smem[];
     if (*r.status) return;
@@ -398,14 +490,14 @@ __global__ void __launch_bounds__(256) k_init_bits(const __grid_constant__ RunDe
         const unsigned first = Gr::grab(r.work, red + 32);
         const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
         if (base >= R0) break;
-        bits_group_init<L, G>(r, (long long)first, first < R0, sp, gl, red);
+        bits_group_init<L, G, D>(r, (long long)first, first < R0, sp, gl, red);
     }
 }
 
-template <int L, int G>
+template <int L, int G, int D = 2>
 __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunDev r, int step)
 {
-    using Gm = Geo<L>;
+    using Gm = Lat<L, D>;
     using Gr = Group<G>;
     extern __shared__ uint32_t smem[];
     if (*r.status) return;
@@ -418,7 +510,7 @@ __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunD
         const unsigned first = Gr::grab(r.work, red + 32);
         const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
         if (base >= Ri) break;
-        bits_group_step<L, G>(r, step, (long long)first, first < Ri, sp, gl, red, families);
+        bits_group_step<L, G, D>(r, step, (long long)first, first < Ri, sp, gl, red, families);
     }
     families = group_sum<32>(families);
     if ((threadIdx.x & 31) == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
@@ -985,7 +1077,7 @@ __device__ __forceinline__ void tables_body(const RunDev& r, int step)
     const int kmin = prev.kmin, kmax = prev.kmax;
     const uint32_t* H = r.H[(step - 1) & 1];
     const double* tw = r.tw;
-    const int P = pad_pow2(r.N + 1);
+    const int P = pad_pow2(r.nlev);
     const int nthr = P < kOneCta ? P : kOneCta;
     const int chunk = P / nthr;
     double v = 0.0;
@@ -1022,7 +1114,7 @@ __device__ __forceinline__ void tables_body(const RunDev& r, int step)
         r.U[kk] = (unsigned long long)ceil(__dmul_rn(frac, 4294967296.0));
     }
     uint32_t* Hn = r.H[step & 1];
-    for (int i = t; i < 2 * (r.N + 1); i += kOneCta) Hn[i] = 0u;
+    for (int i = t; i < 2 * r.nlev; i += kOneCta) Hn[i] = 0u;
     if (t == 0) {
         r.rec[step].S = S;
         r.rec[step].kmin_prev = kmin;
@@ -1243,20 +1335,20 @@ __device__ __forceinline__ void stats_body(const RunDev& r, int step)
     __shared__ __int128 ws[5][kOneCta / 32];
     __shared__ int wmin[kOneCta / 32], wmax[kOneCta / 32];
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const int N = r.N;
+    const int N = r.N, NL = r.nlev;
     const uint32_t* HE = r.H[step & 1];
-    const uint32_t* HM = HE + N + 1;
+    const uint32_t* HM = HE + NL;
     __int128 sE = 0, sE2 = 0, sAM = 0, sM2 = 0, sM4 = 0;
     int kmin = 0x7fffffff, kmax = -1;
     uint32_t* rec_hist = nullptr;
-    if (r.record_hist && r.hist_rec && step < r.hist_steps) rec_hist = r.hist_rec + (size_t)step * 2 * (N + 1);
-    for (int k = t; k <= N; k += kOneCta) {
+    if (r.record_hist && r.hist_rec && step < r.hist_steps) rec_hist = r.hist_rec + (size_t)step * 2 * NL;
+    for (int k = t; k < NL; k += kOneCta) {
         const uint32_t h = HE[k];
         const uint32_t hm = HM[k];
         if (h) {
             kmin = min(kmin, k);
             kmax = max(kmax, k);
-            const long long E = 4ll * k - 2ll * N;
+            const long long E = 4ll * k - r.eoff;
             sE += (__int128)h * E;
             sE2 += (__int128)h * (E * E);
             r.Hsum[k] += h;
@@ -1271,7 +1363,7 @@ __device__ __forceinline__ void stats_body(const RunDev& r, int step)
         }
         if (rec_hist) {
             rec_hist[k] = h;
-            rec_hist[N + 1 + k] = hm;
+            rec_hist[NL + k] = hm;
         }
     }
     sE = warp_sum128(sE);
@@ -1482,10 +1574,26 @@ __global__ void __launch_bounds__(256) k_rng_peak(long long blocks, PhiloxKey ke
 // ======================================================== launch wrappers
 namespace {
 
-template <int L, int G>
+template <int L, int G, int D = 2>
 const void* bits_ptr(bool init)
 {
-    return init ? (const void*)k_init_bits<L, G> : (const void*)k_sweep_bits<L, G>;
+    return init ? (const void*)k_init_bits<L, G, D> : (const void*)k_sweep_bits<L, G, D>;
+}
+
+// simple cubic lattice: the warp groups and CTA groups the default choice
+// uses (power-of-two words per plane: 8, 64, 512, 4096 for L = 8 .. 64)
+template <int L>
+const void* bits3_ptr_L(int gt, bool init)
+{
+    constexpr int WP = Lat<L, 3>::WP;
+    switch (gt) {
+    case 8: if constexpr (WP % 8 == 0 && WP <= 64) return bits_ptr<L, 8, 3>(init); break;
+    case 16: if constexpr (WP % 16 == 0 && WP <= 512) return bits_ptr<L, 16, 3>(init); break;
+    case 32: if constexpr (WP % 32 == 0 && WP <= 512) return bits_ptr<L, 32, 3>(init); break;
+    case 256: if constexpr (WP % 256 == 0) return bits_ptr<L, 256, 3>(init); break;
+    default: break;
+    }
+    return nullptr;
 }
 
 template <int L>
@@ -1523,6 +1631,15 @@ const void* sweep_kernel(const RunDev& h, bool init)
     case LL: return init ? (const void*)k_init_msc<LL> : (const void*)k_sweep_msc<LL>;
             PA_MSC_SIZES(PA_MSC_PTR)
 #undef PA_MSC_PTR
+        default: return nullptr;
+        }
+    }
+    if (h.fmt == 1 && h.dim == 3) {
+        switch (h.L) {
+        case 8: return bits3_ptr_L<8>(h.gt, init);
+        case 16: return bits3_ptr_L<16>(h.gt, init);
+        case 32: return bits3_ptr_L<32>(h.gt, init);
+        case 64: return bits3_ptr_L<64>(h.gt, init);
         default: return nullptr;
         }
     }

@@ -12,9 +12,9 @@ ROW_FIELDS = ["beta", "e", "C", "abs_m", "m2", "m4", "betaF_per_N", "S_per_N", "
 REL_TOL = 1e-12  # derived FP64 rows (integer parts are compared exactly)
 
 
-def oracle_run(L, R, theta, beta_f, dbeta, seed, overlap=0.85, capacity=0):
+def oracle_run(L, R, theta, beta_f, dbeta, seed, overlap=0.85, capacity=0, dim=2):
     pa = PopulationAnnealing(L, R, theta, beta_f=beta_f, dbeta=dbeta, seed=seed, overlap=overlap,
-                             capacity=capacity, record_hist=True)
+                             capacity=capacity, record_hist=True, dim=dim)
     return pa
 
 
@@ -41,7 +41,9 @@ def compare_step(run, pa, i):
         assert info["T4"] == rec.T4 and info["T8"] == rec.T8, (i, "thresholds")
         assert info["kmin_prev"] == rec.kmin_prev, (i, "kmin_prev")
     np.testing.assert_array_equal(run.histogram(i, 0), rec.H_E, err_msg=f"H_E step {i}")
-    np.testing.assert_array_equal(run.histogram(i, 1), rec.H_M, err_msg=f"H_M step {i}")
+    hm = run.histogram(i, 1)  # nlev entries; magnetisation levels use the first N + 1
+    np.testing.assert_array_equal(hm[: rec.H_M.size], rec.H_M, err_msg=f"H_M step {i}")
+    assert not hm[rec.H_M.size:].any(), (i, "H_M beyond N")
 
 
 def fnv1a64(pop) -> int:
