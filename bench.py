@@ -40,14 +40,20 @@ if ROOT not in sys.path:
 
 METRIC = "spin-flip attempts/ns (batched vs single-run, bit-exact); p50/p99 run latency"
 UNIT = "flips/ns"
-WL = dict(L=64, R=20000, theta=100, beta_f=1.0, dbeta=0.005)
+WL = dict(L=64, R=20000, theta=100, beta_f=1.0, dbeta=0.005, dim=2)
 DEFAULT_WL = dict(WL)
 
 
 def workload_label():
     n = int(round(WL["beta_f"] / WL["dbeta"]))
-    return (f"plain PA, 2D Ising L={WL['L']} periodic, R={WL['R']}, theta={WL['theta']}, beta 0->1 "
+    lattice = (f"2D Ising L={WL['L']} periodic" if WL["dim"] == 2 else
+               f"3D Ising (simple cubic) L={WL['L']}^3 periodic")
+    return (f"plain PA, {lattice}, R={WL['R']}, theta={WL['theta']}, beta 0->1 "
             f"dbeta={WL['dbeta']:g} ({n} steps), bit-packed spins")
+
+
+def sites():
+    return WL["L"] ** WL["dim"]
 
 
 WORKLOAD = workload_label()
@@ -141,17 +147,19 @@ def clocks_sampler_stop(h, path, gpu_index):
 
 # ------------------------------------------------------------------ CPU oracle
 def _oracle_sample(args):
-    """One worker: the oracle on R_s replicas of the workload for n_steps
-    temperature steps; returns (attempts, seconds)."""
-    R_s, n_steps, seed = args
+    """One worker: the oracle on R_s replicas of the workload `wl` for n_steps
+    temperature steps; returns (attempts, seconds). (Workers are spawned, so
+    the workload comes in the arguments, not from this module's globals.)"""
+    R_s, n_steps, seed, wl = args
     sys.path.insert(0, ROOT)
     from oracle.pa_oracle import PopulationAnnealing
     t0 = time.perf_counter()
-    pa = PopulationAnnealing(WL["L"], R_s, WL["theta"], beta_f=WL["beta_f"], dbeta=WL["dbeta"], seed=seed)
+    pa = PopulationAnnealing(wl["L"], R_s, wl["theta"], beta_f=wl["beta_f"], dbeta=wl["dbeta"], seed=seed,
+                             dim=wl["dim"])
     att = 0
     for _ in range(n_steps):
         rec = pa.step()
-        att += WL["L"] ** 2 * WL["theta"] * rec.R
+        att += wl["L"] ** wl["dim"] * wl["theta"] * rec.R
     return att, time.perf_counter() - t0
 
 
@@ -161,7 +169,7 @@ def cpu_oracle(workers: int, R_s: int, n_steps: int, seed0: int):
     oracle.build()
     t0 = time.perf_counter()
     with ctx.Pool(workers) as pool:
-        res = pool.map(_oracle_sample, [(R_s, n_steps, seed0 + w) for w in range(workers)])
+        res = pool.map(_oracle_sample, [(R_s, n_steps, seed0 + w, dict(WL)) for w in range(workers)])
     wall = time.perf_counter() - t0
     att = sum(a for a, _ in res)
     return att / wall / 1e9, att, wall
@@ -258,7 +266,7 @@ def run_engine(args):
     fmt = {"bits": eng.SPIN_BITS32, "msc": eng.SPIN_MSC32, "int8": eng.SPIN_INT8,
            "replica": eng.SPIN_REPLICA8}[args.format]
     cfg = eng.PAConfig(L=L, R=WL["R"], theta=theta, beta_f=WL["beta_f"], dbeta=WL["dbeta"], seed=seed_of(0),
-                       spin_format=fmt, use_graph=True, profile=args.profile,
+                       spin_format=fmt, use_graph=True, profile=args.profile, dim=WL["dim"],
                        group_threads=args.group_threads or 0)
     run = eng.PARun(cfg, stream=stream)
     n_steps = int(round(WL["beta_f"] / WL["dbeta"]))
@@ -293,7 +301,7 @@ def run_engine(args):
         ms = e0.elapsed_time(e1)
         rows = run.rows()
         assert len(rows) == n_steps + 1
-        attempts += L * L * theta * int(rows["R"][1:].sum())
+        attempts += sites() * theta * int(rows["R"][1:].sum())
         dev_ms += ms
         per_step_ms.append(ms)
     torch.cuda.synchronize(dev)
@@ -329,7 +337,7 @@ def run_engine(args):
                                  "ops": "4.5 Philox XOR + 1 compare + 0.5 logic per attempt"},
                     "attempts_per_ns": apn, "launch_ms": avg_ms, "launches": sw_n,
                     "share_of_step": sw_ms / dev_ms if dev_ms else None,
-                    "algorithmic_bytes_per_launch": 2 * att_per_launch / (L * L * theta) * (L * L / 8)}
+                    "algorithmic_bytes_per_launch": 2 * att_per_launch / (sites() * theta) * (sites() / 8)}
         try:
             roofline["rng_ceiling_words_per_ns"] = eng.measure_rng_peak(2048, stream)
         except Exception as e:  # measurement only
@@ -354,14 +362,15 @@ def run_engine(args):
         for k in range(max(1, args.e2e_steps)):
             t0 = time.perf_counter()
             r2 = eng.PARun(eng.PAConfig(L=L, R=WL["R"], theta=theta, beta_f=WL["beta_f"], dbeta=WL["dbeta"],
-                                        seed=seed_of(50_000 + k), spin_format=fmt), stream=stream)
+                                        seed=seed_of(50_000 + k), spin_format=fmt, dim=WL["dim"]), stream=stream)
             r2.run()
             rows = r2.rows()
             r2.close()
             wall += time.perf_counter() - t0
-            att_e2e += L * L * theta * int(rows["R"][1:].sum())
+            att_e2e += sites() * theta * int(rows["R"][1:].sum())
             # host tables uploaded by pa_create (thresholds, level weights, key)
-            h2d = 2 * (n_steps + 1) * 4 + (L * L + 1) * 8 + 8
+            thr_words = 3 if WL["dim"] == 3 else 2  # T4-1, T8-1 (and T12-1) per step
+            h2d = thr_words * (n_steps + 1) * 4 + (WL["dim"] * sites() // 2 + 1) * 8 + 8
             d2h = (n_steps + 1) * 128 + 4 + rows.nbytes
         wmax = max_over_ranks(wall, dist)
         e2e = {"value": sum_over_ranks(att_e2e, dist) / (wmax * 1e9), "unit": UNIT,
@@ -510,6 +519,8 @@ def main():
     ap.add_argument("--R", type=int, default=None, help="override the default workload's population")
     ap.add_argument("--theta", type=int, default=None, help="override the default workload's sweeps per step")
     ap.add_argument("--dbeta", type=float, default=None, help="override the default workload's step size")
+    ap.add_argument("--dim", type=int, choices=[2, 3], default=None,
+                    help="3: the simple cubic L x L x L lattice instead of the square one")
     ap.add_argument("--group-threads", type=int, default=None,
                     help="threads per replica of the bit-packed sweep (default: chosen by the engine)")
     ap.add_argument("--c4-steps", type=int, default=200)
@@ -527,7 +538,7 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    for k in ("L", "R", "theta", "dbeta"):  # labelled variants of the default workload
+    for k in ("L", "R", "theta", "dbeta", "dim"):  # labelled variants of the default workload
         if getattr(args, k) is not None:
             WL[k] = getattr(args, k)
     if args.impl == "reference":
