@@ -329,7 +329,7 @@ def run_engine(args):
         gt = shape["group_threads"]
         roofline = {"bound": "alu", "achieved": achieved, "peak": mul_peak, "unit": "Gop/s",
                     "frac": achieved / mul_peak, "traffic": profiled_traffic() if default_wl else None,
-                    "kernel": f"k_sweep_bits<{L},{gt}>", "launch": shape,
+                    "kernel": f"k_sweep_bits<{L},{gt}" + (",3>" if WL["dim"] == 3 else ">"), "launch": shape,
                     "ops": "lane-varying 32x32->64 multiplies of Philox4x32-10, 4 per attempt",
                     "peak_note": "FMA-heavy pipe: SMs x 32 wide multiplies/clk x max SM clock (derived)",
                     "alu_pipe": {"achieved": ALU_OPS_PER_ATTEMPT * apn, "peak": alu_peak,
