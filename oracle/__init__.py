@@ -62,6 +62,9 @@ def core() -> ctypes.CDLL:
                                            ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, i8p, i8p, i8p]
             lib.oracle_measure_j.argtypes = [ctypes.c_int, ctypes.c_int64, i8p, i8p, i8p, i64p, i64p]
             lib.oracle_measure.argtypes = [ctypes.c_int, ctypes.c_int64, i8p, i64p, i64p]
+            lib.oracle_msc_word.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
+                                            ctypes.c_uint32]
+            lib.oracle_msc_word.restype = ctypes.c_uint32
             lib.oracle_init3.argtypes = lib.oracle_init.argtypes
             lib.oracle_sweep3.argtypes = [ctypes.c_int, ctypes.c_int64, i64p, ctypes.c_uint64, ctypes.c_int64,
                                           ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, i8p]

@@ -231,6 +231,12 @@ static uint32_t msc_word(uint64_t seed, uint32_t u, uint32_t c, uint32_t b, uint
     return r;
 }
 
+/* The random word of replica k at site b of colour c in sweep u (for tests). */
+uint32_t oracle_msc_word(uint64_t seed, uint32_t u, uint32_t c, uint32_t b, uint32_t k)
+{
+    return msc_word(seed, u, c, b, k);
+}
+
 void oracle_sweep_msc(int L, int64_t n, const int64_t *slot, uint64_t seed, int64_t u0,
                       int theta, uint64_t T4, uint64_t T8, int8_t *s)
 {
