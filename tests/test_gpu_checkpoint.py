@@ -18,6 +18,8 @@ CASES = [
     ("int8-fixed", dict(L=6, R=500, theta=2, beta_f=0.4, dbeta=0.1, spin_format=eng.SPIN_INT8)),
     ("msc-fixed", dict(L=16, R=700, theta=3, beta_f=0.3, dbeta=0.05, spin_format=eng.SPIN_MSC32)),
     ("replica-fixed", dict(L=8, R=300, theta=2, beta_f=0.3, dbeta=0.1, spin_format=eng.SPIN_REPLICA8)),
+    ("cubic-fixed", dict(L=8, R=600, theta=2, beta_f=0.5, dbeta=0.1, spin_format=eng.SPIN_BITS32, dim=3)),
+    ("cubic-adaptive", dict(L=8, R=400, theta=2, beta_f=0.4, dbeta=0.0, spin_format=eng.SPIN_BITS32, dim=3)),
 ]
 
 
@@ -39,6 +41,18 @@ def test_resume_equals_uninterrupted(name, kw):
     np.testing.assert_array_equal(b.histogram(0, 2), ref.histogram(0, 2))
     np.testing.assert_array_equal(b.mag_sums(), ref.mag_sums())
     ref.close()
+    b.close()
+
+
+def test_restore_rejects_other_lattice_with_the_same_site_count():
+    """L = 16 simple cubic and L = 64 square lattices both have N = 4096."""
+    a = eng.PARun(eng.PAConfig(L=16, R=100, theta=1, beta_f=0.2, dbeta=0.1, seed=3, dim=3))
+    assert a.step()
+    blob = a.checkpoint()
+    a.close()
+    b = eng.PARun(eng.PAConfig(L=64, R=100, theta=1, beta_f=0.2, dbeta=0.1, seed=3))
+    with pytest.raises(eng.PAError):
+        b.restore(blob)
     b.close()
 
 
