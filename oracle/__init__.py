@@ -10,9 +10,9 @@ shares no code with it.
 Modules
 -------
 pa_oracle_core.c : Philox4x32-10, initial spins, Metropolis sweeps (also
-                   the multi-spin-coded LCG variant, the +-J model and the
-                   simple cubic lattice), measurement and the resampling
-                   uniforms (natural layout).
+                   the multi-spin-coded LCG variant, the +-J model, the
+                   simple cubic lattice and the q-state Potts model),
+                   measurement and the resampling uniforms (natural layout).
 pa_oracle.py     : the population-annealing step logic (Sec. 2.1-2.4).
 exact_ising.py   : exact 2D Ising references that pin the oracle.
 """
@@ -65,6 +65,10 @@ def core() -> ctypes.CDLL:
             lib.oracle_msc_word.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
                                             ctypes.c_uint32]
             lib.oracle_msc_word.restype = ctypes.c_uint32
+            lib.oracle_init_potts.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, i64p, ctypes.c_uint64, i8p]
+            lib.oracle_sweep_potts.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, i64p, ctypes.c_uint64,
+                                               ctypes.c_int64, ctypes.c_int, ctypes.POINTER(ctypes.c_uint64), i8p]
+            lib.oracle_measure_potts.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int64, i8p, i64p, i64p]
             lib.oracle_init3.argtypes = lib.oracle_init.argtypes
             lib.oracle_sweep3.argtypes = [ctypes.c_int, ctypes.c_int64, i64p, ctypes.c_uint64, ctypes.c_int64,
                                           ctypes.c_int, ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64, i8p]
@@ -73,6 +77,7 @@ def core() -> ctypes.CDLL:
             lib.oracle_philox_many.argtypes = [ctypes.c_int64, u32p, ctypes.c_uint64, u32p]
             for f in (lib.oracle_philox4x32_10, lib.oracle_init, lib.oracle_sweep, lib.oracle_sweep_msc,
                       lib.oracle_sweep_j, lib.oracle_measure_j, lib.oracle_init3, lib.oracle_sweep3,
+                      lib.oracle_init_potts, lib.oracle_sweep_potts, lib.oracle_measure_potts,
                       lib.oracle_measure3, lib.oracle_measure, lib.oracle_resample_words, lib.oracle_philox_many):
                 f.restype = None
             _lib = lib

@@ -16,7 +16,11 @@ uses beta_c = ln(1 + sqrt 2)/2. Four independent routes are given here:
 * ``transfer_matrix_dos`` counts the exact integer density of states g(E)
   of tori up to 6 x 6 (2^36 states) with the same row transfer;
 * ``kaufman_lnZ`` is Kaufman's (1949) closed form for the finite torus, in
-  the four-product form also used by Beale (1996).
+  the four-product form also used by Beale (1996);
+* ``potts_enumerate`` and ``potts_transfer_dos`` give the q-state Potts
+  model's exact joint counts of (E, majority-state size) on tiny tori and
+  its density of states for L = 4 (q = 2 is the Ising model with
+  E_Potts = E_Ising / 2 - N, a pin between the two).
 
 The tests check them against each other and against closed-form state
 counts before any of them is used as a pin for the oracle.
@@ -289,3 +293,64 @@ def kaufman_observables(L: int, beta: float, h: float = 1e-4) -> dict[str, float
     e = -d1 / N
     betaF = -f0 / N
     return {"e": e, "C": beta * beta * d2 / N, "betaF_per_N": betaF, "S_per_N": beta * e - betaF}
+
+
+# ------------------------------------------------------------ q-state Potts
+def potts_enumerate(L: int, q: int) -> dict[tuple[int, int], int]:
+    """Exact counts of (E, M) over all q^N states of the L x L torus, with
+    E = -(number of the 2N bonds joining equal states) and M the number of
+    sites in the most populated state (q^N <= 2^22)."""
+    N = L * L
+    if q ** N > 1 << 22:
+        raise ValueError("enumeration limited to q^N <= 2^22")
+    idx = np.arange(q ** N, dtype=np.int64)
+    s = np.empty((q ** N, L, L), dtype=np.int8)
+    for y in range(L):
+        for x in range(L):
+            s[:, y, x] = (idx // q ** (y * L + x)) % q
+    E = -((s == np.roll(s, -1, axis=2)).sum(axis=(1, 2)) + (s == np.roll(s, -1, axis=1)).sum(axis=(1, 2)))
+    M = np.max(np.stack([(s == t).sum(axis=(1, 2)) for t in range(q)]), axis=0)
+    keys, counts = np.unique(np.stack([E, M], axis=1), axis=0, return_counts=True)
+    return {(int(e), int(m)): int(c) for (e, m), c in zip(keys, counts)}
+
+
+def potts_averages(joint: dict, beta: float, N: int) -> dict[str, float]:
+    """e, C, <M>/N, <M^2>/N^2, <M^4>/N^4, beta F/N, S/N from exact (E, M)
+    counts (M: the majority state's size)."""
+    E = np.array([k[0] for k in joint], dtype=np.float64)
+    M = np.array([k[1] for k in joint], dtype=np.float64)
+    lw = np.log(np.array(list(joint.values()), dtype=np.float64)) - beta * E
+    lz = _logsumexp(lw)
+    w = np.exp(lw - lz)
+    e1, e2 = float(np.sum(w * E)), float(np.sum(w * E * E))
+    betaF = -lz / N
+    return {"e": e1 / N, "C": beta * beta * (e2 - e1 * e1) / N, "abs_m": float(np.sum(w * M)) / N,
+            "m2": float(np.sum(w * M ** 2)) / N ** 2, "m4": float(np.sum(w * M ** 4)) / N ** 4,
+            "betaF_per_N": betaF, "S_per_N": beta * e1 / N - betaF}
+
+
+def potts_transfer_dos(L: int, q: int) -> dict[int, int]:
+    """Exact g(E) of the q-state Potts model on the L x L torus by row
+    transfer (q^L row states; counts below 2^53, so L = 4 for q <= 8)."""
+    N = L * L
+    if float(q) ** N >= 2.0 ** 53 or q ** L > 4096:
+        raise ValueError("outside the exact float64 range")
+    n_rows = q ** L
+    idx = np.arange(n_rows)
+    rows = np.array([[(i // q ** x) % q for x in range(L)] for i in idx], dtype=np.int64)
+    h = -(rows == np.roll(rows, -1, axis=1)).sum(axis=1)                    # in-row bonds of b
+    v = -(rows[:, None, :] == rows[None, :, :]).sum(axis=2)                 # bonds between rows a, b
+    dE = v + h[None, :]                                                      # in [-2L, 0]
+    n_e = 2 * N + 1                                                          # index i <-> E = -i
+    cnt = np.zeros((n_rows, n_rows, n_e), dtype=np.float64)
+    cnt[idx, idx, 0] = 1.0
+    for _ in range(L):
+        nxt = np.zeros_like(cnt)
+        by_e = cnt.transpose(0, 2, 1)
+        for d in np.unique(dE):
+            moved = (by_e @ (dE == d).astype(np.float64)).transpose(0, 2, 1)
+            shift = -int(d)                                                  # E decreases by |d|
+            nxt[:, :, shift:] += moved[:, :, :n_e - shift]
+        cnt = nxt
+    closed = cnt[idx, idx, :].sum(axis=0)
+    return {-i: int(round(float(closed[i]))) for i in range(n_e) if closed[i] > 0}

@@ -81,13 +81,41 @@ def philox_many(ctr: np.ndarray, seed: int) -> np.ndarray:
     return out
 
 
-def init_spins(L: int, slots: np.ndarray, seed: int, dim: int = 2) -> np.ndarray:
+def init_spins(L: int, slots: np.ndarray, seed: int, dim: int = 2, potts_q: int = 0) -> np.ndarray:
+    """Initial configurations: Ising spins +1/-1, or Potts states 0..q-1
+    (potts_q >= 2, square lattice)."""
     import ctypes
     slots = np.ascontiguousarray(slots, dtype=np.int64)
     s = np.empty((slots.size,) + (L,) * dim, dtype=np.int8)
+    if potts_q:
+        core().oracle_init_potts(L, potts_q, slots.size, _ptr(slots, ctypes.c_int64), seed, _ptr(s, ctypes.c_int8))
+        return s
     fn = core().oracle_init3 if dim == 3 else core().oracle_init
     fn(L, slots.size, _ptr(slots, ctypes.c_int64), seed, _ptr(s, ctypes.c_int8))
     return s
+
+
+def sweep_potts(s: np.ndarray, slots: np.ndarray, seed: int, u0: int, theta: int, q: int, T) -> None:
+    """theta Potts Metropolis sweeps in place; T = (T1, T2, T3, T4), the
+    acceptance thresholds for dE = 1 .. 4."""
+    import ctypes
+    assert s.dtype == np.int8 and s.flags.c_contiguous
+    slots = np.ascontiguousarray(slots, dtype=np.int64)
+    t = (ctypes.c_uint64 * 4)(*[int(v) for v in T])
+    core().oracle_sweep_potts(s.shape[1], q, slots.size, _ptr(slots, ctypes.c_int64), seed, u0, theta, t,
+                              _ptr(s, ctypes.c_int8))
+
+
+def measure_potts(s: np.ndarray, q: int) -> tuple[np.ndarray, np.ndarray]:
+    """E = -(number of satisfied bonds) and M = size of the majority state."""
+    import ctypes
+    s = np.ascontiguousarray(s, dtype=np.int8)
+    n = s.shape[0]
+    E = np.empty(n, dtype=np.int64)
+    M = np.empty(n, dtype=np.int64)
+    core().oracle_measure_potts(s.shape[1], q, n, _ptr(s, ctypes.c_int8), _ptr(E, ctypes.c_int64),
+                                _ptr(M, ctypes.c_int64))
+    return E, M
 
 
 def sweep(s: np.ndarray, slots: np.ndarray, seed: int, u0: int, theta: int, T4: int, T8: int,
@@ -172,9 +200,10 @@ def pairwise_sum(a: np.ndarray) -> float:
     return float(a[0])
 
 
-def level_weights(delta: float, ndiff: int) -> np.ndarray:
-    """t[d] = exp(-(4 delta) d) for d = 0..ndiff-1 (libm exp, one call each)."""
-    f = 4.0 * delta
+def level_weights(delta: float, ndiff: int, estep: int = 4) -> np.ndarray:
+    """t[d] = exp(-(estep delta) d) for d = 0..ndiff-1 (libm exp, one call
+    each); estep is the energy between levels (4 Ising, 1 Potts)."""
+    f = float(estep) * delta
     return np.array([math.exp(-(f * float(d))) for d in range(ndiff)], dtype=np.float64)
 
 
@@ -195,10 +224,11 @@ def copy_tables(R: int, t: np.ndarray, S: float):
     return tau, F.astype(np.int64), U.astype(np.int64)
 
 
-def overlap_alpha(H: np.ndarray, kmin: int, kmax: int, R: int, R_prev: int, delta: float, K: int) -> float:
+def overlap_alpha(H: np.ndarray, kmin: int, kmax: int, R: int, R_prev: int, delta: float, K: int,
+                  estep: int = 4) -> float:
     """Histogram overlap of Sec. 2.3: (1/R_{i-1}) sum_j min(1, tau_hat_j),
     evaluated over levels in ascending order (K: the highest energy level)."""
-    t = level_weights(delta, kmax - kmin + 1)
+    t = level_weights(delta, kmax - kmin + 1, estep)
     S = normaliser_S(H, kmin, kmax, t, K)
     acc = 0.0
     for k in range(kmin, kmax + 1):
@@ -206,16 +236,16 @@ def overlap_alpha(H: np.ndarray, kmin: int, kmax: int, R: int, R_prev: int, delt
     return acc / float(R_prev)
 
 
-def choose_delta(H, kmin, kmax, R, R_prev, beta, beta_f, target, K):
+def choose_delta(H, kmin, kmax, R, R_prev, beta, beta_f, target, K, estep=4):
     """Adaptive step (Sec. 2.3): largest delta found by 60 bisection steps
     with alpha(delta) >= target; the whole remaining interval if it passes."""
     dmax = beta_f - beta
-    if overlap_alpha(H, kmin, kmax, R, R_prev, dmax, K) >= target:
+    if overlap_alpha(H, kmin, kmax, R, R_prev, dmax, K, estep) >= target:
         return dmax, True
     lo, hi = 0.0, dmax
     for _ in range(60):
         mid = 0.5 * (lo + hi)
-        if overlap_alpha(H, kmin, kmax, R, R_prev, mid, K) >= target:
+        if overlap_alpha(H, kmin, kmax, R, R_prev, mid, K, estep) >= target:
             lo = mid
         else:
             hi = mid
@@ -236,6 +266,7 @@ class StepRecord:
     T4: int = 0
     T8: int = 0
     T12: int = 0                    # 3D only (six aligned neighbours)
+    TP: tuple = ()                  # Potts only: thresholds for dE = 1 .. 4
     H_E: np.ndarray | None = None   # histogram of this step's population
     H_M: np.ndarray | None = None
     counts: np.ndarray | None = None  # r_j of the previous population
@@ -272,8 +303,10 @@ def moment_sums(E: np.ndarray, M: np.ndarray):
             sum(v * v for v in Mi), sum(v ** 4 for v in Mi))
 
 
-def make_row(beta: float, N: int, R: int, sums, sum_lnQ: float, lnQ: float, families: int) -> Row:
-    """Eq. observables, Eq. free-energy (Z_beta0 = 2^N) and Eq. entropy.
+def make_row(beta: float, N: int, R: int, sums, sum_lnQ: float, lnQ: float, families: int,
+             states: int = 2) -> Row:
+    """Eq. observables, Eq. free-energy (Z_beta0 = states^N: 2 for Ising
+    spins, q for the q-state Potts model) and Eq. entropy.
     C uses the exact integer numerator R sum E^2 - (sum E)^2, which equals
     beta^2 N (mean(e^2) - mean(e)^2) without cancellation."""
     sE, sE2, sAM, sM2, sM4 = sums
@@ -283,7 +316,7 @@ def make_row(beta: float, N: int, R: int, sums, sum_lnQ: float, lnQ: float, fami
     abs_m = float(sAM) / (fR * fN)
     m2 = float(sM2) / (fR * fN * fN)
     m4 = float(sM4) / (fR * fN * fN * fN * fN)
-    betaF = -(fN * math.log(2.0) + sum_lnQ) / fN
+    betaF = -(fN * math.log(float(states)) + sum_lnQ) / fN
     return Row(beta, e, C, abs_m, m2, m4, betaF, beta * e - betaF, lnQ, R, families, N)
 
 
@@ -295,11 +328,13 @@ class PopulationAnnealing:
     def __init__(self, L: int, R: int, theta: int, beta_f: float = 1.0, dbeta: float = 0.01,
                  seed: int = 1, beta0: float = 0.0, overlap: float = 0.85,
                  capacity: int = 0, record_hist: bool = True, schedule=None, msc: bool = False,
-                 couplings=None, dim: int = 2):
+                 couplings=None, dim: int = 2, potts_q: int = 0):
         if dim not in (2, 3):
             raise ValueError("dim must be 2 or 3")
-        if L % 2 or L < (4 if dim == 2 else 2):
-            raise ValueError("L must be even and >= 4 (>= 2 in 3D)")
+        if potts_q and not (2 <= potts_q <= 8 and dim == 2 and not msc and couplings is None):
+            raise ValueError("the Potts model: 2 <= q <= 8, square lattice, plain Philox sweeps")
+        if L % 2 or L < (4 if dim == 2 and not potts_q else 2):
+            raise ValueError("L must be even and >= 4 (>= 2 in 3D and for the Potts model)")
         if dim == 3 and (msc or couplings is not None):
             raise ValueError("the 3D model has plain Philox sweeps and J = 1")
         if beta0 != 0.0:
@@ -307,9 +342,12 @@ class PopulationAnnealing:
         if R < 1 or theta < 1 or not (beta_f > beta0):
             raise ValueError("bad R, theta or beta_f")
         self.dim = dim
+        self.q = int(potts_q)             # 0: Ising
         self.L, self.N, self.R, self.theta = L, L ** dim, int(R), int(theta)
-        self.eoff = dim * self.N          # E_k = 4 k - eoff
-        self.nl = dim * self.N // 2 + 1   # energy levels
+        self.estep = 1 if self.q else 4   # energy between adjacent levels
+        self.eoff = dim * self.N          # E_k = estep k - eoff
+        # energy levels: Ising (E + dim N)/4 = 0 .. dim N/2; Potts E + 2N = 0 .. 2N
+        self.nl = (2 * self.N if self.q else dim * self.N // 2) + 1
         self.seed = int(seed)
         self.beta_f = float(beta_f)
         self.dbeta = float(dbeta)
@@ -341,8 +379,8 @@ class PopulationAnnealing:
         self.partial = False
         # step 0: random configurations at beta0 = 0, measured, no sweeps
         slots = np.arange(self.R, dtype=np.int64)
-        self.pop = init_spins(L, slots, self.seed, dim)
-        self.E, self.M = measure(self.pop, self.J)
+        self.pop = init_spins(L, slots, self.seed, dim, self.q)
+        self.E, self.M = self._measure(self.pop)
         self.fam = np.arange(self.R, dtype=np.int64)
         self.sum_lnQ = 0.0
         self.Hsum = np.zeros(self.nl, dtype=np.int64)
@@ -355,10 +393,20 @@ class PopulationAnnealing:
 
     # -- helpers
     def levels(self) -> np.ndarray:
-        return (self.E + self.eoff) // 4
+        return (self.E + self.eoff) // self.estep
 
     def mlevels(self) -> np.ndarray:
-        return (self.M + self.N) // 2
+        # Ising: number of up spins; Potts: M itself (the majority state's size)
+        return self.M if self.q else (self.M + self.N) // 2
+
+    def _measure(self, s):
+        return measure_potts(s, self.q) if self.q else measure(s, self.J)
+
+    def _sweep(self, s, slots, u0, T4, T8, T12, TP):
+        if self.q:
+            sweep_potts(s, slots, self.seed, u0, self.theta, self.q, TP)
+        else:
+            sweep(s, slots, self.seed, u0, self.theta, T4, T8, msc=self.msc, couplings=self.J, T12=T12)
 
     def _measure_and_record(self, rec: StepRecord):
         N = self.N
@@ -376,7 +424,8 @@ class PopulationAnnealing:
             rec.H_E, rec.H_M = H_E, H_M
         self.sum_lnQ += rec.lnQ
         self.records.append(rec)
-        self.rows.append(make_row(rec.beta, N, rec.R, rec.sums, self.sum_lnQ, rec.lnQ, rec.families))
+        self.rows.append(make_row(rec.beta, N, rec.R, rec.sums, self.sum_lnQ, rec.lnQ, rec.families,
+                                  self.q or 2))
 
     def n_steps_left(self):
         return None if self.adaptive else self.n_fixed - self.step_index
@@ -402,7 +451,8 @@ class PopulationAnnealing:
             delta = beta_new - self.beta
             final = i == self.n_fixed
         elif self.adaptive:
-            delta, final = choose_delta(H, kmin, kmax, R, R_prev, self.beta, self.beta_f, self.overlap, K)
+            delta, final = choose_delta(H, kmin, kmax, R, R_prev, self.beta, self.beta_f, self.overlap, K,
+                                        self.estep)
             if delta <= 0.0:
                 raise OracleError("stalled", "adaptive step found no positive delta")
             beta_new = self.beta_f if final else self.beta + delta
@@ -411,7 +461,7 @@ class PopulationAnnealing:
             beta_new = 0.0 + i * self.dbeta
             final = i == self.n_fixed
         # Eq. Q with the E_min shift, and the copy numbers of Eq. resampling-factors
-        t = level_weights(delta, kmax - kmin + 1)
+        t = level_weights(delta, kmax - kmin + 1, self.estep)
         S = normaliser_S(H, kmin, kmax, t, K)
         _, F, U = copy_tables(R, t, S)
         x = resample_words(self.seed, i, R_prev).astype(np.int64)
@@ -423,13 +473,15 @@ class PopulationAnnealing:
         if R_new == 0:
             raise OracleError("extinct", f"population died out at step {i}")
         parent = np.repeat(np.arange(R_prev, dtype=np.int64), r)
-        E_min = -self.eoff + 4 * kmin
+        E_min = -self.eoff + self.estep * kmin
         lnQ = (math.log(S) - math.log(float(R_prev))) - delta * float(E_min)
         T4 = metropolis_threshold(beta_new, 4)
         T8 = metropolis_threshold(beta_new, 8)
         T12 = metropolis_threshold(beta_new, 12) if self.dim == 3 else None
+        TP = tuple(metropolis_threshold(beta_new, d) for d in (1, 2, 3, 4)) if self.q else ()
         rec = StepRecord(step=i, beta=beta_new, delta=delta, R=R_new, R_prev=R_prev, kmin_prev=kmin,
-                         S=S, lnQ=lnQ, T4=T4, T8=T8, T12=T12 or 0, counts=r if self.record_hist else None)
+                         S=S, lnQ=lnQ, T4=T4, T8=T8, T12=T12 or 0, TP=TP,
+                         counts=r if self.record_hist else None)
         rec.parent = parent
         u0 = (i - 1) * self.theta
         if sample is not None:
@@ -437,19 +489,18 @@ class PopulationAnnealing:
                 sample = sample(R_new)
             sample = np.asarray(sample, dtype=np.int64)
             sub = np.ascontiguousarray(self.pop[parent[sample]])
-            sweep(sub, sample, self.seed, u0, self.theta, T4, T8, msc=self.msc, couplings=self.J, T12=T12)
+            self._sweep(sub, sample, u0, T4, T8, T12, TP)
             rec.sample = sample
             rec.sample_pop = sub
-            rec.sample_E, rec.sample_M = measure(sub, self.J)
+            rec.sample_E, rec.sample_M = self._measure(sub)
             rec.sample_fam = self.fam[parent[sample]]
             self.partial = True
             self.records.append(rec)
             return rec
         self.pop = np.ascontiguousarray(self.pop[parent])
         self.fam = self.fam[parent]
-        sweep(self.pop, np.arange(R_new, dtype=np.int64), self.seed, u0, self.theta, T4, T8, msc=self.msc,
-              couplings=self.J, T12=T12)
-        self.E, self.M = measure(self.pop, self.J)
+        self._sweep(self.pop, np.arange(R_new, dtype=np.int64), u0, T4, T8, T12, TP)
+        self.E, self.M = self._measure(self.pop)
         self.step_index = i
         self.beta = beta_new
         self.done = bool(final)
@@ -465,9 +516,9 @@ class PopulationAnnealing:
     def ln_dos(self) -> tuple[np.ndarray, np.ndarray]:
         """ln Omega(E_k) for every level with Hsum[k] > 0 (others -inf):
         ln Omega_k = ln Hsum_k - LSE_i(ln R_i + beta_i F_i - beta_i E_k),
-        beta_i F_i = -(N ln 2 + sum_{l<=i} ln Q_l)."""
+        beta_i F_i = -(N ln 2 + sum_{l<=i} ln Q_l) (N ln q for Potts)."""
         N = self.N
-        E_k = (-self.eoff + 4 * np.arange(self.nl)).astype(np.float64)
+        E_k = (-self.eoff + self.estep * np.arange(self.nl)).astype(np.float64)
         betas = np.array([r.beta for r in self.rows])
         lnR = np.log(np.array([float(r.R) for r in self.rows]))
         bF = np.array([r.betaF_per_N for r in self.rows]) * N

@@ -29,6 +29,8 @@
  *   SWEEP    (tag 1): ctr = (2u + c, b>>2, 1, k),                   x = out[b&3]
  *   RESAMPLE (tag 2): ctr = (i, j>>2, 2, 0),                        x = out[j&3]
  *   MSC seed (tag 5): ctr = (2u + c, b>>2, 5, k/32),               x = out[b&3]
+ *   POTTS    (tag 6): ctr = (2u + c, b>>1, 6, k), proposal word out[2(b&1)],
+ *                     acceptance word out[2(b&1) + 1]
  * where c = (x+y)&1 is the checkerboard colour of site (x, y),
  * b = y*(L/2) + (x>>1) its index within the colour, k the replica slot,
  * u the global sweep number, i the temperature step and j the old slot.
@@ -393,5 +395,100 @@ void oracle_measure3(int L, int64_t n, const int8_t *s, int64_t *E, int64_t *M)
                 }
         E[r] = e;
         M[r] = m;
+    }
+}
+
+/* ------------------------------------------------------------------ Potts
+ * q-state Potts model on the periodic L x L lattice (one of the further
+ * models the paper's conclusion names): H = -sum over the 2N bonds of
+ * delta(s_i, s_j), s in {0, .., q-1}. Readings:
+ *  - initial states: s = floor(x q / 2^32) with x the INIT word of the site;
+ *  - Metropolis update of a site in state s: the POTTS words (w0, w1) of the
+ *    site propose s' = (s + 1 + floor(w0 (q-1) / 2^32)) mod q, uniform over
+ *    the q-1 other states; with n(t) the number of the four neighbours in
+ *    state t, dE = n(s) - n(s'); accepted if dE <= 0, else iff w1 < T[dE-1],
+ *    T[d-1] = ceil(exp(-d beta) 2^32) (computed by the caller), d = 1 .. 4;
+ *  - "magnetisation" M = the number of sites in the most populated state.
+ */
+static uint32_t potts_state(uint64_t x, int q)
+{
+    return (uint32_t)((x * (uint64_t)q) >> 32);
+}
+
+void oracle_init_potts(int L, int q, int64_t n, const int64_t *slot, uint64_t seed, int8_t *s)
+{
+    const int N = L * L, half = L / 2;
+    for (int64_t r = 0; r < n; r++) {
+        int8_t *S = s + (size_t)r * N;
+        uint32_t k = (uint32_t)slot[r];
+        for (int y = 0; y < L; y++)
+            for (int x = 0; x < L; x++) {
+                uint32_t c = (uint32_t)((x + y) & 1);
+                uint32_t b = (uint32_t)(y * half + (x >> 1));
+                uint32_t g = c * (uint32_t)(N / 2) + b;
+                uint32_t w = stream_word(seed, 0u, g >> 2, 0u, k, g & 3u);
+                S[y * L + x] = (int8_t)potts_state(w, q);
+            }
+    }
+}
+
+void oracle_sweep_potts(int L, int q, int64_t n, const int64_t *slot, uint64_t seed, int64_t u0, int theta,
+                        const uint64_t *T, int8_t *s)
+{
+    const int N = L * L, half = L / 2;
+    for (int64_t r = 0; r < n; r++) {
+        int8_t *S = s + (size_t)r * N;
+        uint32_t k = (uint32_t)slot[r];
+        for (int sw = 0; sw < theta; sw++) {
+            uint32_t u = (uint32_t)(u0 + sw);
+            for (int c = 0; c < 2; c++) {
+                for (int y = 0; y < L; y++)
+                    for (int x = 0; x < L; x++) {
+                        if (((x + y) & 1) != c)
+                            continue;
+                        uint32_t b = (uint32_t)(y * half + (x >> 1));
+                        uint32_t ctr[4] = {2u * u + (uint32_t)c, b >> 1, 6u, k};
+                        uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32)};
+                        uint32_t out[4];
+                        oracle_philox4x32_10(ctr, key, out);
+                        uint32_t w0 = out[2 * (b & 1u)], w1 = out[2 * (b & 1u) + 1];
+                        int si = S[y * L + x];
+                        int sp = (int)((si + 1 + (int)potts_state(w0, q - 1)) % q);
+                        int nb[4] = {S[y * L + (x + 1) % L], S[y * L + (x + L - 1) % L],
+                                     S[((y + 1) % L) * L + x], S[((y + L - 1) % L) * L + x]};
+                        int ns = 0, np = 0;
+                        for (int j = 0; j < 4; j++) {
+                            ns += nb[j] == si;
+                            np += nb[j] == sp;
+                        }
+                        int dE = ns - np;
+                        int accept = dE <= 0 || (uint64_t)w1 < T[dE - 1];
+                        if (accept)
+                            S[y * L + x] = (int8_t)sp;
+                    }
+            }
+        }
+    }
+}
+
+void oracle_measure_potts(int L, int q, int64_t n, const int8_t *s, int64_t *E, int64_t *M)
+{
+    const int N = L * L;
+    for (int64_t r = 0; r < n; r++) {
+        const int8_t *S = s + (size_t)r * N;
+        int64_t e = 0;
+        int64_t cnt[256] = {0};
+        for (int y = 0; y < L; y++)
+            for (int x = 0; x < L; x++) {
+                int si = S[y * L + x];
+                e -= (S[y * L + (x + 1) % L] == si) + (S[((y + 1) % L) * L + x] == si);
+                cnt[si]++;
+            }
+        int64_t mx = 0;
+        for (int t = 0; t < q; t++)
+            if (cnt[t] > mx)
+                mx = cnt[t];
+        E[r] = e;
+        M[r] = mx;
     }
 }
