@@ -97,7 +97,17 @@ typedef struct {
                                = 0 .. 3N/2, so every histogram has 3N/2 + 1
                                entries; magnetisation levels use the first
                                N + 1)                                           */
-    int32_t reserved[2];    /* must be 0                                          */
+    int32_t potts_q;        /* 0: Ising spins; 2..8: the q-state Potts model,
+                               H = -sum over bonds of delta(s_i, s_j) (a further
+                               model the paper's conclusion names), square
+                               lattice, PA_SPIN_INT8 only (byte states 0..q-1).
+                               Energy levels k = E + 2N = 0 .. 2N (histograms of
+                               2N + 1 entries); the "magnetisation" M is the
+                               number of sites in the most populated state
+                               (levels m = M); Z at beta0 = 0 is q^N. The
+                               update proposes a uniform other state and
+                               accepts by Metropolis on dE = n(s) - n(s')   */
+    int32_t reserved[1];    /* must be 0                                          */
 } pa_config;
 
 /* One output row (Sec. 3 "Further optimization and parameters": beta, e, C,
@@ -201,8 +211,8 @@ pa_status pa_observables(pa_ctx *ctx, pa_obs *rows, int64_t cap, int64_t *n_rows
 pa_status pa_step_info_get(pa_ctx *ctx, int64_t step, pa_step_info *out);
 
 /* Histogram of nlev entries into host `out` (cap >= nlev), where nlev =
- * N + 1 on the square lattice (N = L*L) and 3N/2 + 1 on the simple cubic
- * one (N = L^3):
+ * N + 1 on the square lattice (N = L*L), 3N/2 + 1 on the simple cubic one
+ * (N = L^3) and 2N + 1 for the Potts model (levels k = E + 2N):
  * PA_HIST_E: energy levels k = (E + dim N)/4 of step `step`;
  * PA_HIST_M: magnetisation levels m = (M + N)/2 of step `step` (entries
  * above N are 0);
@@ -212,8 +222,8 @@ pa_status pa_step_info_get(pa_ctx *ctx, int64_t step, pa_step_info *out);
 pa_status pa_histogram(pa_ctx *ctx, int64_t step, int32_t kind, int64_t *out, int64_t cap);
 
 /* Current population in natural layout: host_out[r*N + y*L + x] = +1 / -1
- * (simple cubic: host_out[r*N + (z*L + y)*L + x]) for replica slot r < *n
- * (cap is in replicas). */
+ * (simple cubic: host_out[r*N + (z*L + y)*L + x]; Potts: the state 0..q-1)
+ * for replica slot r < *n (cap is in replicas). */
 pa_status pa_population(pa_ctx *ctx, int8_t *host_out, int64_t cap, int64_t *n);
 
 /* 64-bit FNV-1a hash of the current population in the layout of

@@ -41,7 +41,7 @@ class _Config(ctypes.Structure):
                 ("overlap", ctypes.c_double), ("seed", ctypes.c_uint64), ("spin_format", ctypes.c_int32),
                 ("record_histograms", ctypes.c_int32), ("capacity", ctypes.c_int64),
                 ("group_threads", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("dim", ctypes.c_int32), ("reserved", ctypes.c_int32 * 2)]
+                ("dim", ctypes.c_int32), ("potts_q", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
 
 
 class _Obs(ctypes.Structure):
@@ -171,6 +171,7 @@ class PAConfig:
     use_graph: bool = True
     profile: bool = False
     dim: int = 2                 # 3: the L x L x L simple cubic lattice (bit-packed, L in 8..64)
+    potts_q: int = 0             # 2..8: the q-state Potts model (SPIN_INT8, square lattice)
 
     @property
     def n_sites(self) -> int:
@@ -179,6 +180,8 @@ class PAConfig:
     @property
     def nlev(self) -> int:
         """Entries of every histogram: energy levels k = (E + dim N)/4."""
+        if self.potts_q:
+            return 2 * self.n_sites + 1
         d = 3 if self.dim == 3 else 2
         return d * self.n_sites // 2 + 1
 
@@ -194,6 +197,7 @@ class PAConfig:
         c.use_graph = int(bool(self.use_graph))
         c.profile = int(bool(self.profile))
         c.dim = self.dim
+        c.potts_q = self.potts_q
         return c
 
 

@@ -60,11 +60,12 @@ double tree_sum(const std::vector<long long>& H, const std::vector<double>& w, i
     return a + b;
 }
 
-// level weights exp(-(4 delta) d), d = 0..nd-1 (libm exp, one call each)
-void level_weights(double delta, int nd, std::vector<double>& w)
+// level weights exp(-(estep delta) d), d = 0..nd-1 (libm exp, one call each);
+// estep is the energy between adjacent levels (4 Ising, 1 Potts)
+void level_weights(double delta, int nd, std::vector<double>& w, int estep = 4)
 {
     w.resize((size_t)nd);
-    const double f = 4.0 * delta;
+    const double f = (double)estep * delta;
     for (int d = 0; d < nd; d++) w[(size_t)d] = std::exp(-(f * (double)d));
 }
 
@@ -176,8 +177,10 @@ pa_status validate(const pa_config& c)
     if (c.capacity < 0 || (c.capacity > 0 && c.capacity < c.R)) return PA_EINVAL;
     if (c.group_threads < 0 || (c.group_threads & (c.group_threads - 1))) return PA_EINVAL;
     if (c.group_threads > 32 && !(c.group_threads == 256 && c.spin_format == PA_SPIN_BITS32)) return PA_EINVAL;
-    if (c.reserved[0] || c.reserved[1]) return PA_EINVAL;
+    if (c.reserved[0]) return PA_EINVAL;
     if (c.dim != 0 && c.dim != 2 && c.dim != 3) return PA_EINVAL;
+    if (c.potts_q != 0 && (c.potts_q < 2 || c.potts_q > 8 || c.spin_format != PA_SPIN_INT8 || c.dim == 3))
+        return PA_EINVAL;
     if (c.dim == 3 && (c.spin_format != PA_SPIN_BITS32 || !bits3_L_ok(c.L))) return PA_EINVAL;
     return PA_OK;
 }
@@ -237,7 +240,8 @@ Sizes sizes_of(const pa_config& c)
 {
     Sizes s{};
     s.N = (int)sites_of(c);
-    s.nlev = dim_of(c) * s.N / 2 + 1;
+    // Ising: (E + dim N)/4 = 0 .. dim N/2; Potts: E + 2N = 0 .. 2N
+    s.nlev = (c.potts_q ? 2 * s.N : dim_of(c) * s.N / 2) + 1;
     s.cap = capacity_of(c);
     s.ntiles = (s.cap + pa::kTile - 1) / pa::kTile;
     s.words = words_of(c);
@@ -260,7 +264,7 @@ size_t footprint(const pa_config& c)
     b += 2 * 2 * N1 * 4;                            // H
     b += N1 * 8 * 3 + N1 * 4;                       // Hsum, tw, U, F
     b += N1 * 8 * 5;                                // magnetisation sums per level
-    b += (size_t)(dim_of(c) == 3 ? 3 : 2) * (size_t)(s.steps + 1) * 4;  // thresholds
+    b += (size_t)(dim_of(c) == 3 ? 3 : (c.potts_q ? 6 : 2)) * (size_t)(s.steps + 1) * 4;  // thresholds
     b += (size_t)(s.steps + 1) * sizeof(StepDev);   // records
     b += (size_t)s.hist_steps * 2 * N1 * 4;         // recorded histograms
     b += 64;                                        // status + work
@@ -396,10 +400,10 @@ pa_status pull_records(pa_ctx* c)
 // Host FP64 of the adaptive step (Sec. 2.3): overlap alpha(delta) of the
 // histogram H of population i-1 (levels ascending), bisection to alpha*.
 double overlap_alpha(const std::vector<long long>& H, int kmin, int kmax, long long R, long long Rprev,
-                     double delta, long long P)
+                     double delta, long long P, int estep)
 {
     std::vector<double> w;
-    level_weights(delta, kmax - kmin + 1, w);
+    level_weights(delta, kmax - kmin + 1, w, estep);
     const double S = tree_sum(H, w, kmin, kmax, 0, P);
     double acc = 0.0;
     for (int k = kmin; k <= kmax; k++) {
@@ -451,7 +455,7 @@ pa_status enqueue_step(pa_ctx* c, bool wait = true)
             beta = c->sched[(size_t)(i - 1)];
             delta = beta - bprev;
             final_step = (i == (long long)c->sched.size());
-        } else if (overlap_alpha(H, kmin, kmax, c->cfg.R, pr.R, dmax, P) >= target) {
+        } else if (overlap_alpha(H, kmin, kmax, c->cfg.R, pr.R, dmax, P, c->h.estep) >= target) {
             delta = dmax;
             final_step = true;
             beta = c->cfg.beta_f;
@@ -459,7 +463,7 @@ pa_status enqueue_step(pa_ctx* c, bool wait = true)
             double lo = 0.0, hi = dmax;
             for (int it = 0; it < 60; it++) {
                 const double mid = 0.5 * (lo + hi);
-                if (overlap_alpha(H, kmin, kmax, c->cfg.R, pr.R, mid, P) >= target) lo = mid;
+                if (overlap_alpha(H, kmin, kmax, c->cfg.R, pr.R, mid, P, c->h.estep) >= target) lo = mid;
                 else hi = mid;
             }
             if (!(lo > 0.0)) return PA_ESTALLED;
@@ -469,7 +473,7 @@ pa_status enqueue_step(pa_ctx* c, bool wait = true)
         }
         // level weights for this step and its thresholds
         std::vector<double> w;
-        level_weights(delta, nl, w);
+        level_weights(delta, nl, w, c->h.estep);
         uint32_t thr[2];
         const uint64_t t4 = threshold(beta, 4.0), t8 = threshold(beta, 8.0);
         thr[0] = (uint32_t)(t4 - 1);
@@ -484,6 +488,11 @@ pa_status enqueue_step(pa_ctx* c, bool wait = true)
             uint32_t* t12 = (uint32_t*)(st + sizeof(double) * (size_t)nl + sizeof(thr));
             *t12 = (uint32_t)(threshold(beta, 12.0) - 1);
             PA_CUDA(cudaMemcpyAsync(c->h.thr12 + i, t12, 4, cudaMemcpyHostToDevice, c->stream));
+        }
+        if (c->h.thrp) {
+            uint32_t* tp = (uint32_t*)(st + sizeof(double) * (size_t)nl + sizeof(thr) + 16);
+            for (int d = 1; d <= 4; d++) tp[d - 1] = (uint32_t)(threshold(beta, (double)d) - 1);
+            PA_CUDA(cudaMemcpyAsync(c->h.thrp + 4 * i, tp, 16, cudaMemcpyHostToDevice, c->stream));
         }
         c->T4.push_back(t4);
         c->T8.push_back(t8);
@@ -526,7 +535,8 @@ void make_row(const pa_ctx* c, long long i, double sum_lnQ, double lnQ, pa_obs* 
     o->abs_m = (double)sAM / (fR * fN);
     o->m2 = (double)sM2 / (fR * fN * fN);
     o->m4 = (double)sM4 / (fR * fN * fN * fN * fN);
-    o->betaF_per_N = -(fN * std::log(2.0) + sum_lnQ) / fN;
+    // Z at beta0 = 0 counts every configuration: 2^N spins, q^N Potts states
+    o->betaF_per_N = -(fN * std::log(c->h.potts_q ? (double)c->h.potts_q : 2.0) + sum_lnQ) / fN;
     o->S_per_N = beta * o->e - o->betaF_per_N;
     o->lnQ = lnQ;
     o->R = r.R;
@@ -537,7 +547,7 @@ double lnQ_of(const pa_ctx* c, long long i)
 {
     if (i == 0) return 0.0;
     const StepDev& r = c->recs[(size_t)i];
-    const double Emin = (double)(-c->h.eoff + 4ll * r.kmin_prev);
+    const double Emin = (double)(-c->h.eoff + (long long)c->h.estep * r.kmin_prev);
     return (std::log(r.S) - std::log((double)r.R_prev)) - c->deltas[(size_t)i] * Emin;
 }
 
@@ -801,7 +811,7 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     if (Jr) {
         if (cfg->spin_format != PA_SPIN_BITS32 && cfg->spin_format != PA_SPIN_INT8) return PA_EINVAL;
         long long neg = 0;
-        if (dim_of(*cfg) != 2) return PA_EINVAL;  // +-J bonds: square lattice only
+        if (dim_of(*cfg) != 2 || cfg->potts_q) return PA_EINVAL;  // +-J bonds: square-lattice Ising only
         const long long N = (long long)cfg->L * cfg->L;
         for (long long i = 0; i < N; i++) {
             if ((Jr[i] != 1 && Jr[i] != -1) || (Jd[i] != 1 && Jd[i] != -1)) return PA_EINVAL;
@@ -849,7 +859,9 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     h.unit = 1u;
     h.dim = dim_of(*cfg);
     h.nlev = s.nlev;
-    h.eoff = (long long)h.dim * s.N;
+    h.potts_q = cfg->potts_q;
+    h.estep = cfg->potts_q ? 1 : 4;
+    h.eoff = (long long)h.dim * s.N;  // Ising dim N; Potts (square lattice) 2N
     const size_t N1 = (size_t)s.nlev;
     pa_status st = PA_OK;
 #define PA_ALLOC(p, n)                            \
@@ -880,6 +892,7 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     PA_ALLOC(h.U, N1);
     PA_ALLOC(h.thr, 2 * (size_t)(s.steps + 1));
     if (h.dim == 3) PA_ALLOC(h.thr12, (size_t)(s.steps + 1));
+    if (h.potts_q) PA_ALLOC(h.thrp, 4 * (size_t)(s.steps + 1));
     PA_ALLOC(h.rec, (size_t)(s.steps + 1));
     if (s.hist_steps) PA_ALLOC(h.hist_rec, (size_t)s.hist_steps * 2 * N1);
     PA_ALLOC(h.status, 4);
@@ -917,20 +930,23 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     if (!c->adaptive) {
         // all thresholds and the (fixed) level weights up front
         std::vector<uint32_t> thr(2 * (size_t)(s.steps + 1), 0xffffffffu), thr12((size_t)(s.steps + 1), 0xffffffffu);
+        std::vector<uint32_t> thrp(4 * (size_t)(s.steps + 1), 0xffffffffu);
         for (long long i = 1; i <= s.steps; i++) {
             const double beta = 0.0 + (double)i * cfg->dbeta;
             const uint64_t t4 = threshold(beta, 4.0), t8 = threshold(beta, 8.0);
             thr[2 * (size_t)i] = (uint32_t)(t4 - 1);
             thr[2 * (size_t)i + 1] = (uint32_t)(t8 - 1);
             thr12[(size_t)i] = (uint32_t)(threshold(beta, 12.0) - 1);
+            for (int d = 1; d <= 4; d++) thrp[4 * (size_t)i + (size_t)(d - 1)] = (uint32_t)(threshold(beta, (double)d) - 1);
             c->T4.push_back(t4);
             c->T8.push_back(t8);
         }
         std::vector<double> w;
-        level_weights(cfg->dbeta, (int)N1, w);
+        level_weights(cfg->dbeta, (int)N1, w, h.estep);
         if (cudaMemcpy(h.thr, thr.data(), thr.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
             cudaMemcpy(h.tw, w.data(), N1 * 8, cudaMemcpyHostToDevice) != cudaSuccess ||
-            (h.thr12 && cudaMemcpy(h.thr12, thr12.data(), thr12.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess))
+            (h.thr12 && cudaMemcpy(h.thr12, thr12.data(), thr12.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess) ||
+            (h.thrp && cudaMemcpy(h.thrp, thrp.data(), thrp.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess))
             return fail(PA_ECUDA);
     }
     if (pa::plan_sweep(h, &c->ln) != cudaSuccess) {
@@ -1180,7 +1196,9 @@ pa_status pa_population(pa_ctx* c, int8_t* host_out, int64_t cap, int64_t* n)
                     int up;
                     if (c->h.fmt == PA_SPIN_BITS32) up = (w[col * (N / 64) + (b >> 5)] >> (b & 31)) & 1u;
                     else up = bytes[col * (N / 2) + b];
-                    host_out[(size_t)r * N + ((size_t)z * L + y) * L + x] = up ? 1 : -1;
+                    // Potts: the state 0..q-1 itself
+                    host_out[(size_t)r * N + ((size_t)z * L + y) * L + x] =
+                        c->h.potts_q ? (int8_t)up : (int8_t)(up ? 1 : -1);
                 }
     }
     *n = m;
@@ -1203,8 +1221,8 @@ pa_status pa_replicas(pa_ctx* c, int32_t* E, int32_t* M, int64_t* family, int64_
         PA_CUDA(cudaMemcpy(fv.data(), c->h.fam[last & 1], (size_t)m * 4, cudaMemcpyDeviceToHost));
     }
     for (long long r = 0; r < m; r++) {
-        if (E) E[r] = (int32_t)(4ll * ev[(size_t)r] - c->h.eoff);
-        if (M) M[r] = 2 * mv[(size_t)r] - c->N;
+        if (E) E[r] = (int32_t)((long long)c->h.estep * ev[(size_t)r] - c->h.eoff);
+        if (M) M[r] = c->h.potts_q ? mv[(size_t)r] : 2 * mv[(size_t)r] - c->N;
         if (family) family[r] = fv[(size_t)r];
     }
     *n = m;
@@ -1238,7 +1256,7 @@ pa_status pa_ln_dos(pa_ctx* c, double* out, int64_t cap)
             out[k] = -INFINITY;
             continue;
         }
-        const double Ek = (double)(-c->h.eoff + 4ll * (long long)k);
+        const double Ek = (double)(-c->h.eoff + (long long)c->h.estep * (long long)k);
         double m = -INFINITY;
         for (size_t i = 0; i < nr; i++) {
             a[i] = lnR[i] + bF[i] - b[i] * Ek;
@@ -1288,13 +1306,13 @@ pa_status pa_mhr(pa_ctx* c, const double* betas, int64_t n, pa_obs* out)
         double m = -INFINITY;
         for (size_t k = 0; k < N1; k++) {
             if (!std::isfinite(lno[k])) continue;
-            const double Ek = (double)(-c->h.eoff + 4ll * (long long)k);
+            const double Ek = (double)(-c->h.eoff + (long long)c->h.estep * (long long)k);
             m = std::max(m, lno[k] - beta * Ek);
         }
         double Z = 0.0, e1 = 0.0, e2 = 0.0, a1 = 0.0, a2 = 0.0, a4 = 0.0;
         for (size_t k = 0; k < N1; k++) {
             if (!std::isfinite(lno[k])) continue;
-            const double Ek = (double)(-c->h.eoff + 4ll * (long long)k);
+            const double Ek = (double)(-c->h.eoff + (long long)c->h.estep * (long long)k);
             const double w = std::exp(lno[k] - beta * Ek - m);
             Z += w;
             e1 += w * Ek;

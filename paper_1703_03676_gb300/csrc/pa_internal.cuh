@@ -66,8 +66,10 @@ struct RunDev {
     int nsteps;               // last step of a fixed schedule (batched runs stop there)
     unsigned unit;            // always 1; a run-time multiplier for the accept-bit insert
     int dim;                  // 2: L x L square lattice; 3: L x L x L simple cubic (N = L^dim)
+    int potts_q;              // 0: Ising; 2..8: q-state Potts (byte states 0..q-1, square lattice)
+    int estep;                // energy between adjacent levels: 4 (Ising), 1 (Potts)
     int nlev;                 // energy levels k = (E + eoff)/4 = 0 .. dim N/2, and the length of each histogram
-    long long eoff;           // dim * N: E_k = 4 k - eoff
+    long long eoff;           // E_k = estep k - eoff (dim N for Ising, 2N for Potts)
     uint32_t* pop[2];
     int32_t* elev[2];
     int32_t* mlev[2];
@@ -87,6 +89,7 @@ struct RunDev {
     unsigned long long* U;
     uint32_t* thr;            // per step: T4 - 1, T8 - 1
     uint32_t* thr12;          // per step: T12 - 1 (simple cubic lattice only, else null)
+    uint32_t* thrp;           // per step: T1 - 1 .. T4 - 1 for dE = 1..4 (Potts only, else null)
     StepDev* rec;
     uint32_t* hist_rec;       // (steps) x 2 x (N+1) when record_hist
     int* status;
@@ -117,7 +120,7 @@ __device__ __forceinline__ uint4 philox10(uint4 c, PhiloxKey key)
 }
 
 // stream tags of the counter's fourth word
-constexpr unsigned kTagInit = 0u, kTagSweep = 1u, kTagResample = 2u;
+constexpr unsigned kTagInit = 0u, kTagSweep = 1u, kTagResample = 2u, kTagPotts = 6u;
 
 // ---------------------------------------------------------------- resampling
 // Arguments of the three resampling kernels (copy numbers, tile scan, parent

@@ -232,18 +232,17 @@ __device__ __forceinline__ void atomic_add_u128(unsigned long long* lohi, unsign
     if (hi) atomicAdd(&lohi[1], hi);
 }
 
-// Record a finished replica: levels, histograms, family, and the per-level
+// Record a finished replica from its energy level kl, magnetisation level
+// ml and magnetisation M: levels, histograms, family, and the per-level
 // magnetisation sums used to reweight magnetisations (Sec. 2.4).
-__device__ __forceinline__ void record_replica(const RunDev& r, int nxt, long long k, unsigned anti, unsigned ups,
-                                               uint32_t family)
+__device__ __forceinline__ void record_levels(const RunDev& r, int nxt, long long k, int kl, int ml, long long M,
+                                              uint32_t family)
 {
-    const int kl = (int)(anti >> 1);  // (E + dim N)/4 with E = 2*anti - dim N
     r.elev[nxt][k] = kl;
-    r.mlev[nxt][k] = (int)ups;        // (M + N)/2 = number of up spins
+    r.mlev[nxt][k] = ml;
     r.fam[nxt][k] = family;
     atomicAdd(&r.H[nxt][kl], 1u);
-    atomicAdd(&r.H[nxt][r.nlev + ups], 1u);
-    const long long M = 2ll * (long long)ups - r.N;
+    atomicAdd(&r.H[nxt][r.nlev + ml], 1u);
     const unsigned long long aM = (unsigned long long)(M < 0 ? -M : M);
     const unsigned long long M2 = aM * aM;
     const unsigned __int128 M4 = (unsigned __int128)M2 * M2;
@@ -251,6 +250,14 @@ __device__ __forceinline__ void record_replica(const RunDev& r, int nxt, long lo
     atomicAdd(&ms[0], aM);
     atomic_add_u128(ms + 1, M2, 0ull);
     atomic_add_u128(ms + 3, (unsigned long long)M4, (unsigned long long)(M4 >> 64));
+}
+
+// Ising spins: anti-parallel bonds and up spins give kl = (E + dim N)/4 with
+// E = 2*anti - dim N, ml = (M + N)/2 = ups and M = 2*ups - N.
+__device__ __forceinline__ void record_replica(const RunDev& r, int nxt, long long k, unsigned anti, unsigned ups,
+                                               uint32_t family)
+{
+    record_levels(r, nxt, k, (int)(anti >> 1), (int)ups, 2ll * (long long)ups - r.N, family);
 }
 
 template <int G>
@@ -685,6 +692,184 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
 }
 
 
+
+// ======================================================== q-state Potts
+// Byte states 0..q-1 in the byte layout (plane 0 then plane 1); the update
+// of the oracle's Potts mode: the POTTS block (2u + c, b>>1, 6, k) gives
+// the proposal word out[2(b&1)] and the acceptance word out[2(b&1) + 1].
+// Proposal s' = (s + 1 + floor(w0 (q-1) / 2^32)) mod q; with n(t) the
+// neighbours in state t, dE = n(s) - n(s'); accepted if dE <= 0, else iff
+// w1 <= T_dE - 1.
+__device__ __forceinline__ int potts_state(unsigned x, int q)
+{
+    return (int)(((unsigned long long)x * (unsigned long long)q) >> 32);
+}
+
+// satisfied bonds (each bond once: the four neighbours of every plane-0 site)
+// and the number of sites in each state
+template <int G>
+__device__ __forceinline__ void measure_potts(const uint8_t* sp, int L, int q, int gl, unsigned& eq,
+                                              unsigned cnt[8])
+{
+    const int N = L * L, half = L / 2, NP = N / 2;
+    const uint8_t* o = sp + NP;
+    eq = 0;
+#pragma unroll
+    for (int t = 0; t < 8; t++) cnt[t] = 0;
+    for (int b = gl; b < NP; b += G) {
+        const int s = sp[b];
+        const int y = b / half, h = b - y * half;
+        const int up = ((y == 0 ? L - 1 : y - 1)) * half + h;
+        const int dn = ((y == L - 1 ? 0 : y + 1)) * half + h;
+        eq += (unsigned)((o[b] == s) + (o[nb_index_side(b, 0, L, half)] == s) + (o[up] == s) + (o[dn] == s));
+#pragma unroll
+        for (int t = 0; t < 8; t++) cnt[t] += (unsigned)(s == t) + (unsigned)(o[b] == t);
+    }
+    (void)q;
+}
+
+// group totals of a Potts measurement, then the record (E + 2N = 2N - eq,
+// majority size)
+template <int G>
+__device__ __forceinline__ void record_potts(const RunDev& r, int nxt, long long k, bool active, int gl,
+                                             unsigned eq, unsigned cnt[8], uint32_t family)
+{
+    eq = group_sum<G>(eq);
+    unsigned mx = 0;
+#pragma unroll
+    for (int t = 0; t < 8; t++) {
+        const unsigned c = group_sum<G>(cnt[t]);
+        if (t < r.potts_q) mx = max(mx, c);
+    }
+    if (active && gl == 0) record_levels(r, nxt, k, 2 * r.N - (int)eq, (int)mx, (long long)mx, family);
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_init_potts(const __grid_constant__ RunDev r)
+{
+    constexpr int RPW = 32 / G;
+    extern __shared__ uint32_t smem[];
+    if (*r.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / G, gl = lane % G;
+    uint8_t* sp = reinterpret_cast<uint8_t*>(smem + (warp * RPW + g) * r.words);
+    const PhiloxKey key{r.key[0], r.key[1]};
+    const long long R0 = r.R;
+    const int N = r.N, q = r.potts_q;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= R0) break;
+        const long long k = (long long)base + g;
+        const bool active = k < R0;
+        if (active) {
+            for (int gq = gl; gq < (N + 3) / 4; gq += G) {
+                const uint4 x = philox10(make_uint4(0u, (unsigned)gq, kTagInit, (unsigned)k), key);
+                const unsigned xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+                for (int l = 0; l < 4; l++) {
+                    const int gi = 4 * gq + l;  // = c*N/2 + b
+                    if (gi < N) sp[gi] = (uint8_t)potts_state(xs[l], q);
+                }
+            }
+        }
+        __syncwarp();
+        unsigned eq = 0, cnt[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        if (active) measure_potts<G>(sp, r.L, q, gl, eq, cnt);
+        if (active) {
+            uint32_t* dst = r.pop[0] + (size_t)k * r.words;
+            const uint32_t* s32 = reinterpret_cast<const uint32_t*>(sp);
+            for (int i = gl; i < r.words; i += G) dst[i] = s32[i];
+        }
+        record_potts<G>(r, 0, k, active, gl, eq, cnt, (uint32_t)k);
+        __syncwarp();
+    }
+}
+
+template <int G>
+__global__ void __launch_bounds__(256) k_sweep_potts(const __grid_constant__ RunDev r, int step)
+{
+    constexpr int RPW = 32 / G;
+    extern __shared__ uint32_t smem[];
+    if (*r.status) return;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane / G, gl = lane % G;
+    uint8_t* sp = reinterpret_cast<uint8_t*>(smem + (warp * RPW + g) * r.words);
+    const int cur = (step - 1) & 1, nxt = step & 1;
+    const long long Ri = r.rec[step].R;
+    const uint32_t* T = r.thrp + 4 * step;
+    const uint32_t t1 = T[0], t2 = T[1], t3 = T[2], t4 = T[3];
+    const PhiloxKey key{r.key[0], r.key[1]};
+    const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
+    const int L = r.L, half = r.half, NP = r.N / 2, QP = NP / 2, q = r.potts_q;
+    unsigned families = 0;
+    for (;;) {
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (base >= Ri) break;
+        const long long k = (long long)base + g;
+        const bool active = k < Ri;
+        uint32_t p = 0;
+        if (active) {
+            p = r.parent[k];
+            const uint32_t* src = r.pop[cur] + (size_t)p * r.words;
+            uint32_t* s32 = reinterpret_cast<uint32_t*>(sp);
+            for (int i = gl; i < r.words; i += G) s32[i] = src[i];
+        }
+        __syncwarp();
+        for (int sw = 0; sw < r.theta; sw++) {
+            const unsigned u = u0 + (unsigned)sw;
+            for (int c = 0; c < 2; c++) {
+                if (active) {
+                    uint8_t* P = sp + c * NP;
+                    const uint8_t* O = sp + (1 - c) * NP;
+                    for (int pb = gl; pb < QP; pb += G) {
+                        const uint4 x =
+                            philox10(make_uint4(2u * u + (unsigned)c, (unsigned)pb, kTagPotts, (unsigned)k), key);
+#pragma unroll
+                        for (int l = 0; l < 2; l++) {
+                            const int b = 2 * pb + l;
+                            const unsigned w0 = l ? x.z : x.x, w1 = l ? x.w : x.y;
+                            const int s = P[b];
+                            int sn = s + 1 + potts_state(w0, q - 1);
+                            if (sn >= q) sn -= q;
+                            const int y = b / half, h = b - y * half;
+                            const int nb0 = O[b], nb1 = O[nb_index_side(b, c, L, half)];
+                            const int nb2 = O[(y == 0 ? L - 1 : y - 1) * half + h];
+                            const int nb3 = O[(y == L - 1 ? 0 : y + 1) * half + h];
+                            const int ns = (nb0 == s) + (nb1 == s) + (nb2 == s) + (nb3 == s);
+                            const int nn = (nb0 == sn) + (nb1 == sn) + (nb2 == sn) + (nb3 == sn);
+                            const int dE = ns - nn;
+                            bool acc = dE <= 0;
+                            if (dE == 1) acc = w1 <= t1;
+                            if (dE == 2) acc = w1 <= t2;
+                            if (dE == 3) acc = w1 <= t3;
+                            if (dE == 4) acc = w1 <= t4;
+                            if (acc) P[b] = (uint8_t)sn;
+                        }
+                    }
+                }
+                __syncwarp();
+            }
+        }
+        unsigned eq = 0, cnt[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+        if (active) measure_potts<G>(sp, L, q, gl, eq, cnt);
+        uint32_t f = 0;
+        if (active) {
+            uint32_t* dst = r.pop[nxt] + (size_t)k * r.words;
+            const uint32_t* s32 = reinterpret_cast<const uint32_t*>(sp);
+            for (int i = gl; i < r.words; i += G) dst[i] = s32[i];
+            f = r.fam[cur][p];
+            if (gl == 0) families += (k == 0 || r.fam[cur][r.parent[k - 1]] != f) ? 1u : 0u;
+        }
+        record_potts<G>(r, nxt, k, active, gl, eq, cnt, f);
+        __syncwarp();
+    }
+    families = group_sum<32>(families);
+    if (lane == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
+}
 
 // ======================================================== replica-parallel
 // The paper's generic fallback (Sec. 3 "Spin updates"): one thread per
@@ -1348,13 +1533,13 @@ __device__ __forceinline__ void stats_body(const RunDev& r, int step)
         if (h) {
             kmin = min(kmin, k);
             kmax = max(kmax, k);
-            const long long E = 4ll * k - r.eoff;
+            const long long E = (long long)r.estep * k - r.eoff;
             sE += (__int128)h * E;
             sE2 += (__int128)h * (E * E);
             r.Hsum[k] += h;
         }
         if (hm) {
-            const long long M = 2ll * k - N;
+            const long long M = r.potts_q ? (long long)k : 2ll * k - N;  // Potts: the majority state's size
             const long long aM = M < 0 ? -M : M;
             const long long M2 = M * M;
             sAM += (__int128)hm * aM;
@@ -1619,6 +1804,12 @@ const void* bytes_ptr(bool init)
     return init ? (const void*)k_init_bytes<G> : (const void*)k_sweep_bytes<G>;
 }
 
+template <int G>
+const void* potts_ptr(bool init)
+{
+    return init ? (const void*)k_init_potts<G> : (const void*)k_sweep_potts<G>;
+}
+
 }  // namespace
 
 // The init / sweep kernel of a run's (format, L, threads per replica).
@@ -1652,6 +1843,17 @@ const void* sweep_kernel(const RunDev& h, bool init)
         case 128: return bits_ptr_L<128>(h.gt, init);
         case 256: return bits_ptr_L<256>(h.gt, init);
         case 512: return bits_ptr_L<512>(h.gt, init);
+        default: return nullptr;
+        }
+    }
+    if (h.potts_q) {
+        switch (h.gt) {
+        case 1: return potts_ptr<1>(init);
+        case 2: return potts_ptr<2>(init);
+        case 4: return potts_ptr<4>(init);
+        case 8: return potts_ptr<8>(init);
+        case 16: return potts_ptr<16>(init);
+        case 32: return potts_ptr<32>(init);
         default: return nullptr;
         }
     }
