@@ -10,12 +10,15 @@ justifies the change:
 
 Fixtures:
   exact_dos.txt               exact g(E): 4 x 4 and 2 x 2 x 2 tori by
-                              enumeration, 6 x 6 by transfer matrix
+                              enumeration, 6 x 6 and the 3-state Potts
+                              4 x 4 torus by transfer matrix
   oracle_rows_config1.txt     config 1 (L = 16, R = 1000, theta = 10,
                               dbeta = 0.01 to beta = 1, seed 1): every row
                               and the final population's FNV-1a 64 hash
   oracle_rows_3d_L8.txt       simple cubic L = 8, R = 500, theta = 3,
                               dbeta = 0.1 to beta = 0.6, seed 51
+  oracle_rows_potts_q3_L16.txt  3-state Potts, L = 16, R = 500, theta = 5,
+                              dbeta = 0.1 to beta = 1.2, seed 61
 """
 from __future__ import annotations
 
@@ -25,7 +28,7 @@ import sys
 HERE = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, os.path.dirname(os.path.dirname(HERE)))
 
-from oracle.exact_ising import BruteForce, transfer_matrix_dos  # noqa: E402
+from oracle.exact_ising import BruteForce, potts_transfer_dos, transfer_matrix_dos  # noqa: E402
 from oracle.pa_oracle import PopulationAnnealing  # noqa: E402
 
 ROW_FIELDS = ["beta", "e", "C", "abs_m", "m2", "m4", "betaF_per_N", "S_per_N", "lnQ", "R", "families"]
@@ -33,11 +36,13 @@ ROW_FIELDS = ["beta", "e", "C", "abs_m", "m2", "m4", "betaF_per_N", "S_per_N", "
 RUNS = {
     "oracle_rows_config1.txt": dict(L=16, R=1000, theta=10, beta_f=1.0, dbeta=0.01, seed=1, dim=2),
     "oracle_rows_3d_L8.txt": dict(L=8, R=500, theta=3, beta_f=0.6, dbeta=0.1, seed=51, dim=3),
+    "oracle_rows_potts_q3_L16.txt": dict(L=16, R=500, theta=5, beta_f=1.2, dbeta=0.1, seed=61, dim=2, potts_q=3),
 }
 
 
 def fnv1a64(spins) -> int:
-    """64-bit FNV-1a over int8 +1/-1 spins, one byte each, in natural layout."""
+    """64-bit FNV-1a over int8 spins (+1/-1, or Potts states), one byte each,
+    in natural layout."""
     h = 0xCBF29CE484222325
     for v in spins.astype("int8").ravel().view("uint8").tolist():
         h ^= v
@@ -47,7 +52,7 @@ def fnv1a64(spins) -> int:
 
 def run_rows(p):
     pa = PopulationAnnealing(p["L"], p["R"], p["theta"], beta_f=p["beta_f"], dbeta=p["dbeta"], seed=p["seed"],
-                             dim=p["dim"])
+                             dim=p["dim"], potts_q=p.get("potts_q", 0))
     pa.run()
     return pa.rows, fnv1a64(pa.pop)
 
@@ -67,7 +72,8 @@ def write_rows(name, p):
 def write_dos():
     tables = [("square L=4 (enumeration)", BruteForce(4).energy_dos()),
               ("square L=6 (transfer matrix)", transfer_matrix_dos(6)),
-              ("cubic L=2 (enumeration)", BruteForce(2, dim=3).energy_dos())]
+              ("cubic L=2 (enumeration)", BruteForce(2, dim=3).energy_dos()),
+              ("potts q=3 L=4 (transfer matrix)", potts_transfer_dos(4, 3))]
     with open(os.path.join(HERE, "exact_dos.txt"), "w") as f:
         f.write("# written by tests/golden/make_golden.py from oracle.exact_ising\n")
         f.write("# lattice, then lines: E g(E)\n")

@@ -9,7 +9,7 @@ import numpy as np
 import pytest
 
 from oracle import core
-from oracle.exact_ising import BETA_C, BruteForce, transfer_matrix_dos
+from oracle.exact_ising import BETA_C, BruteForce, potts_transfer_dos, transfer_matrix_dos
 from oracle.pa_oracle import PopulationAnnealing, philox4x32_10
 from tests.golden.make_golden import RUNS, ROW_FIELDS, fnv1a64, read_dos, read_paper_values, read_rows
 
@@ -53,6 +53,7 @@ def test_exact_dos_fixture_reproduced():
     assert dos["square L=4 (enumeration)"] == BruteForce(4).energy_dos()
     assert dos["square L=6 (transfer matrix)"] == transfer_matrix_dos(6)
     assert dos["cubic L=2 (enumeration)"] == BruteForce(2, dim=3).energy_dos()
+    assert dos["potts q=3 L=4 (transfer matrix)"] == potts_transfer_dos(4, 3)
     assert sum(dos["square L=6 (transfer matrix)"].values()) == 2 ** 36
 
 
@@ -62,7 +63,7 @@ def test_oracle_rows_fixture_reproduced(name):
     p = RUNS[name]
     assert {k: params[k] for k in p} == p
     pa = PopulationAnnealing(p["L"], p["R"], p["theta"], beta_f=p["beta_f"], dbeta=p["dbeta"], seed=p["seed"],
-                             dim=p["dim"])
+                             dim=p["dim"], potts_q=p.get("potts_q", 0))
     pa.run()
     assert len(pa.rows) == len(rows)
     for got, ref in zip(pa.rows, rows):
