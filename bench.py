@@ -40,13 +40,15 @@ if ROOT not in sys.path:
 
 METRIC = "spin-flip attempts/ns (batched vs single-run, bit-exact); p50/p99 run latency"
 UNIT = "flips/ns"
-WL = dict(L=64, R=20000, theta=100, beta_f=1.0, dbeta=0.005, dim=2)
+WL = dict(L=64, R=20000, theta=100, beta_f=1.0, dbeta=0.005, dim=2, potts_q=0)
 DEFAULT_WL = dict(WL)
 
 
 def workload_label():
     lattice = (f"2D Ising L={WL['L']} periodic" if WL["dim"] == 2 else
                f"3D Ising (simple cubic) L={WL['L']}^3 periodic")
+    if WL["potts_q"]:
+        lattice = f"2D {WL['potts_q']}-state Potts L={WL['L']} periodic"
     if WL["dbeta"] > 0:
         n = int(round(WL["beta_f"] / WL["dbeta"]))
         steps = f"dbeta={WL['dbeta']:g} ({n} steps)"
@@ -158,7 +160,7 @@ def _oracle_sample(args):
     from oracle.pa_oracle import PopulationAnnealing
     t0 = time.perf_counter()
     pa = PopulationAnnealing(wl["L"], R_s, wl["theta"], beta_f=wl["beta_f"], dbeta=wl["dbeta"], seed=seed,
-                             dim=wl["dim"])
+                             dim=wl["dim"], potts_q=wl["potts_q"])
     att = 0
     for _ in range(n_steps):
         rec = pa.step()
@@ -269,7 +271,7 @@ def run_engine(args):
     fmt = {"bits": eng.SPIN_BITS32, "msc": eng.SPIN_MSC32, "int8": eng.SPIN_INT8,
            "replica": eng.SPIN_REPLICA8}[args.format]
     cfg = eng.PAConfig(L=L, R=WL["R"], theta=theta, beta_f=WL["beta_f"], dbeta=WL["dbeta"], seed=seed_of(0),
-                       spin_format=fmt, use_graph=True, profile=args.profile, dim=WL["dim"],
+                       spin_format=fmt, use_graph=True, profile=args.profile, dim=WL["dim"], potts_q=WL["potts_q"],
                        group_threads=args.group_threads or 0)
     run = eng.PARun(cfg, stream=stream)
     adaptive = not (WL["dbeta"] > 0)  # steps chosen by histogram overlap, one host decision per step
@@ -368,15 +370,18 @@ def run_engine(args):
         for k in range(max(1, args.e2e_steps)):
             t0 = time.perf_counter()
             r2 = eng.PARun(eng.PAConfig(L=L, R=WL["R"], theta=theta, beta_f=WL["beta_f"], dbeta=WL["dbeta"],
-                                        seed=seed_of(50_000 + k), spin_format=fmt, dim=WL["dim"]), stream=stream)
+                                        seed=seed_of(50_000 + k), spin_format=fmt, dim=WL["dim"],
+                                        potts_q=WL["potts_q"]), stream=stream)
             r2.run()
             rows = r2.rows()
             r2.close()
             wall += time.perf_counter() - t0
             att_e2e += sites() * theta * int(rows["R"][1:].sum())
             # host tables uploaded by pa_create (thresholds, level weights, key)
-            thr_words = 3 if WL["dim"] == 3 else 2  # T4-1, T8-1 (and T12-1) per step
-            h2d = thr_words * (n_steps + 1) * 4 + (WL["dim"] * sites() // 2 + 1) * 8 + 8
+            # per step T4-1, T8-1 (and T12-1 in 3D, T1-1..T4-1 for Potts); level weights per level
+            thr_words = 3 if WL["dim"] == 3 else (6 if WL["potts_q"] else 2)
+            nlev = (2 * sites() if WL["potts_q"] else WL["dim"] * sites() // 2) + 1
+            h2d = thr_words * (n_steps + 1) * 4 + nlev * 8 + 8
             d2h = (n_steps + 1) * 128 + 4 + rows.nbytes
         wmax = max_over_ranks(wall, dist)
         e2e = {"value": sum_over_ranks(att_e2e, dist) / (wmax * 1e9), "unit": UNIT,
@@ -527,6 +532,8 @@ def main():
     ap.add_argument("--dbeta", type=float, default=None, help="override the default workload's step size")
     ap.add_argument("--dim", type=int, choices=[2, 3], default=None,
                     help="3: the simple cubic L x L x L lattice instead of the square one")
+    ap.add_argument("--potts-q", type=int, default=None,
+                    help="2..8: the q-state Potts model (byte states, --format int8)")
     ap.add_argument("--group-threads", type=int, default=None,
                     help="threads per replica of the bit-packed sweep (default: chosen by the engine)")
     ap.add_argument("--c4-steps", type=int, default=200)
@@ -544,7 +551,9 @@ def main():
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
-    for k in ("L", "R", "theta", "dbeta", "dim"):  # labelled variants of the default workload
+    if args.potts_q and args.format != "int8":
+        ap.error("--potts-q needs --format int8")
+    for k in ("L", "R", "theta", "dbeta", "dim", "potts_q"):  # labelled variants of the default workload
         if getattr(args, k) is not None:
             WL[k] = getattr(args, k)
     if args.impl == "reference":
