@@ -534,6 +534,28 @@ __device__ __forceinline__ int nb_index_side(int b, int c, int L, int half)
     return y * half + h2;
 }
 
+// Row y = b / half of in-plane index b without a division: with
+// m = ceil(2^32 / half), floor(b m / 2^32) = floor(b / half) exactly for
+// half <= 512 and b < 2^22 (the rounding excess b (m half - 2^32) / 2^32
+// stays below 1/half).
+__device__ __forceinline__ unsigned row_magic(int half)
+{
+    return (unsigned)(((1ull << 32) + (unsigned long long)half - 1ull) / (unsigned long long)half);
+}
+
+// the four neighbours (same index, side, up, down) in the other plane O of
+// site b of plane c, with y = b / half given by the reciprocal m
+__device__ __forceinline__ void byte_neighbours(const uint8_t* __restrict__ O, int b, int c, int L, int half,
+                                                unsigned m, int& n0, int& n1, int& n2, int& n3)
+{
+    const int y = (int)__umulhi((unsigned)b, m), h = b - y * half;
+    const int h2 = ((c + y) & 1) ? (h + 1 == half ? 0 : h + 1) : (h == 0 ? half - 1 : h - 1);
+    n0 = O[b];
+    n1 = O[y * half + h2];
+    n2 = O[(y == 0 ? L - 1 : y - 1) * half + h];
+    n3 = O[(y == L - 1 ? 0 : y + 1) * half + h];
+}
+
 // bond byte (1: J < 0) of direction dir for site b of plane c, or 0
 __device__ __forceinline__ int bond8(const uint8_t* __restrict__ bonds8, int dir, int c, int NP, int b)
 {
@@ -621,6 +643,7 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
     const PhiloxKey key{r.key[0], r.key[1]};
     const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
     const int L = r.L, half = r.half, NP = r.N / 2, QP = (NP + 3) / 4;
+    const unsigned hm = row_magic(half);
     unsigned families = 0;
     for (;;) {
         unsigned base = 0;
@@ -641,8 +664,10 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
             const unsigned u = u0 + (unsigned)sw;
             for (int c = 0; c < 2; c++) {
                 if (active) {
-                    uint8_t* P = sp + c * NP;
-                    const uint8_t* O = sp + (1 - c) * NP;
+                    uint8_t* __restrict__ P = sp + c * NP;
+                    const uint8_t* __restrict__ O = sp + (1 - c) * NP;
+                    // independent Philox blocks: unrolled so that their chains overlap
+#pragma unroll 4
                     for (int q = gl; q < QP; q += G) {
                         const uint4 x = philox10(make_uint4(2u * u + (unsigned)c, (unsigned)q, kTagSweep, (unsigned)k),
                                                  key);
@@ -652,14 +677,13 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
                             const int b = 4 * q + l;
                             if (b < NP) {
                                 const int s = P[b];
-                                const int y = b / half, h = b - y * half;
-                                const int up = (y == 0 ? L - 1 : y - 1) * half + h;
-                                const int dn = (y == L - 1 ? 0 : y + 1) * half + h;
+                                int nb0, nb1, nb2, nb3;
+                                byte_neighbours(O, b, c, L, half, hm, nb0, nb1, nb2, nb3);
                                 const uint8_t* B8 = r.bonds8;
-                                const int n = ((O[b] ^ bond8(B8, 0, c, NP, b)) == s) +
-                                              ((O[nb_index_side(b, c, L, half)] ^ bond8(B8, 1, c, NP, b)) == s) +
-                                              ((O[up] ^ bond8(B8, 2, c, NP, b)) == s) +
-                                              ((O[dn] ^ bond8(B8, 3, c, NP, b)) == s);
+                                const int n = ((nb0 ^ bond8(B8, 0, c, NP, b)) == s) +
+                                              ((nb1 ^ bond8(B8, 1, c, NP, b)) == s) +
+                                              ((nb2 ^ bond8(B8, 2, c, NP, b)) == s) +
+                                              ((nb3 ^ bond8(B8, 3, c, NP, b)) == s);
                                 bool flip = n <= 2;
                                 if (n == 3) flip = xs[l] <= t4m1;
                                 if (n == 4) flip = xs[l] <= t8m1;
@@ -803,6 +827,7 @@ __global__ void __launch_bounds__(256) k_sweep_potts(const __grid_constant__ Run
     const PhiloxKey key{r.key[0], r.key[1]};
     const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
     const int L = r.L, half = r.half, NP = r.N / 2, QP = NP / 2, q = r.potts_q;
+    const unsigned hm = row_magic(half);
     unsigned families = 0;
     for (;;) {
         unsigned base = 0;
@@ -823,8 +848,10 @@ __global__ void __launch_bounds__(256) k_sweep_potts(const __grid_constant__ Run
             const unsigned u = u0 + (unsigned)sw;
             for (int c = 0; c < 2; c++) {
                 if (active) {
-                    uint8_t* P = sp + c * NP;
-                    const uint8_t* O = sp + (1 - c) * NP;
+                    uint8_t* __restrict__ P = sp + c * NP;
+                    const uint8_t* __restrict__ O = sp + (1 - c) * NP;
+                    // independent Philox blocks: unrolled so that their chains overlap
+#pragma unroll 4
                     for (int pb = gl; pb < QP; pb += G) {
                         const uint4 x =
                             philox10(make_uint4(2u * u + (unsigned)c, (unsigned)pb, kTagPotts, (unsigned)k), key);
@@ -835,10 +862,8 @@ __global__ void __launch_bounds__(256) k_sweep_potts(const __grid_constant__ Run
                             const int s = P[b];
                             int sn = s + 1 + potts_state(w0, q - 1);
                             if (sn >= q) sn -= q;
-                            const int y = b / half, h = b - y * half;
-                            const int nb0 = O[b], nb1 = O[nb_index_side(b, c, L, half)];
-                            const int nb2 = O[(y == 0 ? L - 1 : y - 1) * half + h];
-                            const int nb3 = O[(y == L - 1 ? 0 : y + 1) * half + h];
+                            int nb0, nb1, nb2, nb3;
+                            byte_neighbours(O, b, c, L, half, hm, nb0, nb1, nb2, nb3);
                             const int ns = (nb0 == s) + (nb1 == s) + (nb2 == s) + (nb3 == s);
                             const int nn = (nb0 == sn) + (nb1 == sn) + (nb2 == sn) + (nb3 == sn);
                             const int dE = ns - nn;
