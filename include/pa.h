@@ -1,7 +1,10 @@
 /*
  * pa.h -- C ABI of the GB300 population-annealing engine for the 2D
  * ferromagnetic Ising model (Barash, Weigel, Borovsky, Janke, Shchur,
- * "GPU accelerated population annealing algorithm", arXiv:1703.03676).
+ * "GPU accelerated population annealing algorithm", arXiv:1703.03676), with
+ * the further models the paper's conclusion points to: the +-J spin glass
+ * (pa_create_couplings), the simple cubic lattice (pa_config.dim = 3) and
+ * the q-state Potts model (pa_config.potts_q).
  *
  * One pa_ctx is one PA run (Sec. 2.1): R replicas of a periodic L x L Ising
  * lattice (Eq. hamiltonian, J = 1) start from random spins at beta0 = 0 and
@@ -51,7 +54,8 @@ typedef enum {
 
 /* PA_SPIN_INT8: one byte per spin. PA_SPIN_BITS32: 32 same-colour sites of
  * one replica per word (synchronous multi-spin coding). Both draw one
- * Philox4x32-10 word per attempt and give identical results.
+ * Philox4x32-10 word per attempt and give identical results (the Potts
+ * model uses PA_SPIN_INT8 with states 0..q-1 and two words per attempt).
  * PA_SPIN_MSC32: the paper's asynchronous multi-spin coding (Sec. 4): bit j
  * of a site's word is replica 32g + j, and the 32 replicas' random numbers
  * come from the linear congruential generator r <- 1664525 r + 1013904223
