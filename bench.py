@@ -426,10 +426,19 @@ def run_batched(args):
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    draw = eng.batch_config4_draw(64)
-    n_steps = args.c4_steps
-    bf = n_steps * 0.005
-    cfgs = [eng.PAConfig(L=L, R=R, theta=th, beta_f=bf, dbeta=0.005, seed=100 + i) for i, (L, R, th) in enumerate(draw)]
+    if args.batch_set == "config1":
+        # 64 small runs of the config-1 shape (L = 16, R = 1000, theta = 10, 100 steps), bit-packed:
+        # each alone is latency-bound, so this is where batching pays
+        n_steps, bf = 100, 1.0
+        cfgs = [eng.PAConfig(L=16, R=1000, theta=10, beta_f=1.0, dbeta=0.01, seed=100 + i) for i in range(64)]
+        desc = "64 runs of the config-1 shape (L=16, R=1000, theta=10, dbeta 0.01, 100 steps)"
+    else:
+        draw = eng.batch_config4_draw(64)
+        n_steps = args.c4_steps
+        bf = n_steps * 0.005
+        cfgs = [eng.PAConfig(L=L, R=R, theta=th, beta_f=bf, dbeta=0.005, seed=100 + i)
+                for i, (L, R, th) in enumerate(draw)]
+        desc = f"64 runs, L/R/theta from Philox tag 3 seed 99, dbeta 0.005, {n_steps} steps (beta 0->{bf:g})"
     att_of = lambda rows, c: c.L * c.L * c.theta * int(rows["R"][1:].sum())  # noqa: E731
     b = eng.PABatch(cfgs, stream=stream)
     times = []
@@ -467,8 +476,7 @@ def run_batched(args):
     line = {"metric": METRIC, "workload": "batched", "value": v_batched, "unit": UNIT, "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(times) / len(times),
             "higher_is_better": True, "single_run_value": v_alone, "batched_over_single": v_batched / v_alone,
-            "config": {"workload": f"64 runs, L/R/theta from Philox tag 3 seed 99, dbeta 0.005, {n_steps} steps "
-                                   f"(beta 0->{bf:g}), seeds 100..163 (+1000 per bench step), bit-packed",
+            "config": {"workload": f"{desc}, seeds 100..163 (+1000 per bench step), bit-packed",
                        "attempts_per_step": att_b / len(times), "group_threads_by_L": shapes},
             "data": "synthetic"}
     print(json.dumps(line), flush=True)
@@ -537,6 +545,8 @@ def main():
     ap.add_argument("--group-threads", type=int, default=None,
                     help="threads per replica of the bit-packed sweep (default: chosen by the engine)")
     ap.add_argument("--c4-steps", type=int, default=200)
+    ap.add_argument("--batch-set", choices=["config4", "config1"], default="config4",
+                    help="runs of --workload batched: the config-4 draw, or 64 runs of the config-1 shape")
     ap.add_argument("--serve-n", type=int, default=48)
     ap.add_argument("--serve-rdiv", type=int, default=50)
     ap.add_argument("--serve-beta-f", type=float, default=0.5)
