@@ -244,7 +244,7 @@ def run_reference(args):
         tot_wall += wall
     v = tot_att / tot_wall / 1e9
     sample = (f"each step: {workers} independent oracle processes, each the first temperature step of the workload "
-              f"with R={R_s} (not R=20000)")
+              f"with R={R_s} (not R={WL['R']})")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
