@@ -184,7 +184,7 @@ def cpu_baseline_obj(workers, R_s, n_steps):
     v, att, wall = cpu_oracle(workers, R_s, n_steps, 9000)
     return {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
             "sample": f"{workers} independent oracle processes, each the first {n_steps} temperature step(s) of the "
-                      f"workload with R={R_s} (not R=20000): {att:.3e} attempts in {wall:.1f} s wall"}
+                      f"workload with R={R_s} (not R={WL['R']}): {att:.3e} attempts in {wall:.1f} s wall"}
 
 
 # ------------------------------------------------------------------ helpers
