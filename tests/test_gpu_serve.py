@@ -96,3 +96,25 @@ def test_trace_draw_matches_oracle_philox():
     for q in range(12):
         t += -math.log(1.0 - float(w[q, 0]) / 4294967296.0) / 20.0
         assert got[q] == (t, [32, 64, 128, 256, 512][int(w[q, 1]) % 5], 10000 + int(w[q, 2]) % 90001, 1000 + q)
+
+
+def test_served_other_models_equal_alone():
+    """Requests of the further models (simple cubic, q-state Potts, adaptive
+    and fixed) served together with Ising ones: each equals its run alone."""
+    cfgs = [
+        eng.PAConfig(L=16, R=600, theta=3, beta_f=0.3, dbeta=0.0, seed=1101, spin_format=B32, dim=3),
+        eng.PAConfig(L=16, R=900, theta=3, beta_f=0.8, dbeta=0.1, seed=1102, spin_format=I8, potts_q=3),
+        eng.PAConfig(L=32, R=700, theta=3, beta_f=0.4, dbeta=0.0, seed=1103, spin_format=B32),
+        eng.PAConfig(L=8, R=500, theta=2, beta_f=0.6, dbeta=0.0, seed=1104, spin_format=I8, potts_q=5),
+        eng.PAConfig(L=32, R=200, theta=2, beta_f=0.3, dbeta=0.1, seed=1105, spin_format=B32, dim=3),
+    ]
+    reqs = [(0.001 * q, c) for q, c in enumerate(cfgs)]
+    res, runs = eng.serve(reqs, hbm_budget=1 << 34, max_active=3, keep=True)
+    assert all(r["status"] == 0 for r in res), res
+    for (_, c), r in zip(reqs, runs):
+        alone = eng.PARun(eng.PAConfig(**c.__dict__))
+        alone.run()
+        np.testing.assert_array_equal(r.rows(), alone.rows())
+        np.testing.assert_array_equal(r.population(), alone.population())
+        alone.close()
+        r.close()
