@@ -293,7 +293,7 @@ const char *pa_strerror(pa_status s);
 const char *pa_last_error_message(void);
 
 /* ---- batches of independent runs ---------------------------------------
- * Many independent fixed-schedule runs (spec batching; Sec. 2.2 notes
+ * Many independent fixed-schedule runs (batched runs; Sec. 2.2 notes
  * that independent runs combine by free-energy weights) stepped together:
  * every phase of a temperature step is one launch for all runs. The sweep
  * is two persistent kernels over one queue of work items: one replica per
@@ -334,7 +334,7 @@ pa_status pa_batch_shape(pa_batch *b, int32_t i, int32_t *group_threads, int32_t
 void pa_batch_destroy(pa_batch *b);
 
 /* ---- serving ------------------------------------------------------------
- * A request loop with continuous batching (spec serving): requests
+ * A request loop with continuous batching (serving): requests
  * arrive at given times; each is admitted, in arrival order, once it has
  * arrived, fewer than max_active runs are resident and the sum of the
  * resident runs' pa_footprint_bytes stays within hbm_budget (a request

@@ -1556,7 +1556,7 @@ pa_status pa_measure_pipe_peak(int pipe, int64_t iters, uint32_t* sink, void* st
 }  // extern "C"
 
 // ================================================================== batches
-// Independent fixed-schedule runs stepped together (spec batching):
+// Independent fixed-schedule runs stepped together (batched runs):
 // each phase of a temperature step is one launch over all runs, and the
 // sweep is one persistent kernel whose warps pull (run, replica batch)
 // items from a single queue ordered by descending work per replica. The
