@@ -10,14 +10,20 @@ bit-packed spins, a new seed every step (seed = 2 + step). Inputs are
 synthetic (random initial spins generated on the device).
 
   value   device time (CUDA events on the run's stream) of pa_reset +
-          pa_launch, i.e. init, 200 temperature steps as one CUDA graph;
+          pa_launch, i.e. init, 200 temperature steps as one CUDA graph
+          (no profiling events inside the graph);
   e2e     wall clock of the public API a user calls: pa_create (allocation,
           host tables uploaded), pa_run, pa_observables (rows read back),
           pa_destroy;
   roofline  the sweep kernel's average launch time from CUDA events captured
-          in the same graph, against the integer-pipe peak of the device;
-  cpu_baseline  the CPU oracle on a bounded sample of the same workload on
-          all host cores (independent processes).
+          in the graph of a separate profiled pass of the same workload,
+          against the wide-multiply issue peak of the device;
+  batched / served  the batched and served forms of the same engine on
+          labelled prefixes of the batched and served workloads, each beside
+          the same runs one at a time (single GPU only);
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload (whole
+          anneals of a few replicas) on all host cores (independent
+          processes).
 
 --impl reference times that oracle alone on the same metric and workload.
 """
@@ -78,7 +84,8 @@ PAPER_K80_MSC_FLIPS_PER_NS = 4096 * 100 * 200 * 20000 / 17.0 / 1e9
 # A wide multiply occupies the FMA-heavy pipe for 4 cycles per warp (32 lanes
 # per SM per clock, measured: the Philox-only kernel reaches 84% of it); LOP3
 # and compares go to the ALU pipe (64 lanes per SM per clock).
-MUL_OPS_PER_ATTEMPT = 4.0
+MUL_OPS_PER_ATTEMPT = 4.0       # issued by the kernel (lane-varying products)
+MUL_OPS_ALGORITHMIC = 5.0       # a quarter of Philox4x32-10's 20 wide products
 ALU_OPS_PER_ATTEMPT = 4.5 + 1.0 + 0.5
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_bits_L64_R20000_theta100.md")
 
@@ -152,9 +159,10 @@ def clocks_sampler_stop(h, path, gpu_index):
 
 # ------------------------------------------------------------------ CPU oracle
 def _oracle_sample(args):
-    """One worker: the oracle on R_s replicas of the workload `wl` for n_steps
-    temperature steps; returns (attempts, seconds). (Workers are spawned, so
-    the workload comes in the arguments, not from this module's globals.)"""
+    """One worker: the oracle on R_s replicas of the workload `wl`, for
+    n_steps temperature steps (None: the whole anneal to beta_f); returns
+    (attempts, seconds). (Workers are spawned, so the workload comes in the
+    arguments, not from this module's globals.)"""
     R_s, n_steps, seed, wl = args
     sys.path.insert(0, ROOT)
     from oracle.pa_oracle import PopulationAnnealing
@@ -162,13 +170,15 @@ def _oracle_sample(args):
     pa = PopulationAnnealing(wl["L"], R_s, wl["theta"], beta_f=wl["beta_f"], dbeta=wl["dbeta"], seed=seed,
                              dim=wl["dim"], potts_q=wl["potts_q"])
     att = 0
-    for _ in range(n_steps):
+    k = 0
+    while not pa.done and (n_steps is None or k < n_steps):
         rec = pa.step()
         att += wl["L"] ** wl["dim"] * wl["theta"] * rec.R
+        k += 1
     return att, time.perf_counter() - t0
 
 
-def cpu_oracle(workers: int, R_s: int, n_steps: int, seed0: int):
+def cpu_oracle(workers: int, R_s: int, n_steps, seed0: int):
     ctx = mp.get_context("spawn")
     import oracle
     oracle.build()
@@ -180,11 +190,16 @@ def cpu_oracle(workers: int, R_s: int, n_steps: int, seed0: int):
     return att / wall / 1e9, att, wall
 
 
-def cpu_baseline_obj(workers, R_s, n_steps):
-    v, att, wall = cpu_oracle(workers, R_s, n_steps, 9000)
+def anneal_label():
+    return "the whole anneal (every temperature step to beta_f)" if WL["dbeta"] > 0 else \
+        "the whole adaptive anneal to beta_f"
+
+
+def cpu_baseline_obj(workers, R_s):
+    v, att, wall = cpu_oracle(workers, R_s, None, 9000)
     return {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
-            "sample": f"{workers} independent oracle processes, each the first {n_steps} temperature step(s) of the "
-                      f"workload with R={R_s} (not R={WL['R']}): {att:.3e} attempts in {wall:.1f} s wall"}
+            "sample": f"{workers} independent oracle processes, each {anneal_label()} of the workload with "
+                      f"R={R_s} (not R={WL['R']}): {att:.3e} attempts in {wall:.1f} s wall"}
 
 
 # ------------------------------------------------------------------ helpers
@@ -236,14 +251,14 @@ def run_reference(args):
     workers = os.cpu_count() or 1
     R_s = args.ref_replicas
     for _ in range(args.warmup):
-        cpu_oracle(workers, max(8, R_s // 4), 1, 500)
+        cpu_oracle(workers, 1, 10, 500)  # untimed: spawn, build and page in
     tot_att, tot_wall = 0, 0.0
     for k in range(args.steps):
-        _, att, wall = cpu_oracle(workers, R_s, 1, 1000 + 100 * k)
+        _, att, wall = cpu_oracle(workers, R_s, None, 1000 + 100 * k)
         tot_att += att
         tot_wall += wall
     v = tot_att / tot_wall / 1e9
-    sample = (f"each step: {workers} independent oracle processes, each the first temperature step of the workload "
+    sample = (f"each step: {workers} independent oracle processes, each {anneal_label()} of the workload "
               f"with R={R_s} (not R={WL['R']})")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_wall / args.steps,
@@ -256,6 +271,78 @@ def run_reference(args):
 
 
 # ------------------------------------------------------------------ engine arm
+def sweep_roofline(eng, cfg, stream, dev, runs, clocks, seed0):
+    """The sweep kernel against its binding pipe, from a separate profiled
+    pass (runs complete runs with CUDA events around every launch, recorded
+    on the engine's stream inside the graph)."""
+    import dataclasses
+
+    import torch
+    pcfg = dataclasses.replace(cfg, profile=True)
+    run = eng.PARun(pcfg, stream=stream)
+    run.reset(seed0)
+    run.launch()
+    run.sync()
+    base = run.phase_times()
+    attempts, dev_ms = 0, 0.0
+    for k in range(runs):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        run.reset(seed0 + 1 + k)
+        run.launch()
+        e1.record(stream)
+        run.sync()
+        dev_ms += e0.elapsed_time(e1)
+        attempts += sites() * WL["theta"] * int(run.rows()["R"][1:].sum())
+    pt = run.phase_times()
+    shape = run.launch_shape()
+    run.close()
+    sw_ms = pt["sweep"][0] - base["sweep"][0]
+    sw_n = pt["sweep"][1] - base["sweep"][1]
+    avg_ms = sw_ms / max(sw_n, 1)
+    att_per_launch = attempts / max(sw_n, 1)
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk_max = clocks.get("sm_max_mhz") or 2070.0
+    apn = att_per_launch / (avg_ms * 1e6)  # attempts per ns in the sweep kernel
+    mul_peak = sm * 32 * clk_max * 1e6 / 1e9  # Gop/s, wide multiplies (FMA-heavy pipe)
+    alu_peak = sm * 64 * clk_max * 1e6 / 1e9  # Gop/s, ALU pipe
+    achieved = MUL_OPS_ALGORITHMIC * apn
+    gt = shape["group_threads"]
+    roof = {"bound": "fma_heavy", "achieved": achieved, "peak": mul_peak, "unit": "Gop/s",
+            "frac": achieved / mul_peak,
+            "traffic": profiled_traffic() if WL == DEFAULT_WL else None,
+            "kernel": f"k_sweep_bits<{WL['L']},{gt}" + (",3>" if WL["dim"] == 3 else ">"), "launch": shape,
+            "ops": "wide 32x32->64 multiplies of Philox4x32-10, 5 per attempt (a quarter of a block's 20)",
+            "peak_note": "FMA-heavy (integer wide-multiply) pipe: SMs x 32 lanes/clk x max SM clock (derived, "
+                         "of measured max clock)",
+            "issued": {"ops_per_attempt": MUL_OPS_PER_ATTEMPT, "achieved": MUL_OPS_PER_ATTEMPT * apn,
+                       "frac": MUL_OPS_PER_ATTEMPT * apn / mul_peak,
+                       "note": "the kernel issues 4 lane-varying products per attempt: the two first-round "
+                               "products are warp-uniform under its counter layout"},
+            "alu_pipe": {"achieved": ALU_OPS_PER_ATTEMPT * apn, "peak": alu_peak,
+                         "frac": ALU_OPS_PER_ATTEMPT * apn / alu_peak,
+                         "ops": "4.5 Philox XOR + 1 compare + 0.5 logic per attempt"},
+            "attempts_per_ns": apn, "launch_ms": avg_ms, "launches": sw_n,
+            "share_of_step": sw_ms / dev_ms if dev_ms else None,
+            "timing": f"separate profiled pass: {runs} complete runs, CUDA events around every launch",
+            "algorithmic_bytes_per_launch": 2 * att_per_launch / (sites() * WL["theta"]) * (sites() / 8)}
+    try:
+        roof["rng_ceiling_words_per_ns"] = eng.measure_rng_peak(2048, stream)
+    except Exception as e:  # measurement only
+        roof["rng_ceiling_words_per_ns"] = f"unavailable: {e}"
+    try:
+        # measured issue rates of the instruction classes behind the derived peaks
+        mp_ = {"wide_mul": eng.measure_pipe_peak(eng.PIPE_WIDE_MUL, 16384, stream),
+               "lop3": eng.measure_pipe_peak(eng.PIPE_LOP3, 16384, stream),
+               "imad": eng.measure_pipe_peak(eng.PIPE_IMAD, 16384, stream)}
+        roof["measured_pipe_peaks_gops"] = mp_
+        roof["frac_of_measured_wide_mul"] = achieved / mp_["wide_mul"]
+        roof["alu_pipe"]["frac_of_measured_lop3"] = ALU_OPS_PER_ATTEMPT * apn / mp_["lop3"]
+    except Exception as e:  # measurement only
+        roof["measured_pipe_peaks_gops"] = f"unavailable: {e}"
+    return roof
+
+
 def run_engine(args):
     import torch
 
@@ -271,7 +358,7 @@ def run_engine(args):
     fmt = {"bits": eng.SPIN_BITS32, "msc": eng.SPIN_MSC32, "int8": eng.SPIN_INT8,
            "replica": eng.SPIN_REPLICA8}[args.format]
     cfg = eng.PAConfig(L=L, R=WL["R"], theta=theta, beta_f=WL["beta_f"], dbeta=WL["dbeta"], seed=seed_of(0),
-                       spin_format=fmt, use_graph=True, profile=args.profile, dim=WL["dim"], potts_q=WL["potts_q"],
+                       spin_format=fmt, use_graph=True, profile=False, dim=WL["dim"], potts_q=WL["potts_q"],
                        group_threads=args.group_threads or 0)
     run = eng.PARun(cfg, stream=stream)
     adaptive = not (WL["dbeta"] > 0)  # steps chosen by histogram overlap, one host decision per step
@@ -285,9 +372,6 @@ def run_engine(args):
     for w in range(args.warmup):
         one(seed_of(10_000 + w))
         run.sync()
-    if args.profile:
-        run.phase_times()  # drop warm-up
-        base = run.phase_times()
     torch.cuda.synchronize(dev)
     barrier(dist)
     clk_path = os.path.join(tempfile.gettempdir(), f"pa_clocks_{os.getpid()}.csv")
@@ -301,6 +385,7 @@ def run_engine(args):
         flush.fill_(k)  # evict L2 between timed steps (outside the events)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
+        n0 = run.kernel_launches()
         e0.record(stream)
         one(seed_of(k))
         e1.record(stream)
@@ -309,7 +394,7 @@ def run_engine(args):
         rows = run.rows()
         assert adaptive or len(rows) == n_steps + 1
         attempts += sites() * theta * int(rows["R"][1:].sum())
-        launches += 2 + 6 * (len(rows) - 1)
+        launches += run.kernel_launches() - n0
         dev_ms += ms
         per_step_ms.append(ms)
     torch.cuda.synchronize(dev)
@@ -321,45 +406,7 @@ def run_engine(args):
 
     roofline = None
     if args.profile and args.format == "bits":
-        pt = run.phase_times()
-        sw_ms = pt["sweep"][0] - base["sweep"][0]
-        sw_n = pt["sweep"][1] - base["sweep"][1]
-        avg_ms = sw_ms / max(sw_n, 1)
-        att_per_launch = attempts / max(sw_n, 1)
-        sm = torch.cuda.get_device_properties(dev).multi_processor_count
-        clk_max = clocks.get("sm_max_mhz") or 2070.0
-        apn = att_per_launch / (avg_ms * 1e6)  # attempts per ns in the sweep kernel
-        mul_peak = sm * 32 * clk_max * 1e6 / 1e9  # Gop/s, wide multiplies
-        alu_peak = sm * 64 * clk_max * 1e6 / 1e9  # Gop/s, ALU pipe
-        achieved = MUL_OPS_PER_ATTEMPT * apn
-        default_wl = WL == DEFAULT_WL
-        shape = run.launch_shape()
-        gt = shape["group_threads"]
-        roofline = {"bound": "alu", "achieved": achieved, "peak": mul_peak, "unit": "Gop/s",
-                    "frac": achieved / mul_peak, "traffic": profiled_traffic() if default_wl else None,
-                    "kernel": f"k_sweep_bits<{L},{gt}" + (",3>" if WL["dim"] == 3 else ">"), "launch": shape,
-                    "ops": "lane-varying 32x32->64 multiplies of Philox4x32-10, 4 per attempt",
-                    "peak_note": "FMA-heavy pipe: SMs x 32 wide multiplies/clk x max SM clock (derived)",
-                    "alu_pipe": {"achieved": ALU_OPS_PER_ATTEMPT * apn, "peak": alu_peak,
-                                 "frac": ALU_OPS_PER_ATTEMPT * apn / alu_peak,
-                                 "ops": "4.5 Philox XOR + 1 compare + 0.5 logic per attempt"},
-                    "attempts_per_ns": apn, "launch_ms": avg_ms, "launches": sw_n,
-                    "share_of_step": sw_ms / dev_ms if dev_ms else None,
-                    "algorithmic_bytes_per_launch": 2 * att_per_launch / (sites() * theta) * (sites() / 8)}
-        try:
-            roofline["rng_ceiling_words_per_ns"] = eng.measure_rng_peak(2048, stream)
-        except Exception as e:  # measurement only
-            roofline["rng_ceiling_words_per_ns"] = f"unavailable: {e}"
-        try:
-            # measured issue rates of the instruction classes behind the derived peaks
-            mp = {"wide_mul": eng.measure_pipe_peak(eng.PIPE_WIDE_MUL, 16384, stream),
-                  "lop3": eng.measure_pipe_peak(eng.PIPE_LOP3, 16384, stream),
-                  "imad": eng.measure_pipe_peak(eng.PIPE_IMAD, 16384, stream)}
-            roofline["measured_pipe_peaks_gops"] = mp
-            roofline["frac_of_measured_wide_mul"] = achieved / mp["wide_mul"]
-            roofline["alu_pipe"]["frac_of_measured_lop3"] = ALU_OPS_PER_ATTEMPT * apn / mp["lop3"]
-        except Exception as e:  # measurement only
-            roofline["measured_pipe_peaks_gops"] = f"unavailable: {e}"
+        roofline = sweep_roofline(eng, cfg, stream, dev, args.prof_runs, clocks, seed_of(20_000))
 
     # end to end through the public API with host buffers
     e2e = None
@@ -387,12 +434,24 @@ def run_engine(args):
         e2e = {"value": sum_over_ranks(att_e2e, dist) / (wmax * 1e9), "unit": UNIT,
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                "note": "wall clock of pa_create + pa_run + pa_observables + pa_destroy per run"}
+    run.close()
+    del flush
+
+    batched = served = None
+    if ws == 1 and not args.no_extras and WL == DEFAULT_WL and args.format == "bits":
+        clk2 = clocks_sampler_start(clk_path)
+        batched = {"config4_prefix": measure_batched(eng, stream, "config4", args.extras_c4_steps, 2, 1),
+                   "config1_set": measure_batched(eng, stream, "config1", 100, 5, 3)}
+        served = measure_served(eng, args.extras_serve_n, args.extras_serve_rdiv, args.extras_serve_beta_f,
+                                args.serve_active, args.serve_budget_gb)
+        c2 = clocks_sampler_stop(clk2, clk_path, local)
+        batched["clocks"] = c2
+        served["clocks"] = c2
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        cpu = cpu_baseline_obj(os.cpu_count() or 1, args.cpu_replicas, 1)
+        cpu = cpu_baseline_obj(os.cpu_count() or 1, args.cpu_replicas)
 
-    run.close()
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -407,7 +466,7 @@ def run_engine(args):
                            "baseline_ref": "paper K80 multi-spin-coded run, 17 s for this workload",
                            "parallelism": f"independent runs x{ws}"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-                "roofline": roofline, "cpu_baseline": cpu,
+                "roofline": roofline, "batched": batched, "served": served, "cpu_baseline": cpu,
                 "per_step_ms": per_step_ms}
         print(json.dumps(line), flush=True)
     if dist is not None:
@@ -415,42 +474,41 @@ def run_engine(args):
     return 0
 
 
-# ------------------------------------------------------------------ other workloads
-def run_batched(args):
-    """Config 4: 64 runs (L, R, theta drawn from Philox tag 3, seed 99), fixed
-    dbeta = 0.005 over beta 0->1, seeds 100..163; all runs in one batched
-    graph launch vs the same runs one at a time (each a graph-captured run)."""
-    import torch
-
-    import paper_1703_03676_gb300 as eng
-    torch.cuda.set_device(0)
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    if args.batch_set == "config1":
-        # 64 small runs of the config-1 shape (L = 16, R = 1000, theta = 10, 100 steps), bit-packed:
-        # each alone is latency-bound, so this is where batching pays
-        n_steps, bf = 100, 1.0
+# ------------------------------------------------------------------ batched and served forms
+def batch_configs(eng, which: str, n_steps: int):
+    """(configs, label) of a batched workload: the config-4 draw (64 runs;
+    L, R, theta from Philox tag 3 seed 99; dbeta 0.005) over its first
+    n_steps steps, or 64 runs of the config-1 shape."""
+    if which == "config1":
         cfgs = [eng.PAConfig(L=16, R=1000, theta=10, beta_f=1.0, dbeta=0.01, seed=100 + i) for i in range(64)]
-        desc = "64 runs of the config-1 shape (L=16, R=1000, theta=10, dbeta 0.01, 100 steps)"
-    else:
-        draw = eng.batch_config4_draw(64)
-        n_steps = args.c4_steps
-        bf = n_steps * 0.005
-        cfgs = [eng.PAConfig(L=L, R=R, theta=th, beta_f=bf, dbeta=0.005, seed=100 + i)
-                for i, (L, R, th) in enumerate(draw)]
-        desc = f"64 runs, L/R/theta from Philox tag 3 seed 99, dbeta 0.005, {n_steps} steps (beta 0->{bf:g})"
+        return cfgs, "64 runs of the config-1 shape (L=16, R=1000, theta=10, dbeta 0.01, 100 steps), bit-packed"
+    draw = eng.batch_config4_draw(64)
+    bf = n_steps * 0.005
+    cfgs = [eng.PAConfig(L=L, R=R, theta=th, beta_f=bf, dbeta=0.005, seed=100 + i)
+            for i, (L, R, th) in enumerate(draw)]
+    label = (f"64 runs, L/R/theta from Philox tag 3 seed 99, dbeta 0.005, bit-packed; "
+             + ("all 200 steps" if n_steps == 200 else
+                f"deviation: the first {n_steps} of 200 steps (beta 0->{bf:g})"))
+    return cfgs, label
+
+
+def measure_batched(eng, stream, which: str, n_steps: int, reps: int, warm: int):
+    """All runs in one batched graph launch vs the same runs one at a time
+    (each its own graph-captured run, launched back to back), device time
+    with CUDA events on the shared stream."""
+    import torch
+    cfgs, label = batch_configs(eng, which, n_steps)
     att_of = lambda rows, c: c.L * c.L * c.theta * int(rows["R"][1:].sum())  # noqa: E731
     b = eng.PABatch(cfgs, stream=stream)
-    times = []
-    att_b = 0
-    for k in range(args.warmup + args.steps):
-        b.reset([100 + i + 1000 * k for i in range(64)])
+    times, att_b = [], 0
+    for k in range(warm + reps):
+        b.reset([100 + i + 1000 * k for i in range(len(cfgs))])
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         b.launch()
         e1.record(stream)
         b.sync()
-        if k >= args.warmup:
+        if k >= warm:
             times.append(e0.elapsed_time(e1))
             att_b += sum(att_of(r.rows(), c) for r, c in zip(b.runs, cfgs))
     v_batched = att_b / (sum(times) * 1e6)
@@ -458,7 +516,7 @@ def run_batched(args):
     b.close()
     runs = [eng.PARun(c, stream=stream) for c in cfgs]
     t_alone, att_a = 0.0, 0
-    for k in range(max(1, args.warmup // 3) + args.steps):
+    for k in range(warm + reps):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         for i, r in enumerate(runs):
             r.reset(100 + i + 1000 * k)
@@ -467,58 +525,84 @@ def run_batched(args):
             r.launch()
         e1.record(stream)
         torch.cuda.synchronize()
-        if k >= max(1, args.warmup // 3):
+        if k >= warm:
             t_alone += e0.elapsed_time(e1)
             att_a += sum(att_of(r.rows(), c) for r, c in zip(runs, cfgs))
     for r in runs:
         r.close()
     v_alone = att_a / (t_alone * 1e6)
-    line = {"metric": METRIC, "workload": "batched", "value": v_batched, "unit": UNIT, "n_gpus": 1,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sum(times) / len(times),
-            "higher_is_better": True, "single_run_value": v_alone, "batched_over_single": v_batched / v_alone,
-            "config": {"workload": f"{desc}, seeds 100..163 (+1000 per bench step), bit-packed",
-                       "attempts_per_step": att_b / len(times), "group_threads_by_L": shapes},
+    return {"value": v_batched, "unit": UNIT, "single_run_value": v_alone,
+            "batched_over_single": v_batched / v_alone, "ms_per_batch": sum(times) / len(times),
+            "reps": reps, "warmup": warm, "workload": f"{label}; seeds 100..163 (+1000 per repetition)",
+            "attempts_per_batch": att_b / len(times), "group_threads_by_L": shapes}
+
+
+def measure_served(eng, n: int, rdiv: int, beta_f: float, active: int, budget_gb: float):
+    """Continuous batching (pa_serve, up to `active` resident runs within an
+    HBM budget) vs the same requests one at a time, on the first n requests
+    of the served trace with R divided by rdiv and beta_f lowered."""
+    import torch
+    trace = eng.served_trace(n)
+    reqs = [(t, eng.PAConfig(L=L, R=max(100, R // rdiv), theta=50, beta_f=beta_f, dbeta=0.0,
+                             overlap=0.85, seed=seed)) for (t, L, R, seed) in trace]
+    free, _ = torch.cuda.mem_get_info()
+    budget = int(min(budget_gb * 2 ** 30, 0.8 * free))
+    out = {}
+    for name, max_active in (("served", active), ("one_at_a_time", 1)):
+        t0 = time.perf_counter()
+        res, _ = eng.serve(reqs, hbm_budget=budget, max_active=max_active)
+        wall = time.perf_counter() - t0
+        lat = sorted(r["finish_s"] - t for r, (t, _) in zip(res, reqs))
+        att = sum(r["attempts"] for r in res)
+        out[name] = {"flips_per_ns": att / (wall * 1e9), "makespan_s": wall, "p50_latency_s": lat[len(lat) // 2],
+                     "p99_latency_s": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+                     "all_ok": all(r["status"] == 0 for r in res), "attempts": att}
+    return {"value": out["served"]["flips_per_ns"], "unit": UNIT,
+            "p50_latency_s": out["served"]["p50_latency_s"], "p99_latency_s": out["served"]["p99_latency_s"],
+            "served_over_one_at_a_time": out["served"]["flips_per_ns"] / out["one_at_a_time"]["flips_per_ns"],
+            "served": out["served"], "one_at_a_time": out["one_at_a_time"],
+            "workload": f"deviation: the first {n} requests of the 500-request served trace (Poisson 20/s, L in "
+                        f"32..512, theta 50, adaptive overlap 0.85, seeds 1000+q) with R/{rdiv} and beta_f "
+                        f"{beta_f:g} instead of 1 (the full trace is ~1e17 attempts)",
+            "max_active": active, "hbm_budget_bytes": budget}
+
+
+def run_batched(args):
+    """The batched workload alone (--workload batched): the config-4 draw or
+    the 64 config-1-shaped runs."""
+    import torch
+
+    import paper_1703_03676_gb300 as eng
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    n_steps = 100 if args.batch_set == "config1" else args.c4_steps
+    r = measure_batched(eng, stream, args.batch_set, n_steps, args.steps, args.warmup)
+    line = {"metric": METRIC, "workload": "batched", "value": r["value"], "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_batch"], "higher_is_better": True,
+            "single_run_value": r["single_run_value"], "batched_over_single": r["batched_over_single"],
+            "config": {"workload": r["workload"], "attempts_per_step": r["attempts_per_batch"],
+                       "group_threads_by_L": r["group_threads_by_L"]},
             "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
 
 
 def run_served(args):
-    """Config 5, scaled: the first n requests of the served trace (Poisson
-    arrivals at 20/s, L in {32..512}, seeds 1000+q, all drawn from Philox tag
-    4 seed 999), theta = 50, adaptive steps with overlap 0.85, with R divided
-    by r_div and beta_f lowered to beta_f_serve. Continuous batching
-    (max_active, HBM budget) vs one run at a time; p50/p99 latency."""
+    """The served workload alone (--workload served), scaled (see
+    measure_served)."""
     import torch
 
     import paper_1703_03676_gb300 as eng
     torch.cuda.set_device(0)
-    trace = eng.served_trace(args.serve_n)
-    reqs = [(t, eng.PAConfig(L=L, R=max(100, R // args.serve_rdiv), theta=50, beta_f=args.serve_beta_f, dbeta=0.0,
-                             overlap=0.85, seed=seed)) for (t, L, R, seed) in trace]
-    free, total = torch.cuda.mem_get_info()
-    budget = int(min(args.serve_budget_gb * 2 ** 30, 0.8 * free))
-    out = {}
-    for name, max_active in (("served", args.serve_active), ("one_at_a_time", 1)):
-        t0 = time.perf_counter()
-        res, _ = eng.serve(reqs, hbm_budget=budget, max_active=max_active)
-        wall = time.perf_counter() - t0
-        lat = sorted(r["finish_s"] - t for r, (t, _) in zip(res, reqs))
-        att = sum(r["attempts"] for r in res)
-        ok = all(r["status"] == 0 for r in res)
-        out[name] = {"flips_per_ns": att / (wall * 1e9), "makespan_s": wall, "p50_latency_s": lat[len(lat) // 2],
-                     "p99_latency_s": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
-                     "all_ok": ok, "attempts": att}
-    line = {"metric": METRIC, "workload": "served", "value": out["served"]["flips_per_ns"], "unit": UNIT,
-            "n_gpus": 1, "higher_is_better": True,
-            "p50_latency_s": out["served"]["p50_latency_s"], "p99_latency_s": out["served"]["p99_latency_s"],
-            "one_at_a_time": out["one_at_a_time"],
-            "served_over_one_at_a_time": out["served"]["flips_per_ns"] / out["one_at_a_time"]["flips_per_ns"],
-            "served": out["served"],
-            "config": {"workload": f"first {args.serve_n} requests of the 500-request trace (Poisson 20/s, L in "
-                                   f"32..512, seeds 1000+q); deviation: R/{args.serve_rdiv}, beta_f "
-                                   f"{args.serve_beta_f} instead of 1 (the full trace is ~1e17 attempts)",
-                       "max_active": args.serve_active, "hbm_budget_bytes": budget, "theta": 50, "overlap": 0.85},
+    r = measure_served(eng, args.serve_n, args.serve_rdiv, args.serve_beta_f, args.serve_active,
+                       args.serve_budget_gb)
+    line = {"metric": METRIC, "workload": "served", "value": r["value"], "unit": UNIT, "n_gpus": 1,
+            "higher_is_better": True, "p50_latency_s": r["p50_latency_s"], "p99_latency_s": r["p99_latency_s"],
+            "one_at_a_time": r["one_at_a_time"], "served_over_one_at_a_time": r["served_over_one_at_a_time"],
+            "served": r["served"],
+            "config": {"workload": r["workload"], "max_active": r["max_active"],
+                       "hbm_budget_bytes": r["hbm_budget_bytes"], "theta": 50, "overlap": 0.85},
             "data": "synthetic"}
     print(json.dumps(line), flush=True)
     return 0
@@ -552,12 +636,23 @@ def main():
     ap.add_argument("--serve-beta-f", type=float, default=0.5)
     ap.add_argument("--serve-active", type=int, default=8)
     ap.add_argument("--serve-budget-gb", type=float, default=100.0)
-    ap.add_argument("--no-profile", dest="profile", action="store_false")
+    ap.add_argument("--no-profile", dest="profile", action="store_false",
+                    help="skip the separate profiled pass behind the roofline")
+    ap.add_argument("--prof-runs", type=int, default=2, help="complete runs of the profiled pass")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the batched and served sub-objects of the default line")
+    ap.add_argument("--extras-c4-steps", type=int, default=20,
+                    help="steps of the config-4 prefix in the default line's batched object")
+    ap.add_argument("--extras-serve-n", type=int, default=16)
+    ap.add_argument("--extras-serve-rdiv", type=int, default=100)
+    ap.add_argument("--extras-serve-beta-f", type=float, default=0.3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--cpu-replicas", type=int, default=2000)
-    ap.add_argument("--ref-replicas", type=int, default=400)
+    ap.add_argument("--cpu-replicas", type=int, default=8,
+                    help="replicas per process of the cpu_baseline sample (whole anneals)")
+    ap.add_argument("--ref-replicas", type=int, default=2,
+                    help="replicas per process of each --impl reference step (whole anneals)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

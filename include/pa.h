@@ -261,6 +261,10 @@ pa_status pa_ln_dos(pa_ctx *ctx, double *out, int64_t cap);
  * [4] sweep, [5] stats, [6] init; launches[p] gets the launch count. */
 pa_status pa_phase_times(pa_ctx *ctx, double ms[7], int64_t launches[7]);
 
+/* Number of this library's kernels launched for the run since pa_create
+ * (a replay of the captured schedule counts every kernel node it runs). */
+pa_status pa_kernel_launches(pa_ctx *ctx, int64_t *n);
+
 /* The sweep launch shape chosen for this run (threads per replica, CTA size,
  * persistent CTAs). */
 pa_status pa_launch_shape(pa_ctx *ctx, int32_t *group_threads, int32_t *block_threads, int32_t *grid_blocks);
@@ -392,8 +396,12 @@ pa_status pa_philox_device(const uint32_t *dev_ctr, int64_t n, uint64_t seed, ui
  * in old-slot order. Device inputs: dev_levels[n_old] (0 <= k < n_levels),
  * dev_F[n_levels] = floor(tau_hat_k), dev_U[n_levels] = ceil(frac 2^32).
  * Device output: dev_parent[parent_cap]. Host output: *n_new = R_i.
- * Scratch (about 8 bytes per old slot) is allocated and freed inside the
- * call. PA_ECAPACITY if R_i > parent_cap (dev_parent is then unspecified),
+ * Any F values are accepted (copy numbers and their sums are formed in 64
+ * bits, so no total wraps); 1 <= n_old <= 2^31 and
+ * 1 <= parent_cap <= 2^31. Scratch (about 8 bytes per old slot) is
+ * allocated and freed inside the call. PA_ECAPACITY if R_i > parent_cap:
+ * dev_parent is then left unwritten and *n_new is R_i, or 0 when the
+ * copies of one 1024-slot tile alone already exceed parent_cap.
  * PA_EEXTINCT if R_i = 0, PA_EINVAL on bad sizes. Synchronous on
  * `cuda_stream` (NULL: the legacy default stream). */
 pa_status pa_resample(const int32_t *dev_levels, int64_t n_old, const uint32_t *dev_F, const uint64_t *dev_U,

@@ -85,6 +85,7 @@ SIGNATURES = [
     ("pa_ln_dos", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), ctypes.c_int64]),
     ("pa_mag_sums", ctypes.c_int, [_P, _P, ctypes.c_int64]),
     ("pa_phase_times", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I64P]),
+    ("pa_kernel_launches", ctypes.c_int, [_P, _I64P]),
     ("pa_launch_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32)]),
     ("pa_footprint_bytes", ctypes.c_size_t, [ctypes.POINTER(_Config)]),
@@ -382,6 +383,12 @@ class PARun:
         _check(self._lib.pa_phase_times(self._h, ms, n), "pa_phase_times")
         names = ["tables", "counts", "scan", "parent", "sweep", "stats", "init"]
         return {k: (ms[i], n[i]) for i, k in enumerate(names)}
+
+    def kernel_launches(self) -> int:
+        """Kernels of the engine launched for this run so far (pa_kernel_launches)."""
+        n = ctypes.c_int64()
+        _check(self._lib.pa_kernel_launches(self._h, ctypes.byref(n)), "pa_kernel_launches")
+        return n.value
 
     def launch_shape(self):
         g, b, n = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()

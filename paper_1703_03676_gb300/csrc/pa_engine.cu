@@ -115,6 +115,8 @@ struct pa_ctx {
     bool gev_pending = false;
     double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};
     long long phase_n[7] = {0, 0, 0, 0, 0, 0, 0};
+    long long n_kern = 0;         // kernels of this library launched for the run
+    long long graph_kern = 0;     // kernels in one launch of `graph`
 };
 
 namespace {
@@ -350,6 +352,7 @@ pa_status prof_collect(pa_ctx* c)
         cudaEvent_t ev_;                               \
         PA_TRY(prof_begin(ctx, ph, &ev_));             \
         PA_CUDA(launch);                               \
+        (ctx)->n_kern++;                               \
         PA_TRY(prof_end(ctx));                         \
     } while (0)
 
@@ -600,6 +603,7 @@ pa_status reset_run(pa_ctx* c, uint64_t seed)
     PA_TRY(prof_begin(c, 5, &ev));
     PA_CUDA(pa::launch_stats(nullptr, h, 0, c->stream));
     PA_TRY(prof_end(c));
+    c->n_kern += 2;
     return enqueue_readback(c);
 }
 
@@ -619,12 +623,15 @@ pa_status launch_rest(pa_ctx* c)
             c->capturing = true;
             cudaGraph_t g = nullptr;
             pa_status st = PA_OK;
+            const long long k0 = c->n_kern;
             if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = PA_ECUDA;
             while (st == PA_OK && !c->done) st = enqueue_step(c);
             if (st == PA_DONE) st = PA_OK;
             const cudaError_t ce = cudaStreamEndCapture(cap, &g);
             c->stream = saved;
             c->capturing = false;
+            c->graph_kern = c->n_kern - k0;  // captured, not launched yet
+            c->n_kern = k0;
             if (st == PA_OK && ce != cudaSuccess) st = PA_ECUDA;
             if (st == PA_OK && cudaGraphInstantiate(&c->graph, g, 0) != cudaSuccess) st = PA_ECUDA;
             if (g) cudaGraphDestroy(g);
@@ -652,6 +659,7 @@ pa_status launch_rest(pa_ctx* c)
             }
         }
         PA_CUDA(cudaGraphLaunch(c->graph, c->stream));
+        c->n_kern += c->graph_kern;
         if (c->cfg.profile) c->gev_pending = true;
         return PA_OK;
     }
@@ -702,7 +710,11 @@ pa_status noalloc_scratch(unsigned char** out)
 {
     int dev = 0;
     PA_CUDA(cudaGetDevice(&dev));
-    if (dev < 0 || dev >= kMaxDevices) return PA_EINVAL;
+    if (dev < 0 || dev >= kMaxDevices) {
+        std::snprintf(g_last_error, sizeof(g_last_error),
+                      "pa_resample_noalloc: device index %d is not below the supported %d devices", dev, kMaxDevices);
+        return PA_EINVAL;
+    }
     std::lock_guard<std::mutex> g(g_noalloc_mu);
     if (!g_noalloc_addr[dev]) {
         void* p = nullptr;
@@ -1352,6 +1364,13 @@ pa_status pa_phase_times(pa_ctx* c, double ms[7], int64_t launches[7])
     return PA_OK;
 }
 
+pa_status pa_kernel_launches(pa_ctx* c, int64_t* n)
+{
+    if (!c || !n) return PA_EINVAL;
+    *n = c->n_kern;
+    return PA_OK;
+}
+
 pa_status pa_launch_shape(pa_ctx* c, int32_t* gt, int32_t* bt, int32_t* gb)
 {
     if (!c) return PA_EINVAL;
@@ -1382,7 +1401,7 @@ pa_status pa_resample(const int32_t* lev, int64_t n_old, const uint32_t* F, cons
                       uint64_t seed, int64_t step, uint32_t* parent, int64_t cap, int64_t* n_new, void* stream)
 {
     if (!lev || !F || !U || !parent || !n_new || n_old < 1 || n_old > (1ll << 31) || n_levels < 1 || cap < 1 ||
-        step < 0 || step > 0xffffffffll)
+        cap > (1ll << 31) || step < 0 || step > 0xffffffffll)
         return PA_EINVAL;
     *n_new = 0;
     cudaStream_t s = (cudaStream_t)stream;
@@ -1430,6 +1449,7 @@ pa_status pa_resample(const int32_t* lev, int64_t n_old, const uint32_t* F, cons
         int hs = 0;
         cudaError_t e = cudaMemcpyAsync(key, hk, 8, cudaMemcpyHostToDevice, s);
         if (e == cudaSuccess) e = cudaMemsetAsync(st, 0, 16, s);
+        if (e == cudaSuccess) e = cudaMemsetAsync(nn, 0, 16, s);  // stays 0 if a tile alone exceeds cap
         if (e == cudaSuccess) e = pa::launch_resample(a, (int)tiles, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hn, nn, 8, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, st, 4, cudaMemcpyDeviceToHost, s);
@@ -1452,8 +1472,8 @@ pa_status pa_resample_noalloc(const int32_t* lev, int64_t n_old, const uint32_t*
                               int64_t n_levels, uint64_t seed, int64_t step, uint32_t* parent, int64_t cap,
                               int64_t* n_new, void* stream)
 {
-    if (!lev || !F || !U || !parent || !n_new || n_old < 1 || n_levels < 1 || cap < 1 || step < 0 ||
-        step > 0xffffffffll)
+    if (!lev || !F || !U || !parent || !n_new || n_old < 1 || n_levels < 1 || cap < 1 || cap > (1ll << 31) ||
+        step < 0 || step > 0xffffffffll)
         return PA_EINVAL;
     *n_new = 0;
     if (n_old > kNoAllocMaxOld) {
@@ -1487,13 +1507,15 @@ pa_status pa_resample_noalloc(const int32_t* lev, int64_t n_old, const uint32_t*
     a.n_prev_out = nullptr;
     a.status = st;
     a.work = nullptr;
-    // the array keeps the previous call's contents: the status word must
-    // start at zero; every other part is written before it is read
+    // the array keeps the previous call's contents: the status word and R_i
+    // must start at zero (R_i stays 0 when one tile alone exceeds cap); every
+    // other part is written before it is read
     const unsigned hk[2] = {(unsigned)(seed & 0xffffffffu), (unsigned)(seed >> 32)};
     long long hn = 0;
     int hs = 0;
     PA_CUDA(cudaMemcpyAsync(key, hk, 8, cudaMemcpyHostToDevice, s));
     PA_CUDA(cudaMemsetAsync(st, 0, 4, s));
+    PA_CUDA(cudaMemsetAsync(nn, 0, 8, s));
     PA_CUDA(pa::launch_resample(a, (int)tiles, s));
     PA_CUDA(cudaMemcpyAsync(&hn, nn, 8, cudaMemcpyDeviceToHost, s));
     PA_CUDA(cudaMemcpyAsync(&hs, st, 4, cudaMemcpyDeviceToHost, s));

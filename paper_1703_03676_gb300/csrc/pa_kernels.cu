@@ -1353,14 +1353,21 @@ __device__ __forceinline__ long long n_old_of(const ResampleArgs& a)
     return a.n_old_dev ? *a.n_old_dev : a.n_old;
 }
 
+// The copy numbers, their tile prefix and the tile total are summed in 64
+// bits: the tables may come from a caller (pa_resample), and 1024 slots with
+// F near 2^32 would wrap a 32-bit total to a small R_i. A tile whose total
+// exceeds the capacity sets the capacity status here, so the scan and the
+// parent scatter (later launches, which return when the status is set) never
+// see a wrapped total; the stored 32-bit values are exact whenever the
+// status stays clear (every total <= cap < 2^31).
 __device__ __forceinline__ void counts_body(const ResampleArgs& a, int tile)
 {
-    __shared__ uint32_t wsum[kTileThreads / 32];
+    __shared__ unsigned long long wsum[kTileThreads / 32];
     const long long Rp = n_old_of(a);
     const long long tile0 = (long long)tile * kTile;
     if (tile0 >= Rp) return;
     const long long j0 = tile0 + 4 * threadIdx.x;
-    uint32_t c[4] = {0u, 0u, 0u, 0u};
+    unsigned long long c[4] = {0ull, 0ull, 0ull, 0ull};
     if (j0 < Rp) {
         const uint4 x = philox10(make_uint4(a.step, (unsigned)(j0 >> 2), kTagResample, 0u),
                                  PhiloxKey{a.key[0], a.key[1]});
@@ -1370,38 +1377,43 @@ __device__ __forceinline__ void counts_body(const ResampleArgs& a, int tile)
             const long long j = j0 + l;
             if (j < Rp) {
                 const int lv = a.lev[j];
-                c[l] = a.F[lv] + (((unsigned long long)xs[l] < a.U[lv]) ? 1u : 0u);
+                c[l] = (unsigned long long)a.F[lv] + (((unsigned long long)xs[l] < a.U[lv]) ? 1ull : 0ull);
             }
         }
     }
-    const uint32_t tsum = c[0] + c[1] + c[2] + c[3];
+    const unsigned long long tsum = c[0] + c[1] + c[2] + c[3];
     // block exclusive scan of tsum
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t incl = tsum;
+    unsigned long long incl = tsum;
 #pragma unroll
     for (int off = 1; off < 32; off <<= 1) {
-        const uint32_t y = __shfl_up_sync(0xffffffffu, incl, off);
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, off);
         if (lane >= off) incl += y;
     }
     if (lane == 31) wsum[warp] = incl;
     __syncthreads();
-    uint32_t wbase = 0;
-    for (int w = 0; w < warp; w++) wbase += wsum[w];
-    uint32_t run = wbase + incl - tsum;
+    unsigned long long wbase = 0, tot = 0;
+#pragma unroll
+    for (int w = 0; w < kTileThreads / 32; w++) {
+        if (w < warp) wbase += wsum[w];
+        tot += wsum[w];
+    }
+    if (tot > (unsigned long long)a.cap) {
+        // R_i > cap for certain: leave cnt/loc/tile_sum alone (never read)
+        if (threadIdx.x == 0) *a.status = kStatusCapacity;
+        return;
+    }
+    unsigned long long run = wbase + incl - tsum;
 #pragma unroll
     for (int l = 0; l < 4; l++) {
         const long long j = j0 + l;
         if (j < Rp) {
-            a.cnt[j] = c[l];
-            a.loc[j] = run;
+            a.cnt[j] = (uint32_t)c[l];
+            a.loc[j] = (uint32_t)run;
         }
         run += c[l];
     }
-    if (threadIdx.x == kTileThreads - 1) {
-        uint32_t tot = 0;
-        for (int w = 0; w < kTileThreads / 32; w++) tot += wsum[w];
-        a.tile_sum[tile] = tot;
-    }
+    if (threadIdx.x == 0) a.tile_sum[tile] = (uint32_t)tot;
 }
 
 __global__ void __launch_bounds__(kTileThreads) k_counts(const __grid_constant__ ResampleArgs a)

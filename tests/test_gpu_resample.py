@@ -52,3 +52,39 @@ def test_resample_capacity_error():
                      torch.from_numpy(F.astype(np.uint32).view(np.int32)).cuda(),
                      torch.from_numpy(U).cuda(), seed, step, parent.size - 1)
     assert ei.value.kind == "capacity"
+
+
+@pytest.mark.parametrize("noalloc", [False, True])
+def test_resample_wrapping_copy_numbers_rejected(noalloc):
+    """Caller tables whose copy numbers sum past 2^32: F = 2^31 for two slots
+    and 1 for a third give R_i = 2^32 + 1, which a 32-bit total would wrap
+    to 1 and accept. The call must report the capacity error and leave the
+    parent buffer unwritten."""
+    F = np.array([2 ** 31, 1], dtype=np.int64)
+    lev = np.array([0, 0, 1], dtype=np.int64)
+    total = int(sum(int(F[k]) for k in lev))  # exact, on the CPU
+    assert total == 2 ** 32 + 1 and total % 2 ** 32 == 1
+    cap = 8
+    parent = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    with pytest.raises(eng.PAError) as ei:
+        eng.resample(torch.from_numpy(lev.astype(np.int32)).cuda(),
+                     torch.from_numpy(F.astype(np.uint32).view(np.int32)).cuda(),
+                     torch.zeros(2, dtype=torch.int64, device="cuda"), 3, 1, cap, parent=parent, noalloc=noalloc)
+    assert ei.value.kind == "capacity"
+    assert bool((parent == -7).all())
+
+
+def test_resample_capacity_over_tiles_leaves_parent_unwritten():
+    """A ragged population of 2500 slots (three tiles) whose tiles each fit
+    the capacity but whose total does not: capacity error, nothing written."""
+    n_old = 2500
+    lev = np.zeros(n_old, dtype=np.int64)
+    F = np.array([3], dtype=np.int64)
+    cap = 4000  # each tile holds at most 1024 * 3 = 3072 copies; the total is 7500
+    parent = torch.full((cap,), -7, dtype=torch.int32, device="cuda")
+    with pytest.raises(eng.PAError) as ei:
+        eng.resample(torch.from_numpy(lev.astype(np.int32)).cuda(),
+                     torch.from_numpy(F.astype(np.uint32).view(np.int32)).cuda(),
+                     torch.zeros(1, dtype=torch.int64, device="cuda"), 9, 2, cap, parent=parent)
+    assert ei.value.kind == "capacity"
+    assert bool((parent == -7).all())

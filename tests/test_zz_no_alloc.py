@@ -38,6 +38,25 @@ def test_noalloc_matches_allocating_entry_point_twice():
         np.testing.assert_array_equal(got.cpu().numpy(), ref.cpu().numpy())
 
 
+def test_noalloc_after_a_failed_call_and_at_the_size_limit():
+    # a call that leaves a capacity status in the shared array, then good
+    # calls: the status word is cleared and every other part of the scratch
+    # is written before it is read, so they must match pa_resample
+    lev, F, U, parent = oracle_case(3000, 4096, 5, 3, 0.05, 3000)
+    with pytest.raises(eng.PAError) as ei:
+        _call(lev, F, U, 5, 3, parent.size - 1, noalloc=True)
+    assert ei.value.kind == "capacity"
+    n_old = eng.RESAMPLE_NOALLOC_MAX_OLD  # the largest population the array holds
+    for n, seed, step in [(2000, 11, 4), (n_old, 12, 7)]:
+        lev, F, U, parent = oracle_case(n, 4096, seed, step, 0.004, n)
+        cap = 2 * n + 16
+        ref, n_ref = _call(lev, F, U, seed, step, cap, noalloc=False)
+        got, n_got = _call(lev, F, U, seed, step, cap, noalloc=True)
+        assert n_got == n_ref == parent.size
+        np.testing.assert_array_equal(got.cpu().numpy(), ref.cpu().numpy())
+        np.testing.assert_array_equal(got.cpu().numpy(), parent)
+
+
 def test_noalloc_rejects_oversize():
     n_old = eng.RESAMPLE_NOALLOC_MAX_OLD + 1
     lev = torch.zeros(n_old, dtype=torch.int32, device="cuda")
