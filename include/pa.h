@@ -258,7 +258,13 @@ pa_status pa_ln_dos(pa_ctx *ctx, double *out, int64_t cap);
 
 /* Accumulated device time in ms of each kernel phase (needs profile != 0):
  * [0] tables (Q and copy tables), [1] counts, [2] scan, [3] parent scatter,
- * [4] sweep, [5] stats, [6] init; launches[p] gets the launch count. */
+ * [4] sweep, [5] stats, [6] init; launches[p] gets the launch count. A run
+ * whose capacity is at most 16384 replicas resamples in one single-CTA
+ * launch per step, counted under [0] (tables, copy numbers, scan and
+ * parents, plus the previous step's statistics when the whole schedule is
+ * enqueued at once by pa_run or pa_launch). The events themselves add a few
+ * microseconds per launch: a small run's profiled time is well above its
+ * unprofiled one. */
 pa_status pa_phase_times(pa_ctx *ctx, double ms[7], int64_t launches[7]);
 
 /* Number of this library's kernels launched for the run since pa_create

@@ -328,7 +328,12 @@ class PopulationAnnealing:
     def __init__(self, L: int, R: int, theta: int, beta_f: float = 1.0, dbeta: float = 0.01,
                  seed: int = 1, beta0: float = 0.0, overlap: float = 0.85,
                  capacity: int = 0, record_hist: bool = True, schedule=None, msc: bool = False,
-                 couplings=None, dim: int = 2, potts_q: int = 0):
+                 couplings=None, dim: int = 2, potts_q: int = 0, workers: int = 1):
+        """workers > 1 splits the population into that many contiguous
+        blocks of replicas for the initial spins, the sweeps and the
+        measurements, each block run by the same single-threaded C routine on
+        its own thread. Replicas are independent given their slot numbers, so
+        every result is identical to workers = 1."""
         if dim not in (2, 3):
             raise ValueError("dim must be 2 or 3")
         if potts_q and not (2 <= potts_q <= 8 and dim == 2 and not msc and couplings is None):
@@ -377,9 +382,11 @@ class PopulationAnnealing:
         self.beta = 0.0
         self.done = False
         self.partial = False
+        self.workers = max(1, int(workers))
         # step 0: random configurations at beta0 = 0, measured, no sweeps
         slots = np.arange(self.R, dtype=np.int64)
-        self.pop = init_spins(L, slots, self.seed, dim, self.q)
+        self.pop = self._blocks(lambda a, b: init_spins(L, slots[a:b], self.seed, dim, self.q), self.R,
+                                combine=np.concatenate)
         self.E, self.M = self._measure(self.pop)
         self.fam = np.arange(self.R, dtype=np.int64)
         self.sum_lnQ = 0.0
@@ -399,14 +406,35 @@ class PopulationAnnealing:
         # Ising: number of up spins; Potts: M itself (the majority state's size)
         return self.M if self.q else (self.M + self.N) // 2
 
+    def _blocks(self, fn, n, combine=None):
+        """fn(a, b) on the replica blocks [a, b) of n replicas: one block, or
+        `workers` contiguous blocks on a thread pool (the C routines release
+        the interpreter lock). combine joins the blocks' results in order."""
+        w = self.workers if n >= 2 * self.workers else 1
+        cuts = [n * i // w for i in range(w + 1)]
+        if w == 1:
+            parts = [fn(0, n)]
+        else:
+            from concurrent.futures import ThreadPoolExecutor
+            with ThreadPoolExecutor(w) as ex:
+                parts = list(ex.map(lambda i: fn(cuts[i], cuts[i + 1]), range(w)))
+        return combine(parts) if combine else None
+
     def _measure(self, s):
-        return measure_potts(s, self.q) if self.q else measure(s, self.J)
+        def one(a, b):
+            sub = s[a:b]
+            return measure_potts(sub, self.q) if self.q else measure(sub, self.J)
+        parts = self._blocks(one, s.shape[0], combine=list)
+        return np.concatenate([p[0] for p in parts]), np.concatenate([p[1] for p in parts])
 
     def _sweep(self, s, slots, u0, T4, T8, T12, TP):
-        if self.q:
-            sweep_potts(s, slots, self.seed, u0, self.theta, self.q, TP)
-        else:
-            sweep(s, slots, self.seed, u0, self.theta, T4, T8, msc=self.msc, couplings=self.J, T12=T12)
+        def one(a, b):  # s[a:b] is a contiguous block of s: swept in place
+            if self.q:
+                sweep_potts(s[a:b], slots[a:b], self.seed, u0, self.theta, self.q, TP)
+            else:
+                sweep(s[a:b], slots[a:b], self.seed, u0, self.theta, T4, T8, msc=self.msc, couplings=self.J,
+                      T12=T12)
+        self._blocks(one, s.shape[0])
 
     def _measure_and_record(self, rec: StepRecord):
         N = self.N
@@ -513,50 +541,66 @@ class PopulationAnnealing:
         return self.rows
 
     # -- multi-histogram reweighting (Sec. 2.4, Eq. MHReq1)
+    # Plain loops in ascending level and row order, one libm exp/log per term
+    # and sums accumulated left to right: every result is the value of the
+    # formula evaluated in that stated order.
     def ln_dos(self) -> tuple[np.ndarray, np.ndarray]:
         """ln Omega(E_k) for every level with Hsum[k] > 0 (others -inf):
         ln Omega_k = ln Hsum_k - LSE_i(ln R_i + beta_i F_i - beta_i E_k),
-        beta_i F_i = -(N ln 2 + sum_{l<=i} ln Q_l) (N ln q for Potts)."""
+        beta_i F_i = -(N ln 2 + sum_{l<=i} ln Q_l) (N ln q for Potts), with
+        LSE_i(a_i) = m + ln sum_i exp(a_i - m), m = max_i a_i."""
         N = self.N
-        E_k = (-self.eoff + self.estep * np.arange(self.nl)).astype(np.float64)
-        betas = np.array([r.beta for r in self.rows])
-        lnR = np.log(np.array([float(r.R) for r in self.rows]))
-        bF = np.array([r.betaF_per_N for r in self.rows]) * N
+        E_k = [float(-self.eoff + self.estep * k) for k in range(self.nl)]
+        betas = [r.beta for r in self.rows]
+        lnR = [math.log(float(r.R)) for r in self.rows]
+        bF = [r.betaF_per_N * N for r in self.rows]
         out = np.full(self.nl, -np.inf)
         for k in range(self.nl):
             if self.Hsum[k] > 0:
-                a = lnR + bF - betas * E_k[k]
-                m = a.max()
-                out[k] = math.log(float(self.Hsum[k])) - (m + math.log(float(np.exp(a - m).sum())))
-        return E_k, out
+                a = [lnR[i] + bF[i] - betas[i] * E_k[k] for i in range(len(betas))]
+                m = max(a)
+                s = 0.0
+                for v in a:
+                    s += math.exp(v - m)
+                out[k] = math.log(float(self.Hsum[k])) - (m + math.log(s))
+        return np.array(E_k), out
 
     def mhr(self, betas) -> list[dict]:
         """Reweighted e, C, beta F / N, S / N and magnetisation moments at each
-        beta. The Boltzmann weight depends on E only, so the joint estimate
+        beta: Z(beta) = sum_k Omega_k exp(-beta E_k), sums over the visited
+        levels in ascending order (shifted by the largest exponent). The
+        Boltzmann weight depends on E only, so the joint estimate
         Omega(E, M) of Eq. MHReq1 gives sum_M Omega(E, M) f(M) =
         Omega(E) * (sum of f(M) over every sample at level E) / Hsum(E)."""
         N = self.N
+        fN = float(N)
         E_k, lno = self.ln_dos()
-        ok = np.isfinite(lno)
-        E, lo = E_k[ok], lno[ok]
-        idx = np.nonzero(ok)[0]
-        cnt = np.array([float(self.Hsum[k]) for k in idx])
-        mic = np.array([[float(self.Msums[k][j]) / c for j in range(3)] for k, c in zip(idx, cnt)])
+        lev = [k for k in range(self.nl) if np.isfinite(lno[k])]
+        mic = {k: [float(self.Msums[k][j]) / float(self.Hsum[k]) for j in range(3)] for k in lev}
         out = []
         for b in betas:
-            a = lo - b * E
-            m = a.max()
-            w = np.exp(a - m)
-            Z = w.sum()
-            lnZ = m + math.log(float(Z))
-            e1 = float((w * E).sum() / Z)
-            e2 = float((w * E * E).sum() / Z)
-            am, m2, m4 = (float((w * mic[:, j]).sum() / Z) for j in range(3))
-            e = e1 / N
-            bF = -lnZ / N
-            out.append({"beta": float(b), "e": e, "C": b * b * (e2 - e1 * e1) / N,
+            b = float(b)
+            m = -math.inf
+            for k in lev:
+                m = max(m, lno[k] - b * E_k[k])
+            Z = e1 = e2 = a1 = a2 = a4 = 0.0
+            for k in lev:
+                Ek = E_k[k]
+                w = math.exp(lno[k] - b * Ek - m)
+                Z += w
+                e1 += w * Ek
+                e2 += w * Ek * Ek
+                a1 += w * mic[k][0]
+                a2 += w * mic[k][1]
+                a4 += w * mic[k][2]
+            e1 /= Z
+            e2 /= Z
+            lnZ = m + math.log(Z)
+            e = e1 / fN
+            bF = -lnZ / fN
+            out.append({"beta": b, "e": e, "C": b * b * (e2 - e1 * e1) / fN,
                         "betaF_per_N": bF, "S_per_N": b * e - bF, "lnZ": lnZ,
-                        "abs_m": am / N, "m2": m2 / N ** 2, "m4": m4 / N ** 4})
+                        "abs_m": a1 / Z / fN, "m2": a2 / Z / (fN * fN), "m4": a4 / Z / (fN * fN * fN * fN)})
         return out
 
 

@@ -117,6 +117,8 @@ struct pa_ctx {
     long long phase_n[7] = {0, 0, 0, 0, 0, 0, 0};
     long long n_kern = 0;         // kernels of this library launched for the run
     long long graph_kern = 0;     // kernels in one launch of `graph`
+    bool small_rs = false;        // capacity <= kSmallCap: one-CTA resampling launch per step
+    bool stats_pending = false;   // statistics of the last enqueued step not yet launched
 };
 
 namespace {
@@ -224,6 +226,11 @@ int auto_group(const pa_config& c)
         if (wp >= 256) return 256;
         int g = 32;
         while (g > 1 && wp % g) g >>= 1;
+        // square lattices with few words per replica and a population too
+        // small to occupy the device: up to 8 threads share each word's
+        // Philox blocks, until the run has ~16 warps per SM
+        if (dim_of(c) == 2)
+            while (g < 32 && g < 8 * wp && c.R * 2 * g <= 152ll * 16 * 32) g <<= 1;
         return g;
     }
     const long long qp = (N / 2 + 3) / 4;
@@ -357,15 +364,27 @@ pa_status prof_collect(pa_ctx* c)
     } while (0)
 
 // ---------------------------------------------------------------- steps
-pa_status enqueue_kernels(pa_ctx* c, int step)
+// One temperature step. Small populations (capacity <= kSmallCap) resample
+// in one single-CTA launch; larger ones in four (tables, counts, scan,
+// parent). The statistics of the step run at once when stats_now (the host
+// may read them next), else they are deferred into the next step's first
+// launch (a whole schedule enqueued at once; its last step has stats_now).
+pa_status enqueue_kernels(pa_ctx* c, int step, bool stats_now)
 {
     const RunDev& h = c->h;
-    PA_PHASE(c, 0, pa::launch_tables(nullptr, h, step, c->stream));
-    PA_PHASE(c, 1, pa::launch_counts(nullptr, h, c->ln, step, c->stream));
-    PA_PHASE(c, 2, pa::launch_scan(nullptr, h, step, c->stream));
-    PA_PHASE(c, 3, pa::launch_parent(nullptr, h, c->ln, step, c->stream));
+    if (c->small_rs) {
+        PA_PHASE(c, 0, pa::launch_resample_small(h, step, c->stats_pending, c->stream));
+    } else {
+        if (c->stats_pending) PA_PHASE(c, 5, pa::launch_stats(nullptr, h, step - 1, c->stream));
+        PA_PHASE(c, 0, pa::launch_tables(nullptr, h, step, c->stream));
+        PA_PHASE(c, 1, pa::launch_counts(nullptr, h, c->ln, step, c->stream));
+        PA_PHASE(c, 2, pa::launch_scan(nullptr, h, step, c->stream));
+        PA_PHASE(c, 3, pa::launch_parent(nullptr, h, c->ln, step, c->stream));
+    }
+    c->stats_pending = false;
     PA_PHASE(c, 4, pa::launch_sweep(nullptr, h, c->ln, step, c->stream));
-    PA_PHASE(c, 5, pa::launch_stats(nullptr, h, step, c->stream));
+    if (stats_now) PA_PHASE(c, 5, pa::launch_stats(nullptr, h, step, c->stream));
+    else c->stats_pending = true;
     return PA_OK;
 }
 
@@ -418,7 +437,7 @@ double overlap_alpha(const std::vector<long long>& H, int kmin, int kmax, long l
 
 pa_status enqueue_readback(pa_ctx* c);
 
-pa_status enqueue_step(pa_ctx* c, bool wait = true)
+pa_status enqueue_step(pa_ctx* c, bool wait = true, bool defer_stats = false)
 {
     if (c->done) return PA_DONE;
     const long long i = c->enq_step + 1;
@@ -500,7 +519,7 @@ pa_status enqueue_step(pa_ctx* c, bool wait = true)
         c->T4.push_back(t4);
         c->T8.push_back(t8);
     }
-    PA_TRY(enqueue_kernels(c, (int)i));
+    PA_TRY(enqueue_kernels(c, (int)i, !defer_stats || final_step || c->adaptive));
     c->betas.push_back(beta);
     c->deltas.push_back(delta);
     c->enq_step = i;
@@ -596,6 +615,7 @@ pa_status reset_run(pa_ctx* c, uint64_t seed)
     c->done_rows = 0;
     c->enq_step = 0;
     c->done = false;
+    c->stats_pending = false;
     cudaEvent_t ev;
     PA_TRY(prof_begin(c, 6, &ev));
     PA_CUDA(pa::launch_init(nullptr, h, c->ln, c->stream));
@@ -625,7 +645,7 @@ pa_status launch_rest(pa_ctx* c)
             pa_status st = PA_OK;
             const long long k0 = c->n_kern;
             if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = PA_ECUDA;
-            while (st == PA_OK && !c->done) st = enqueue_step(c);
+            while (st == PA_OK && !c->done) st = enqueue_step(c, true, true);
             if (st == PA_DONE) st = PA_OK;
             const cudaError_t ce = cudaStreamEndCapture(cap, &g);
             c->stream = saved;
@@ -646,6 +666,7 @@ pa_status launch_rest(pa_ctx* c)
                 c->enq_step = 0;
                 c->done = false;
                 c->graph = nullptr;
+                c->stats_pending = false;
                 return st;
             }
         } else {
@@ -664,7 +685,7 @@ pa_status launch_rest(pa_ctx* c)
         return PA_OK;
     }
     pa_status st = PA_OK;
-    while (st == PA_OK) st = enqueue_step(c);
+    while (st == PA_OK) st = enqueue_step(c, true, true);
     return st == PA_DONE ? PA_OK : st;
 }
 
@@ -861,7 +882,11 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     h.fmt = cfg->spin_format;
     h.gt = cfg->group_threads ? cfg->group_threads : auto_group(*cfg);
     if (h.fmt == PA_SPIN_MSC32 || h.fmt == PA_SPIN_REPLICA8) h.gt = 1;  // not thread groups
-    if (h.fmt == PA_SPIN_BITS32 && (s.N / 64) % h.gt) return fail(PA_EINVAL);
+    if (h.fmt == PA_SPIN_BITS32 && (s.N / 64) % h.gt) {
+        // several threads per word: square lattice, at most 8 per word, warp groups
+        const int wp = s.N / 64;
+        if (h.dim != 2 || h.gt > 32 || h.gt % wp || h.gt / wp > 8) return fail(PA_EINVAL);
+    }
     h.R = cfg->R;
     h.cap = s.cap;
     h.ntiles = (int)s.ntiles;
@@ -874,6 +899,7 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     h.potts_q = cfg->potts_q;
     h.estep = cfg->potts_q ? 1 : 4;
     h.eoff = (long long)h.dim * s.N;  // Ising dim N; Potts (square lattice) 2N
+    c->small_rs = s.cap <= pa::kSmallCap;
     const size_t N1 = (size_t)s.nlev;
     pa_status st = PA_OK;
 #define PA_ALLOC(p, n)                            \
@@ -2207,6 +2233,7 @@ extern "C" pa_status pa_restore(pa_ctx* c, const void* host_buf, size_t n)
     c->enq_step = i;
     c->done = hd.done != 0;
     c->failed = PA_OK;
+    c->stats_pending = false;
     if (c->adaptive && !c->done) PA_TRY(enqueue_readback(c));
     return PA_OK;
 }

@@ -34,6 +34,7 @@ namespace pa {
 constexpr int kTile = 1024;            // replicas per copy-count tile
 constexpr int kTileThreads = 256;      // 4 replicas (one Philox block) per thread
 constexpr int kOneCta = 1024;          // threads of the per-run single-CTA kernels
+constexpr long long kSmallCap = 16384; // populations resampled by one CTA in one launch
 
 // device status word values (mirror pa_status)
 constexpr int kStatusCapacity = -3;
@@ -179,6 +180,9 @@ cudaError_t launch_parent(const RunDev* d_run, const RunDev& h, const Launch& ln
 cudaError_t launch_resample(const ResampleArgs& a, int tiles, cudaStream_t s);
 cudaError_t launch_sweep(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s);
 cudaError_t launch_stats(const RunDev* d_run, const RunDev& h, int step, cudaStream_t s);
+// statistics of step-1 (optional), tables, copy numbers, offsets and parents
+// of step `step` in one single-CTA launch (capacity <= kSmallCap)
+cudaError_t launch_resample_small(const RunDev& h, int step, bool with_stats, cudaStream_t s);
 cudaError_t launch_rng_peak(long long blocks, uint32_t* sink, int grid, int threads, cudaStream_t s);
 cudaError_t launch_pipe_peak(int pipe, long long iters, uint32_t* sink, int grid, int threads, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint32_t* out, cudaStream_t s);

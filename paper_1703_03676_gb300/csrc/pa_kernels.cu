@@ -130,12 +130,12 @@ __device__ __forceinline__ uint32_t accept_bit(uint32_t acc, uint32_t x, uint32_
 }
 
 // Bits 4q .. 4q+3 of acc4 (x <= T4-1) and acc8 (x <= T8-1) from Philox
-// block q, then blocks q+1 .. 7
-template <int Q>
+// block c0 + q, then blocks q+1 .. NQ-1
+template <int Q, int NQ = 8>
 __device__ __forceinline__ void accept_blocks(uint32_t& acc4, uint32_t& acc8, unsigned c0, unsigned k, unsigned c2,
                                               uint32_t t4m1, uint32_t t8m1, uint32_t unit, PhiloxKey key)
 {
-    if constexpr (Q < 8) {
+    if constexpr (Q < NQ) {
         const uint4 x = philox10(make_uint4(c2, c0 + Q, kTagSweep, k), key);
         acc4 = accept_bit<4 * Q + 0>(acc4, x.x, t4m1, unit);
         acc8 = accept_bit<4 * Q + 0>(acc8, x.x, t8m1, unit);
@@ -145,7 +145,7 @@ __device__ __forceinline__ void accept_blocks(uint32_t& acc4, uint32_t& acc8, un
         acc8 = accept_bit<4 * Q + 2>(acc8, x.z, t8m1, unit);
         acc4 = accept_bit<4 * Q + 3>(acc4, x.w, t4m1, unit);
         acc8 = accept_bit<4 * Q + 3>(acc8, x.w, t8m1, unit);
-        accept_blocks<Q + 1>(acc4, acc8, c0, k, c2, t4m1, t8m1, unit, key);
+        accept_blocks<Q + 1, NQ>(acc4, acc8, c0, k, c2, t4m1, t8m1, unit, key);
     }
 }
 
@@ -169,6 +169,35 @@ __device__ __forceinline__ uint32_t metropolis_word(uint32_t s, uint32_t same, u
     const uint32_t eq0 = ~(d1 | d2 | d3 | d4);
     uint32_t acc4 = 0, acc8 = 0;
     accept_blocks<0>(acc4, acc8, c0, k, c2, t4m1, t8m1, unit, key);
+    return s ^ (ge2 | (acc4 & ~eq0) | (acc8 & eq0));
+}
+
+// The update of metropolis_word shared by S lanes (small lattices, where a
+// population has too few words to occupy the GPU): lane `sub` of the S
+// evaluates Philox blocks sub*8/S .. (sub+1)*8/S - 1 of the word (counter
+// word 1 = 8w + block, as in metropolis_word) into its bits of the accept
+// words, which the S lanes (adjacent lanes of the group, mask gmask) then
+// OR together. Every lane returns the same new word.
+template <int S>
+__device__ __forceinline__ uint32_t metropolis_word_split(uint32_t s, uint32_t same, uint32_t side, uint32_t up,
+                                                          uint32_t down, unsigned w8, int sub, unsigned k,
+                                                          unsigned c2, uint32_t t4m1, uint32_t t8m1, uint32_t unit,
+                                                          PhiloxKey key, unsigned gmask)
+{
+    constexpr int QPL = 8 / S;  // Philox blocks per lane
+    const uint32_t d1 = s ^ same, d2 = s ^ side, d3 = s ^ up, d4 = s ^ down;
+    const uint32_t a = d1 ^ d2, b = d1 & d2, cc = d3 ^ d4, e = d3 & d4;
+    const uint32_t ge2 = b | e | (a & cc);
+    const uint32_t eq0 = ~(d1 | d2 | d3 | d4);
+    uint32_t acc4 = 0, acc8 = 0;
+    accept_blocks<0, QPL>(acc4, acc8, w8 + (unsigned)(sub * QPL), k, c2, t4m1, t8m1, unit, key);
+    acc4 <<= 4 * QPL * sub;
+    acc8 <<= 4 * QPL * sub;
+#pragma unroll
+    for (int off = 1; off < S; off <<= 1) {
+        acc4 |= __shfl_xor_sync(gmask, acc4, off);
+        acc8 |= __shfl_xor_sync(gmask, acc8, off);
+    }
     return s ^ (ge2 | (acc4 & ~eq0) | (acc8 & eq0));
 }
 
@@ -379,14 +408,29 @@ struct Group {
 // One temperature step of the replica in new slot k (gather of its parent,
 // theta sweeps, measurement, write-back). Every thread of the group calls
 // this, active or not (inactive groups only take part in the syncs).
+// Threads per replica that a bit-packed lattice supports: a power of two
+// dividing the plane's words (each thread owns whole words), or, on the
+// square lattice, 2..8 threads per word (G = S * words per plane <= 32)
+// sharing each word's eight Philox blocks.
+template <int L, int D>
+__host__ __device__ constexpr bool bits_group_ok(int G)
+{
+    constexpr int WP = Lat<L, D>::WP;
+    if (G < 1 || (G & (G - 1))) return false;
+    if (WP % G == 0) return true;
+    return D == 2 && G <= 32 && G % WP == 0 && G / WP <= 8;
+}
+
 template <int L, int G, int D = 2>
 __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long long k, bool active,
                                                 uint32_t* sp, int gl, unsigned* red, unsigned& families)
 {
     using Gm = Lat<L, D>;
     using Gr = Group<G>;
-    constexpr int WPT = Gm::WP / G;  // words per thread per plane
-    static_assert(Gm::WP % G == 0, "group must divide the plane");
+    static_assert(bits_group_ok<L, D>(G), "unsupported threads per replica");
+    constexpr bool kSplit = G > Gm::WP;             // several lanes per word
+    constexpr int S = kSplit ? G / Gm::WP : 1;      // lanes per word
+    constexpr int WPT = kSplit ? 1 : Gm::WP / G;    // words per thread per plane
     const int cur = (step - 1) & 1, nxt = step & 1;
     const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
     uint32_t t12m1 = 0;
@@ -395,6 +439,9 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
     const int theta = r.theta;
     const unsigned u0 = (unsigned)(step - 1) * (unsigned)theta;
     const uint32_t* __restrict__ bonds = r.bonds;
+    // read once: batched runs pass r in global memory, where a load inside
+    // the update loop would be repeated for every word
+    const uint32_t unit = r.unit;
     uint32_t p = 0;
     if (active) {
         p = r.parent[k];
@@ -405,7 +452,22 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
         const unsigned u = u0 + (unsigned)sw;
 #pragma unroll
         for (int c = 0; c < 2; c++) {
-            if (active) {
+            if constexpr (kSplit) {
+                if (active) {
+                    uint32_t* P = sp + c * Gm::WP;
+                    const uint32_t* O = sp + (1 - c) * Gm::WP;
+                    const int w = gl / S, sub = gl - (gl / S) * S;
+                    const unsigned gmask = G == 32 ? 0xffffffffu
+                                                   : ((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1));
+                    uint32_t same, side, up, down;
+                    neighbours<L>(O, c, w, same, side, up, down);
+                    if (bonds) apply_bonds<L>(bonds, c, w, same, side, up, down);
+                    const uint32_t nw = metropolis_word_split<S>(P[w], same, side, up, down, 8u * (unsigned)w, sub,
+                                                                 (unsigned)k, 2u * u + (unsigned)c, t4m1, t8m1,
+                                                                 unit, key, gmask);
+                    if (sub == 0) P[w] = nw;
+                }
+            } else if (active) {
                 uint32_t* P = sp + c * Gm::WP;
                 const uint32_t* O = sp + (1 - c) * Gm::WP;
                 const unsigned c2 = 2u * u + (unsigned)c;
@@ -416,13 +478,13 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
                         uint32_t same, side, up, down, zup, zdn;
                         neighbours3<L>(O, c, w, same, side, up, down, zup, zdn);
                         P[w] = metropolis_word3(P[w], same, side, up, down, zup, zdn, 8u * (unsigned)w,
-                                                (unsigned)k, c2, t4m1, t8m1, t12m1, r.unit, key);
+                                                (unsigned)k, c2, t4m1, t8m1, t12m1, unit, key);
                     } else {
                         uint32_t same, side, up, down;
                         neighbours<L>(O, c, w, same, side, up, down);
                         if (bonds) apply_bonds<L>(bonds, c, w, same, side, up, down);
                         P[w] = metropolis_word(P[w], same, side, up, down, 8u * (unsigned)w, (unsigned)k, c2,
-                                               t4m1, t8m1, r.unit, key);
+                                               t4m1, t8m1, unit, key);
                     }
                 }
             }
@@ -1645,6 +1707,104 @@ __global__ void __launch_bounds__(kOneCta) k_stats_batch(const __grid_constant__
     stats_body(r, step);
 }
 
+// ======================================================== one-CTA resampling
+// For populations of at most kSmallCap slots, the per-step bookkeeping of a
+// run is one launch of one 1024-thread CTA instead of five: optionally the
+// statistics of population i-1 (deferred from the previous step when the
+// whole schedule is enqueued at once), then S and the copy tables (as
+// k_tables), then the copy numbers, their running offsets and the parent
+// list (as k_counts + k_scan + k_parent). The slots are walked in chunks of
+// 4096 (one Philox block of 4 slots per thread, RESAMPLE stream (i, j>>2, 2,
+// 0) as in k_counts); each chunk's exclusive scan is added to the total of
+// the chunks before it, so parent[] gets exactly the same old-slot order.
+// A chunk that would take R_i past the capacity sets the capacity status
+// before any of its parents is written.
+__device__ __forceinline__ void resample_small_body(const RunDev& r, int step)
+{
+    __shared__ unsigned long long s_wsum[kOneCta / 32];
+    __shared__ unsigned long long s_chunk;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    const long long Rp = r.rec[step - 1].R;
+    const int32_t* __restrict__ lev = r.elev[(step - 1) & 1];
+    const PhiloxKey key{r.key[0], r.key[1]};
+    const unsigned long long cap = (unsigned long long)r.cap;
+    unsigned long long base = 0;  // copies of the chunks before this one (same in every thread)
+    bool over = false;
+    for (long long c0 = 0; c0 < Rp; c0 += 4 * kOneCta) {
+        const long long j0 = c0 + 4 * t;
+        unsigned long long cnt[4] = {0ull, 0ull, 0ull, 0ull};
+        if (j0 < Rp) {
+            const uint4 x = philox10(make_uint4((unsigned)step, (unsigned)(j0 >> 2), kTagResample, 0u), key);
+            const unsigned xs[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+            for (int l = 0; l < 4; l++) {
+                const long long j = j0 + l;
+                if (j < Rp) {
+                    const int lv = lev[j];
+                    cnt[l] = (unsigned long long)r.F[lv] + (((unsigned long long)xs[l] < r.U[lv]) ? 1ull : 0ull);
+                }
+            }
+        }
+        const unsigned long long tsum = cnt[0] + cnt[1] + cnt[2] + cnt[3];
+        unsigned long long incl = tsum;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) s_wsum[warp] = incl;
+        __syncthreads();
+        if (warp == 0) {
+            // exclusive scan of the 32 warp totals, and the chunk total
+            const unsigned long long v = s_wsum[lane];
+            unsigned long long w = v;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const unsigned long long y = __shfl_up_sync(0xffffffffu, w, off);
+                if (lane >= off) w += y;
+            }
+            s_wsum[lane] = w - v;
+            if (lane == 31) s_chunk = w;
+        }
+        __syncthreads();
+        const unsigned long long chunk = s_chunk;
+        if (base + chunk > cap) {  // same decision in every thread
+            over = true;
+            break;
+        }
+        unsigned long long o = base + s_wsum[warp] + incl - tsum;
+#pragma unroll
+        for (int l = 0; l < 4; l++) {
+            const long long j = j0 + l;
+            for (unsigned long long c = 0; c < cnt[l]; c++) r.parent[o + c] = (uint32_t)j;
+            o += cnt[l];
+        }
+        base += chunk;
+        __syncthreads();  // s_wsum and s_chunk are rewritten by the next chunk
+    }
+    if (t == 0) {
+        StepDev& rec = r.rec[step];
+        rec.R = over ? 0ll : (long long)base;
+        rec.R_prev = Rp;
+        if (over) *r.status = kStatusCapacity;
+        else if (base == 0) *r.status = kStatusExtinct;
+        *r.work = 0u;
+    }
+}
+
+template <bool kStats>
+__global__ void __launch_bounds__(kOneCta) k_resample_small(const __grid_constant__ RunDev r, int step)
+{
+    if (*r.status) return;
+    if constexpr (kStats) {
+        stats_body(r, step - 1);  // population i-1, deferred from its own step
+        __syncthreads();
+    }
+    tables_body(r, step);
+    __syncthreads();  // F, U and rec[step] are read by the whole CTA below
+    resample_small_body(r, step);
+}
+
 // ======================================================== batched sweep
 // Work items of step `step`, laid out in queue order: one per replica of a
 // run with CTA-wide groups (those come first), ceil(R_i / (replicas per
@@ -1824,11 +1984,11 @@ const void* bits_ptr_L(int gt, bool init)
     constexpr int WP = L * L / 64;
     switch (gt) {
     case 1: return bits_ptr<L, 1>(init);
-    case 2: if constexpr (WP % 2 == 0) return bits_ptr<L, 2>(init); break;
-    case 4: if constexpr (WP % 4 == 0) return bits_ptr<L, 4>(init); break;
-    case 8: if constexpr (WP % 8 == 0) return bits_ptr<L, 8>(init); break;
-    case 16: if constexpr (WP % 16 == 0) return bits_ptr<L, 16>(init); break;
-    case 32: if constexpr (WP % 32 == 0) return bits_ptr<L, 32>(init); break;
+    case 2: if constexpr (bits_group_ok<L, 2>(2)) return bits_ptr<L, 2>(init); break;
+    case 4: if constexpr (bits_group_ok<L, 2>(4)) return bits_ptr<L, 4>(init); break;
+    case 8: if constexpr (bits_group_ok<L, 2>(8)) return bits_ptr<L, 8>(init); break;
+    case 16: if constexpr (bits_group_ok<L, 2>(16)) return bits_ptr<L, 16>(init); break;
+    case 32: if constexpr (bits_group_ok<L, 2>(32)) return bits_ptr<L, 32>(init); break;
     case 256: if constexpr (WP % 256 == 0) return bits_ptr<L, 256>(init); break;
     default: break;
     }
@@ -2022,6 +2182,14 @@ cudaError_t launch_resample(const ResampleArgs& a, int tiles, cudaStream_t s)
     k_scan<<<1, kOneCta, 0, s>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     k_parent<<<tiles, kTile, 0, s>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_resample_small(const RunDev& h, int step, bool with_stats, cudaStream_t s)
+{
+    if (h.cap > kSmallCap) return cudaErrorInvalidValue;
+    if (with_stats) k_resample_small<true><<<1, kOneCta, 0, s>>>(h, step);
+    else k_resample_small<false><<<1, kOneCta, 0, s>>>(h, step);
     return cudaGetLastError();
 }
 

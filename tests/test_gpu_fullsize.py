@@ -1,6 +1,13 @@
 """Full-size checks on the configurations of the paper's workloads, in the
 launch configuration bench.py times.
 
+Step-by-step parity at full population: the oracle's block-parallel form
+(bit-identical to its serial form) runs the first steps of config 2 (L=64,
+R=20000, theta=100, dbeta=0.005, seed 2) and config 3 (L=128, R=50000,
+theta=50, adaptive overlap 0.85, seed 3) beside the engine; after every step
+the whole population, every energy, magnetisation and family, both
+histograms, R_i, S, the step size, the thresholds and the row must agree.
+
 Sampled parity: the oracle computes step 1 from scratch (all initial spins
 and energies, every copy number, the parents) and sweeps only sampled new
 slots; the GPU's spins, energies and families of those slots must match
@@ -11,6 +18,7 @@ recomputed from the final spins, the exact beta = 0 row, and agreement with
 Kaufman's exact finite-lattice results within statistical error.
 """
 import math
+import os
 
 import numpy as np
 import pytest
@@ -71,6 +79,38 @@ def test_config2_step1_sampled_parity():
 def test_config3_step1_sampled_parity():
     """L=128, R=50000, theta=50, adaptive overlap 0.85, seed 3."""
     sampled_step1(128, 50000, 50, 0.0, 3, nsample=12)
+
+
+def stepwise_fullsize(L, R, theta, dbeta, seed, n_steps):
+    from tests._parity import assert_row_close, compare_step
+    pa = PopulationAnnealing(L, R, theta, beta_f=1.0, dbeta=dbeta, seed=seed, overlap=0.85, record_hist=True,
+                             workers=os.cpu_count() or 1)
+    run = eng.PARun(eng.PAConfig(L=L, R=R, theta=theta, beta_f=1.0, dbeta=dbeta, overlap=0.85, seed=seed,
+                                 spin_format=B32, record_histograms=True))
+
+    def check(i):
+        compare_step(run, pa, i)
+        assert_row_close(run.rows()[i], pa.rows[i], f"row {i}")
+        E, M, fam = run.replicas()
+        np.testing.assert_array_equal(E, pa.E, err_msg=f"E step {i}")
+        np.testing.assert_array_equal(M, pa.M, err_msg=f"M step {i}")
+        np.testing.assert_array_equal(fam, pa.fam, err_msg=f"families step {i}")
+        np.testing.assert_array_equal(run.population(), pa.pop, err_msg=f"spins step {i}")
+
+    check(0)
+    for i in range(1, n_steps + 1):
+        assert run.step()
+        pa.step()
+        check(i)
+    run.close()
+
+
+def test_config2_first_10_steps_bit_exact():
+    stepwise_fullsize(64, 20000, 100, 0.005, 2, 10)
+
+
+def test_config3_first_5_steps_bit_exact():
+    stepwise_fullsize(128, 50000, 50, 0.0, 3, 5)
 
 
 def check_run_properties(run, L, R):

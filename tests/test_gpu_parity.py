@@ -13,7 +13,7 @@ import math
 import numpy as np
 import pytest
 
-from tests._parity import assert_row_close, compare_step, fnv1a64, oracle_run
+from tests._parity import REL_TOL, assert_row_close, compare_step, fnv1a64, oracle_run
 
 pytestmark = pytest.mark.gpu
 
@@ -165,9 +165,12 @@ def test_adaptive_parity(L, fmt):
     betas = [0.1, 0.3, 0.45, 0.6]
     m_ref = pa.mhr(betas)
     m_got = run.mhr(betas)
+    # the engine's host loops evaluate Eq. MHReq1 in the oracle's order
+    # (ascending levels, left-to-right sums, libm exp/log): same IEEE results
     for a, b in zip(m_got, m_ref):
         for f in ("e", "C", "betaF_per_N", "S_per_N", "abs_m", "m2", "m4"):
-            assert math.isclose(float(a[f]), b[f], rel_tol=1e-11, abs_tol=1e-13), f
+            x, y = float(a[f]), b[f]
+            assert x == y or math.isclose(x, y, rel_tol=REL_TOL, abs_tol=1e-300), (f, x, y)
     # the exact integer sums behind the magnetisation reweighting
     ms = run.mag_sums()
     for k in range(L * L + 1):
@@ -238,5 +241,6 @@ def test_schedule_reuse_and_weighted_average():
     ref = weighted_average([p.rows for p in oracle_runs])
     for i, g in enumerate(ref):
         for f in ("e", "C", "abs_m", "m2", "m4", "betaF_per_N", "S_per_N"):
-            assert math.isclose(float(comb[f][i]), g[f], rel_tol=1e-11, abs_tol=1e-13), (i, f)
+            x, y = float(comb[f][i]), g[f]
+            assert x == y or math.isclose(x, y, rel_tol=REL_TOL, abs_tol=1e-300), (i, f, x, y)
     r1.close()
