@@ -343,6 +343,51 @@ def sweep_roofline(eng, cfg, stream, dev, runs, clocks, seed0):
     return roof
 
 
+def measured_peaks():
+    """(HBM GB/s, label) from MEASURED_PEAKS.json, else the fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "of measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "of fallback"
+
+
+def gather_roofline(eng, stream, reps=5, warm=3):
+    """The resampling copy alone (pa_gather) on the sizes of the adaptive
+    L = 128, R = 50000 workload, where the two populations (2 x 102 MB)
+    exceed L2: algorithmic bytes = read + write of every new replica
+    (2 x R_i x L^2/8) + its parent index (4 B), over the kernel's device
+    time, against the measured HBM copy bandwidth."""
+    import numpy as np
+    import torch
+    L, R = 128, 50000
+    words = L * L // 32
+    rng = np.random.default_rng(12345)
+    r = rng.choice(4, size=R, p=[0.3, 0.45, 0.2, 0.05])  # copy numbers of a resampling step, mean 1
+    parent = torch.from_numpy(np.repeat(np.arange(R), r).astype(np.int32)).cuda()
+    n_new = parent.numel()
+    src = torch.randint(-2 ** 31, 2 ** 31 - 1, (R * words,), dtype=torch.int32, device="cuda")
+    dst = torch.empty(n_new * words, dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.int32, device="cuda")
+    ts = []
+    for k in range(warm + reps):
+        flush.fill_(k)
+        torch.cuda.synchronize()
+        _, ms = eng.gather(src, parent, words, dst=dst, stream=stream)
+        if k >= warm:
+            ts.append(ms)
+    ms = sorted(ts)[len(ts) // 2]
+    byts = 2.0 * n_new * words * 4 + 4.0 * n_new
+    peak, lab = measured_peaks()
+    gbs = byts / (ms * 1e6)
+    return {"bound": "hbm", "kernel": "k_gather<32> (pa_gather)", "achieved": gbs, "peak": peak, "unit": "GB/s",
+            "frac": gbs / peak, "peak_note": lab + " (MEASURED_PEAKS.json hbm_gbs)" if lab == "of measured"
+            else lab, "algorithmic_bytes_per_launch": byts, "launch_ms": ms, "reps": reps,
+            "traffic": None,
+            "workload": f"resampling copy of L={L} bit-packed replicas ({words * 4} B each), R_(i-1)={R}, "
+                        f"R_i={n_new}, sorted parents with copy numbers 0..3; L2 flushed before each launch"}
+
+
 def run_engine(args):
     import torch
 
@@ -405,8 +450,11 @@ def run_engine(args):
     value = att_all / (t_max * 1e6)
 
     roofline = None
+    gather = None
     if args.profile and args.format == "bits":
         roofline = sweep_roofline(eng, cfg, stream, dev, args.prof_runs, clocks, seed_of(20_000))
+        if WL == DEFAULT_WL and ws == 1:
+            gather = gather_roofline(eng, stream)
 
     # end to end through the public API with host buffers
     e2e = None
@@ -466,7 +514,7 @@ def run_engine(args):
                            "baseline_ref": "paper K80 multi-spin-coded run, 17 s for this workload",
                            "parallelism": f"independent runs x{ws}"},
                 "clocks": clocks, "e2e": e2e, "gpu_launches": launches,
-                "roofline": roofline, "batched": batched, "served": served, "cpu_baseline": cpu,
+                "roofline": roofline, "gather": gather, "batched": batched, "served": served, "cpu_baseline": cpu,
                 "per_step_ms": per_step_ms}
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -436,6 +436,19 @@ pa_status pa_resample_noalloc(const int32_t *dev_levels, int64_t n_old, const ui
                               const uint64_t *dev_U, int64_t n_levels, uint64_t seed, int64_t step,
                               uint32_t *dev_parent, int64_t parent_cap, int64_t *n_new, void *cuda_stream);
 
+/* The replica copy of the resampling step (Sec. 3, the resampling kernel's
+ * copy of each selected replica) as a standalone kernel, for measuring it
+ * against HBM bandwidth (the engine fuses this copy into the sweep's load):
+ * dev_dst[o * words + w] = dev_src[dev_parent[o] * words + w] for
+ * o < n_new, w < words. dev_src holds n_src replicas of `words` uint32
+ * words (words a multiple of 4; dev_src and dev_dst 16-byte aligned, not
+ * overlapping); dev_parent holds n_new old-slot indices. A parent >= n_src is
+ * skipped (nothing read or written for that slot) and the call returns
+ * PA_EINVAL after the copy. Allocates and frees a 4-byte flag. Synchronous
+ * on `cuda_stream`; ms, if not NULL, gets the kernel's device time. */
+pa_status pa_gather(const uint32_t *dev_src, int64_t n_src, const uint32_t *dev_parent, int64_t n_new, int32_t words,
+                    uint32_t *dev_dst, void *cuda_stream, double *ms);
+
 /* Throughput ceiling of the random-number generator alone: a persistent
  * kernel that evaluates Philox4x32-10 on `blocks_per_thread` counters per
  * thread over the whole device and XOR-folds the words (one store per

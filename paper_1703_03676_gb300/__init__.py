@@ -112,6 +112,8 @@ SIGNATURES = [
                                            _P, ctypes.POINTER(_P)]),
     ("pa_weighted_average", ctypes.c_int, [_P, ctypes.c_int32, ctypes.c_int64, ctypes.c_int32, _P]),
     ("pa_serve", ctypes.c_int, [_P, ctypes.c_int32, _P, _P, _P]),
+    ("pa_gather", ctypes.c_int, [_P, ctypes.c_int64, _P, ctypes.c_int64, ctypes.c_int32, _P, _P,
+                                 ctypes.POINTER(ctypes.c_double)]),
     ("pa_measure_rng_peak", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     ("pa_measure_pipe_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     ("pa_resample", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64, _P,
@@ -575,6 +577,25 @@ def measure_pipe_peak(pipe: int, iters: int = 4096, stream=None) -> float:
     _check(lib().pa_measure_pipe_peak(pipe, iters, ctypes.c_void_p(sink.data_ptr()), _stream_handle(stream),
                                       ctypes.byref(out)), "pa_measure_pipe_peak")
     return out.value
+
+
+def gather(src, parent, words: int, dst=None, stream=None):
+    """Standalone replica copy (pa_gather): src is a CUDA int32 tensor of
+    n_src * words words, parent a CUDA int32 tensor of old-slot indices.
+    Returns (dst, device ms)."""
+    import torch
+    assert src.is_cuda and src.dtype == torch.int32 and src.is_contiguous() and src.numel() % words == 0
+    assert parent.is_cuda and parent.dtype == torch.int32 and parent.is_contiguous()
+    n_new = parent.numel()
+    if dst is None:
+        dst = torch.empty(n_new * words, dtype=torch.int32, device=src.device)
+    assert dst.is_cuda and dst.dtype == torch.int32 and dst.numel() >= n_new * words
+    torch.cuda.current_stream().synchronize()
+    ms = ctypes.c_double()
+    _check(lib().pa_gather(ctypes.c_void_p(src.data_ptr()), src.numel() // words, ctypes.c_void_p(parent.data_ptr()),
+                           n_new, words, ctypes.c_void_p(dst.data_ptr()), _stream_handle(stream), ctypes.byref(ms)),
+           "pa_gather")
+    return dst, ms.value
 
 
 RESAMPLE_NOALLOC_MAX_OLD = 262144

@@ -885,7 +885,7 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     if (h.fmt == PA_SPIN_BITS32 && (s.N / 64) % h.gt) {
         // several threads per word: square lattice, at most 8 per word, warp groups
         const int wp = s.N / 64;
-        if (h.dim != 2 || h.gt > 32 || h.gt % wp || h.gt / wp > 8) return fail(PA_EINVAL);
+        if (dim_of(*cfg) != 2 || h.gt > 32 || h.gt % wp || h.gt / wp > 8) return fail(PA_EINVAL);
     }
     h.R = cfg->R;
     h.cap = s.cap;
@@ -1548,6 +1548,42 @@ pa_status pa_resample_noalloc(const int32_t* lev, int64_t n_old, const uint32_t*
     PA_CUDA(cudaStreamSynchronize(s));
     *n_new = hn;
     return hs != 0 ? (pa_status)hs : PA_OK;
+}
+
+pa_status pa_gather(const uint32_t* src, int64_t n_src, const uint32_t* parent, int64_t n_new, int32_t words,
+                    uint32_t* dst, void* stream, double* ms)
+{
+    if (!src || !parent || !dst || n_src < 1 || n_new < 0 || words < 4 || words % 4 ||
+        ((uintptr_t)src | (uintptr_t)dst) % 16)
+        return PA_EINVAL;
+    if (n_new == 0) {
+        if (ms) *ms = 0.0;
+        return PA_OK;
+    }
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0, sms = 0;
+    PA_CUDA(cudaGetDevice(&dev));
+    PA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    unsigned* bad = nullptr;
+    PA_CUDA(cudaMalloc(&bad, 4));
+    cudaEvent_t a = nullptr, b = nullptr;
+    unsigned hbad = 0;
+    cudaError_t e = cudaMemsetAsync(bad, 0, 4, s);
+    if (e == cudaSuccess) e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e == cudaSuccess) e = cudaEventRecord(a, s);
+    if (e == cudaSuccess) e = pa::launch_gather(src, parent, n_new, n_src, words, dst, bad, sms * 8, s);
+    if (e == cudaSuccess) e = cudaEventRecord(b, s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hbad, bad, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    float t = 0.f;
+    if (e == cudaSuccess && ms) e = cudaEventElapsedTime(&t, a, b);
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+    cudaFree(bad);
+    if (e != cudaSuccess) return from_cuda(e, __LINE__);
+    if (ms) *ms = (double)t;
+    return hbad ? PA_EINVAL : PA_OK;
 }
 
 pa_status pa_measure_rng_peak(int64_t blocks_per_thread, uint32_t* sink, void* stream, double* words_per_ns)

@@ -186,6 +186,8 @@ cudaError_t launch_resample_small(const RunDev& h, int step, bool with_stats, cu
 cudaError_t launch_rng_peak(long long blocks, uint32_t* sink, int grid, int threads, cudaStream_t s);
 cudaError_t launch_pipe_peak(int pipe, long long iters, uint32_t* sink, int grid, int threads, cudaStream_t s);
 cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint32_t* out, cudaStream_t s);
+cudaError_t launch_gather(const uint32_t* src, const uint32_t* parent, long long n_new, long long n_src, int words,
+                          uint32_t* dst, unsigned* bad, int grid, cudaStream_t s);
 
 struct BatchLaunch {
     int tiles;                // copy-count tiles over all runs

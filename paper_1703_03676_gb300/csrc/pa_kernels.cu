@@ -1670,22 +1670,28 @@ __device__ __forceinline__ void stats_body(const RunDev& r, int step)
         wmax[warp] = kmax;
     }
     __syncthreads();
+    // warps 0..4 each total one moment over the 32 warp partials (exact
+    // integer sums); warp 5 the occupied range
+    StepDev& rec = r.rec[step];
+    if (warp < 5) {
+        const I128 p = to_i128(warp_sum128(ws[warp][lane]));
+        if (lane == 0) {
+            rec.sums[2 * warp] = p.lo;
+            rec.sums[2 * warp + 1] = p.hi;
+        }
+    } else if (warp == 5) {
+        int mn = wmin[lane], mx = wmax[lane];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+            mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+        }
+        if (lane == 0) {
+            rec.kmin = mn;
+            rec.kmax = mx;
+        }
+    }
     if (t == 0) {
-        StepDev& rec = r.rec[step];
-        for (int q = 0; q < 5; q++) {
-            __int128 a = 0;
-            for (int w = 0; w < kOneCta / 32; w++) a += ws[q][w];
-            const I128 p = to_i128(a);
-            rec.sums[2 * q] = p.lo;
-            rec.sums[2 * q + 1] = p.hi;
-        }
-        int mn = 0x7fffffff, mx = -1;
-        for (int w = 0; w < kOneCta / 32; w++) {
-            mn = min(mn, wmin[w]);
-            mx = max(mx, wmax[w]);
-        }
-        rec.kmin = mn;
-        rec.kmax = mx;
         if (step == 0) {
             rec.R = r.R;
             rec.R_prev = r.R;
@@ -1925,6 +1931,50 @@ __global__ void __launch_bounds__(256) k_sweep_batch(const __grid_constant__ Bat
         default: break;
         }
     }
+}
+
+// ======================================================== standalone gather
+// The replica copy of the resampling step (the paper's resampleKer) on its
+// own: new slot o receives the words of old slot parent[o]. The engine fuses
+// this copy into the sweep's shared-memory load; this kernel measures the
+// copy against HBM bandwidth. LPR lanes copy one replica in 16-byte vectors
+// with streaming (evict-first) loads and stores; a parent outside the source
+// is skipped and counted in *bad.
+template <int LPR>
+__global__ void __launch_bounds__(256) k_gather(const uint4* __restrict__ src, const uint32_t* __restrict__ parent,
+                                                long long n_new, long long n_src, int w4, uint4* __restrict__ dst,
+                                                unsigned* bad)
+{
+    constexpr int RPW = 32 / LPR;  // replicas per warp at a time
+    const int lane = threadIdx.x & 31, sub = lane / LPR, l = lane % LPR;
+    const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const long long warps = ((long long)gridDim.x * blockDim.x) >> 5;
+    for (long long o = warp * RPW + sub; o < n_new; o += warps * RPW) {
+        const uint32_t p = parent[o];
+        if ((long long)p >= n_src) {
+            if (l == 0) atomicAdd(bad, 1u);
+            continue;
+        }
+        const uint4* s = src + (size_t)p * (size_t)w4;
+        uint4* d = dst + (size_t)o * (size_t)w4;
+        for (int i = l; i < w4; i += LPR) __stcs(d + i, __ldcs(s + i));
+    }
+}
+
+cudaError_t launch_gather(const uint32_t* src, const uint32_t* parent, long long n_new, long long n_src, int words,
+                          uint32_t* dst, unsigned* bad, int grid, cudaStream_t s)
+{
+    if (words < 4 || words % 4 || grid < 1) return cudaErrorInvalidValue;
+    const int w4 = words / 4;
+    const uint4* s4 = reinterpret_cast<const uint4*>(src);
+    uint4* d4 = reinterpret_cast<uint4*>(dst);
+    if (w4 >= 32) k_gather<32><<<grid, 256, 0, s>>>(s4, parent, n_new, n_src, w4, d4, bad);
+    else if (w4 >= 16) k_gather<16><<<grid, 256, 0, s>>>(s4, parent, n_new, n_src, w4, d4, bad);
+    else if (w4 >= 8) k_gather<8><<<grid, 256, 0, s>>>(s4, parent, n_new, n_src, w4, d4, bad);
+    else if (w4 >= 4) k_gather<4><<<grid, 256, 0, s>>>(s4, parent, n_new, n_src, w4, d4, bad);
+    else if (w4 >= 2) k_gather<2><<<grid, 256, 0, s>>>(s4, parent, n_new, n_src, w4, d4, bad);
+    else k_gather<1><<<grid, 256, 0, s>>>(s4, parent, n_new, n_src, w4, d4, bad);
+    return cudaGetLastError();
 }
 
 // ======================================================== Philox test kernel
