@@ -60,7 +60,8 @@ def workload_label():
         steps = f"dbeta={WL['dbeta']:g} ({n} steps)"
     else:
         steps = "adaptive dbeta (histogram overlap 0.85, one host decision per step)"
-    return f"plain PA, {lattice}, R={WL['R']}, theta={WL['theta']}, beta 0->1 {steps}, bit-packed spins"
+    return (f"plain PA, {lattice}, R={WL['R']}, theta={WL['theta']}, beta 0->{WL['beta_f']:g} {steps}, "
+            f"bit-packed spins")
 
 
 def sites():
@@ -615,6 +616,22 @@ def measure_served(eng, n: int, rdiv: int, beta_f: float, active: int, budget_gb
             "max_active": active, "hbm_budget_bytes": budget}
 
 
+def run_gather(args):
+    """The resampling copy alone (--workload gather, see gather_roofline)."""
+    import torch
+
+    import paper_1703_03676_gb300 as eng
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    g = gather_roofline(eng, stream, reps=args.steps, warm=args.warmup)
+    line = {"metric": "resampling copy bandwidth", "workload": "gather", "value": g["achieved"], "unit": "GB/s",
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": g["launch_ms"],
+            "higher_is_better": True, "roofline": g, "data": "synthetic"}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_batched(args):
     """The batched workload alone (--workload batched): the config-4 draw or
     the 64 config-1-shaped runs."""
@@ -662,7 +679,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
-    ap.add_argument("--workload", choices=["default", "batched", "served"], default="default")
+    ap.add_argument("--workload", choices=["default", "batched", "served", "gather"], default="default")
     ap.add_argument("--format", choices=["bits", "msc", "int8", "replica"], default="bits",
                     help="spin format of the default workload: bits (Philox per attempt, the reference contract), "
                          "msc (the paper's multi-spin coding with a Philox-seeded LCG), int8")
@@ -670,6 +687,8 @@ def main():
     ap.add_argument("--R", type=int, default=None, help="override the default workload's population")
     ap.add_argument("--theta", type=int, default=None, help="override the default workload's sweeps per step")
     ap.add_argument("--dbeta", type=float, default=None, help="override the default workload's step size")
+    ap.add_argument("--beta-f", type=float, default=None,
+                    help="override the default workload's final inverse temperature (a labelled prefix)")
     ap.add_argument("--dim", type=int, choices=[2, 3], default=None,
                     help="3: the simple cubic L x L x L lattice instead of the square one")
     ap.add_argument("--potts-q", type=int, default=None,
@@ -706,7 +725,7 @@ def main():
         ap.error("--warmup must be >= 3")
     if args.potts_q and args.format != "int8":
         ap.error("--potts-q needs --format int8")
-    for k in ("L", "R", "theta", "dbeta", "dim", "potts_q"):  # labelled variants of the default workload
+    for k in ("L", "R", "theta", "dbeta", "beta_f", "dim", "potts_q"):  # labelled variants of the default workload
         if getattr(args, k) is not None:
             WL[k] = getattr(args, k)
     if args.impl == "reference":
@@ -715,6 +734,8 @@ def main():
         return run_batched(args)
     if args.workload == "served":
         return run_served(args)
+    if args.workload == "gather":
+        return run_gather(args)
     return run_engine(args)
 
 

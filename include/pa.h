@@ -111,7 +111,13 @@ typedef struct {
                                (levels m = M); Z at beta0 = 0 is q^N. The
                                update proposes a uniform other state and
                                accepts by Metropolis on dE = n(s) - n(s')   */
-    int32_t reserved[1];    /* must be 0                                          */
+    int32_t block_warps;    /* warps per CTA of the warp-group sweeps (group_threads
+                               <= 32): 1, 2, 4 or 8; 0 -> 8 (fewer when one
+                               warp's replicas need much shared memory). With
+                               group_threads == 0 and block_warps == 0 the
+                               launch shape is the one pa_autotune chose for
+                               runs like this one in this process, if any,
+                               else a fixed rule                            */
 } pa_config;
 
 /* One output row (Sec. 3 "Further optimization and parameters": beta, e, C,
@@ -301,6 +307,51 @@ const char *pa_strerror(pa_status s);
 /* Text of the last CUDA failure seen by a call on this thread (the CUDA
  * error name and the engine source line), or "" if none. */
 const char *pa_last_error_message(void);
+
+/* ---- autotuner ------------------------------------------------------------
+ * The sweep's launch shape (threads per replica, warps per CTA) changes
+ * only the speed of a run, never its results. pa_autotune times every shape
+ * a run like cfg accepts on a two-step probe with cfg's lattice, format,
+ * model and population size, and keeps the fastest; later pa_create calls in
+ * the process whose config leaves the shape open (group_threads == 0 and
+ * block_warps == 0) and that share the choice's key use it. Batches tune
+ * their runs' threads per replica the same way (key batched = 1). Not part
+ * of the paper (its kernels have a fixed shape): a deployment aid. */
+typedef struct {
+    int32_t L, spin_format, dim, potts_q;
+    int32_t r_log2;         /* floor(log2 R): populations within a factor of 2 share a choice */
+    int32_t batched;        /* 1: runs of a batch (the batched sweep), 0: runs alone */
+    int32_t sms;            /* multiprocessors of the device                     */
+    char gpu[64];           /* device name (no '|' or newline), NUL-terminated   */
+} pa_tune_key;
+
+typedef struct {
+    int32_t group_threads;  /* chosen threads per replica                         */
+    int32_t block_warps;    /* chosen warps per CTA (0: the default)              */
+    double attempts_per_ns; /* sweep rate of the choice on its probe              */
+    int32_t candidates;     /* shapes timed; 0 when read from a cache             */
+    int32_t pad;
+} pa_tune_choice;
+
+/* The key of runs like cfg on the current device (name and SM count from
+ * the CUDA runtime). Errors: PA_EINVAL, PA_ECUDA (no device). */
+pa_status pa_tune_key_of(const pa_config *cfg, int32_t batched, pa_tune_key *out);
+
+/* Tune (or recall) the launch shape of runs like cfg. The choice is kept
+ * in the process and, with a cache file (cache_path, else the environment
+ * variable PA_TUNE_CACHE, else none), read from and written to that text
+ * file: one line per key, "v1|L|format|dim|potts_q|r_log2|batched|sms|gpu|
+ * group_threads|block_warps|attempts_per_ns"; a known key is returned
+ * without probing (candidates = 0). The probes allocate, run and free small
+ * runs on `cuda_stream`. */
+pa_status pa_autotune(const pa_config *cfg, const char *cache_path, void *cuda_stream, pa_tune_choice *out);
+
+/* The cache file alone (host only, no device needed): store replaces the
+ * line of the same key (written through a temporary file and a rename);
+ * lookup sets *found to 1 and fills *out if the key is present, else 0.
+ * Malformed lines are ignored. PA_EINVAL for a bad path, key or choice. */
+pa_status pa_tune_cache_store(const char *path, const pa_tune_key *key, const pa_tune_choice *choice);
+pa_status pa_tune_cache_lookup(const char *path, const pa_tune_key *key, pa_tune_choice *out, int32_t *found);
 
 /* ---- batches of independent runs ---------------------------------------
  * Many independent fixed-schedule runs (batched runs; Sec. 2.2 notes

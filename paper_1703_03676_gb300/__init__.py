@@ -41,7 +41,18 @@ class _Config(ctypes.Structure):
                 ("overlap", ctypes.c_double), ("seed", ctypes.c_uint64), ("spin_format", ctypes.c_int32),
                 ("record_histograms", ctypes.c_int32), ("capacity", ctypes.c_int64),
                 ("group_threads", ctypes.c_int32), ("use_graph", ctypes.c_int32), ("profile", ctypes.c_int32),
-                ("dim", ctypes.c_int32), ("potts_q", ctypes.c_int32), ("reserved", ctypes.c_int32 * 1)]
+                ("dim", ctypes.c_int32), ("potts_q", ctypes.c_int32), ("block_warps", ctypes.c_int32)]
+
+
+class _TuneKey(ctypes.Structure):
+    _fields_ = [("L", ctypes.c_int32), ("spin_format", ctypes.c_int32), ("dim", ctypes.c_int32),
+                ("potts_q", ctypes.c_int32), ("r_log2", ctypes.c_int32), ("batched", ctypes.c_int32),
+                ("sms", ctypes.c_int32), ("gpu", ctypes.c_char * 64)]
+
+
+class _TuneChoice(ctypes.Structure):
+    _fields_ = [("group_threads", ctypes.c_int32), ("block_warps", ctypes.c_int32),
+                ("attempts_per_ns", ctypes.c_double), ("candidates", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
 class _Obs(ctypes.Structure):
@@ -86,6 +97,11 @@ SIGNATURES = [
     ("pa_mag_sums", ctypes.c_int, [_P, _P, ctypes.c_int64]),
     ("pa_phase_times", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_double), _I64P]),
     ("pa_kernel_launches", ctypes.c_int, [_P, _I64P]),
+    ("pa_tune_key_of", ctypes.c_int, [ctypes.POINTER(_Config), ctypes.c_int32, ctypes.POINTER(_TuneKey)]),
+    ("pa_autotune", ctypes.c_int, [ctypes.POINTER(_Config), ctypes.c_char_p, _P, ctypes.POINTER(_TuneChoice)]),
+    ("pa_tune_cache_store", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_TuneKey), ctypes.POINTER(_TuneChoice)]),
+    ("pa_tune_cache_lookup", ctypes.c_int, [ctypes.c_char_p, ctypes.POINTER(_TuneKey), ctypes.POINTER(_TuneChoice),
+                                            ctypes.POINTER(ctypes.c_int32)]),
     ("pa_launch_shape", ctypes.c_int, [_P, ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_int32),
                                        ctypes.POINTER(ctypes.c_int32)]),
     ("pa_footprint_bytes", ctypes.c_size_t, [ctypes.POINTER(_Config)]),
@@ -175,6 +191,7 @@ class PAConfig:
     profile: bool = False
     dim: int = 2                 # 3: the L x L x L simple cubic lattice (bit-packed, L in 8..64)
     potts_q: int = 0             # 2..8: the q-state Potts model (SPIN_INT8, square lattice)
+    block_warps: int = 0         # warps per CTA of warp-group sweeps (1, 2, 4, 8; 0: default/tuned)
 
     @property
     def n_sites(self) -> int:
@@ -201,6 +218,7 @@ class PAConfig:
         c.profile = int(bool(self.profile))
         c.dim = self.dim
         c.potts_q = self.potts_q
+        c.block_warps = self.block_warps
         return c
 
 
@@ -596,6 +614,58 @@ def gather(src, parent, words: int, dst=None, stream=None):
                            n_new, words, ctypes.c_void_p(dst.data_ptr()), _stream_handle(stream), ctypes.byref(ms)),
            "pa_gather")
     return dst, ms.value
+
+
+TUNE_KEY_FIELDS = ["L", "spin_format", "dim", "potts_q", "r_log2", "batched", "sms", "gpu"]
+
+
+def _tune_key(d: dict) -> _TuneKey:
+    k = _TuneKey()
+    for f in TUNE_KEY_FIELDS[:-1]:
+        setattr(k, f, int(d[f]))
+    k.gpu = d["gpu"].encode() if isinstance(d["gpu"], str) else d["gpu"]
+    return k
+
+
+def _choice_dict(c: _TuneChoice) -> dict:
+    return {"group_threads": c.group_threads, "block_warps": c.block_warps,
+            "attempts_per_ns": c.attempts_per_ns, "candidates": c.candidates}
+
+
+def tune_key(cfg: PAConfig, batched: bool = False) -> dict:
+    """The autotuner's key of runs like cfg on the current device."""
+    k = _TuneKey()
+    c = cfg._c()
+    _check(lib().pa_tune_key_of(ctypes.byref(c), int(bool(batched)), ctypes.byref(k)), "pa_tune_key_of")
+    return {f: (getattr(k, f).decode() if f == "gpu" else getattr(k, f)) for f in TUNE_KEY_FIELDS}
+
+
+def autotune(cfg: PAConfig, cache_path=None, stream=None) -> dict:
+    """Tune (or recall) the sweep's launch shape for runs like cfg
+    (pa_autotune); later runs created with group_threads = block_warps = 0
+    and the same key use the choice."""
+    c = cfg._c()
+    out = _TuneChoice()
+    path = None if cache_path is None else os.fsencode(cache_path)
+    _check(lib().pa_autotune(ctypes.byref(c), path, _stream_handle(stream), ctypes.byref(out)), "pa_autotune")
+    return _choice_dict(out)
+
+
+def tune_cache_store(path, key: dict, choice: dict):
+    """Write one choice into a tuner cache file (host only)."""
+    c = _TuneChoice(int(choice["group_threads"]), int(choice["block_warps"]), float(choice["attempts_per_ns"]), 0, 0)
+    k = _tune_key(key)
+    _check(lib().pa_tune_cache_store(os.fsencode(path), ctypes.byref(k), ctypes.byref(c)), "pa_tune_cache_store")
+
+
+def tune_cache_lookup(path, key: dict):
+    """The choice stored for key in a tuner cache file, or None (host only)."""
+    k = _tune_key(key)
+    c = _TuneChoice()
+    found = ctypes.c_int32()
+    _check(lib().pa_tune_cache_lookup(os.fsencode(path), ctypes.byref(k), ctypes.byref(c), ctypes.byref(found)),
+           "pa_tune_cache_lookup")
+    return _choice_dict(c) if found.value else None
 
 
 RESAMPLE_NOALLOC_MAX_OLD = 262144

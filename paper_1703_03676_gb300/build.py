@@ -19,7 +19,7 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(BUILD, "libpa_gb300.so")
-SOURCES = ["pa_kernels.cu", "pa_engine.cu", "pa_peaks.cu"]
+SOURCES = ["pa_kernels.cu", "pa_engine.cu", "pa_peaks.cu", "pa_tune.cu"]
 HEADERS = ["pa_internal.cuh", os.path.join("..", "..", "include", "pa.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -181,7 +181,8 @@ pa_status validate(const pa_config& c)
     if (c.capacity < 0 || (c.capacity > 0 && c.capacity < c.R)) return PA_EINVAL;
     if (c.group_threads < 0 || (c.group_threads & (c.group_threads - 1))) return PA_EINVAL;
     if (c.group_threads > 32 && !(c.group_threads == 256 && c.spin_format == PA_SPIN_BITS32)) return PA_EINVAL;
-    if (c.reserved[0]) return PA_EINVAL;
+    if (c.block_warps != 0 && c.block_warps != 1 && c.block_warps != 2 && c.block_warps != 4 && c.block_warps != 8)
+        return PA_EINVAL;
     if (c.dim != 0 && c.dim != 2 && c.dim != 3) return PA_EINVAL;
     if (c.potts_q != 0 && (c.potts_q < 2 || c.potts_q > 8 || c.spin_format != PA_SPIN_INT8 || c.dim == 3))
         return PA_EINVAL;
@@ -214,12 +215,30 @@ int words_of(const pa_config& c)
     return (int)(((N + 15) / 16) * 4);  // bytes padded to 16, in words
 }
 
+// Byte spins of the square-lattice ferromagnet on a lattice the bit-packed
+// kernels support are swept by those kernels (each replica packed into
+// shared memory on load, unpacked on store); the population stays one byte
+// per site in HBM.
+bool packed_bytes(const pa_config& c, bool couplings)
+{
+    return c.spin_format == PA_SPIN_INT8 && c.potts_q == 0 && dim_of(c) == 2 && !couplings && bits_L_ok(c.L);
+}
+
+// a thread count the bit-packed square-lattice kernels accept for L
+bool bits_group_valid(int L, int g)
+{
+    const int wp = L * L / 64;
+    if (g < 1 || (g & (g - 1))) return false;
+    if (g == 256) return wp % 256 == 0;
+    return wp % g == 0 || (g <= 32 && g % wp == 0 && g / wp <= 8);
+}
+
 // threads per replica: enough to fill the device, a power of two dividing
 // the plane's words (bit-packed) or the Philox blocks per plane (bytes)
-int auto_group(const pa_config& c)
+int auto_group(const pa_config& c, bool bits_kernel)
 {
     const long long N = sites_of(c);
-    if (c.spin_format == PA_SPIN_BITS32) {
+    if (bits_kernel) {
         const long long wp = N / 64;
         // L >= 128: one replica per 256-thread CTA (measured faster than warp
         // groups: 1431 vs 1376 attempts/ns at L = 128, 1382 vs 1267 at L = 256)
@@ -880,7 +899,14 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     h.wp = s.N / 64;
     h.theta = cfg->theta;
     h.fmt = cfg->spin_format;
-    h.gt = cfg->group_threads ? cfg->group_threads : auto_group(*cfg);
+    int tuned_g = 0, tuned_bw = 0;
+    if (!cfg->group_threads && !cfg->block_warps && !pa::tuned_shape(*cfg, 0, &tuned_g, &tuned_bw)) tuned_g = 0;
+    const int want_g = cfg->group_threads ? cfg->group_threads : tuned_g;
+    h.packed = packed_bytes(*cfg, Jr != nullptr) ? 1 : 0;
+    if (h.packed && want_g && !bits_group_valid(cfg->L, want_g))
+        h.packed = 0;  // a group shape only the byte kernels have
+    h.gt = want_g ? want_g : auto_group(*cfg, h.packed || h.fmt == PA_SPIN_BITS32);
+    h.bw = cfg->block_warps ? cfg->block_warps : tuned_bw;
     if (h.fmt == PA_SPIN_MSC32 || h.fmt == PA_SPIN_REPLICA8) h.gt = 1;  // not thread groups
     if (h.fmt == PA_SPIN_BITS32 && (s.N / 64) % h.gt) {
         // several threads per word: square lattice, at most 8 per word, warp groups
@@ -1664,73 +1690,6 @@ struct pa_batch {
 
 namespace {
 
-// Autotuned threads per replica for the batched sweep, per (L, SM count):
-// the candidate with the fastest sweep on a probe run. Results never depend
-// on the choice; only speed does.
-std::mutex g_tune_mu;
-std::map<long long, int> g_tuned;
-
-int batch_candidates(int L, int out[8])
-{
-    int n = 0;
-    for (int g : {1, 2, 4, 8, 16, 32, 256})
-        if (pa::batch_supports(L, g)) out[n++] = g;
-    return n;
-}
-
-pa_status tune_group(int L, void* stream, int* out)
-{
-    int dev = 0, sms = 0;
-    PA_CUDA(cudaGetDevice(&dev));
-    PA_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    const long long key = (long long)L * 100000 + sms;
-    {
-        std::lock_guard<std::mutex> g(g_tune_mu);
-        auto it = g_tuned.find(key);
-        if (it != g_tuned.end()) {
-            *out = it->second;
-            return PA_OK;
-        }
-    }
-    int cand[8];
-    const int nc = batch_candidates(L, cand);
-    if (nc == 0) return PA_EINVAL;
-    // one population for every candidate (the same work), four rounds of the
-    // smallest group's persistent warps (16 warps per SM)
-    const long long R_probe = std::max(2048ll, 4ll * sms * 16 * (32 / std::min(cand[0], 32)));
-    int best = cand[0];
-    double best_ms = 1e300;
-    for (int i = 0; i < nc && nc > 1; i++) {
-        pa_config pc;
-        pa_config_default(&pc);
-        pc.L = L;
-        pc.R = R_probe;
-        pc.theta = 20;
-        pc.beta_f = 0.02;
-        pc.dbeta = 0.01;
-        pc.spin_format = PA_SPIN_BITS32;
-        pc.group_threads = cand[i];
-        pc.use_graph = 0;
-        pc.profile = 1;
-        pa_ctx* t = nullptr;
-        PA_TRY(pa_create(&pc, stream, &t));
-        pa_status st = pa_run(t);
-        double ms[7];
-        int64_t n[7];
-        if (st == PA_OK) st = pa_phase_times(t, ms, n);
-        pa_destroy(t);
-        PA_TRY(st);
-        if (ms[4] < best_ms) {
-            best_ms = ms[4];
-            best = cand[i];
-        }
-    }
-    std::lock_guard<std::mutex> g(g_tune_mu);
-    g_tuned[key] = best;
-    *out = best;
-    return PA_OK;
-}
-
 // host side of a fixed schedule: the betas of every step the graph runs
 void advance_fixed(pa_ctx* c)
 {
@@ -1849,8 +1808,10 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
         pa_config c = cfgs[i];
         if (c.profile) b->profile = true;
         if (!c.group_threads) {
-            const pa_status ts = tune_group(c.L, b->stream, &c.group_threads);
+            pa_tune_choice tc{};
+            const pa_status ts = pa::autotune_impl(&c, 1, nullptr, b->stream, &tc);
             if (ts != PA_OK) return fail(ts);
+            c.group_threads = tc.group_threads;
         }
         c.use_graph = 0;
         c.profile = 0;

@@ -58,7 +58,9 @@ struct RunDev {
     int wp;                   // bit-packed words per colour plane (N/64)
     int theta;
     int fmt;                  // 0 byte spins, 1 bit-packed
+    int packed;               // byte spins swept by the bit-packed kernels (packed in shared memory)
     int gt;                   // threads per replica in the sweep
+    int bw;                   // warps per CTA of a warp-group sweep (0: 8)
     long long R, cap;
     const unsigned* key;      // Philox key (2 words) in device memory
     int ntiles;               // copy-count tiles covering cap
@@ -200,6 +202,13 @@ cudaError_t plan_batch(const BatchDev& b, BatchLaunch* ln);
 cudaError_t launch_batch_step(const BatchDev& b, const BatchLaunch& ln, int step, cudaStream_t s, int phase,
                               int* phase_of_launch);
 bool batch_supports(int L, int gt);
+
+#ifdef PA_GB300_H
+// Autotuner (pa_tune.cu): the launch shape chosen in this process for runs
+// like cfg (batched != 0: the batched sweep), and the tuner itself.
+bool tuned_shape(const pa_config& cfg, int batched, int* G, int* bw);
+pa_status autotune_impl(const pa_config* cfg, int batched, const char* cache_path, void* stream, pa_tune_choice* out);
+#endif
 
 // Sweep launch shape: persistent CTAs for this run (group threads gt).
 cudaError_t plan_sweep(const RunDev& h, Launch* ln);

@@ -309,6 +309,60 @@ __device__ __forceinline__ void copy_words(uint32_t* __restrict__ dst, const uin
     }
 }
 
+// A replica stored one byte per site (0/1, colour plane 0 then plane 1,
+// site b of a plane at byte b) and the same replica bit-packed (site b of a
+// plane at bit b&31 of word b>>5): word i of the packed image holds bytes
+// 32i .. 32i+31 of the byte image, bit j = byte 32i + j.
+__device__ __forceinline__ uint32_t nibble_of(uint32_t v)  // bytes 0..3 of v (each 0/1) -> bits 0..3
+{
+    return (v & 1u) | ((v >> 7) & 2u) | ((v >> 14) & 4u) | ((v >> 21) & 8u);
+}
+
+__device__ __forceinline__ uint32_t bytes_of(uint32_t n)  // bits 0..3 of n -> bytes 0..3 (0/1)
+{
+    return (n & 1u) | ((n & 2u) << 7) | ((n & 4u) << 14) | ((n & 8u) << 21);
+}
+
+template <int WORDS, int G>
+__device__ __forceinline__ void pack_bytes(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, int gl)
+{
+    for (int i = gl; i < WORDS; i += G) {
+        const uint4* s4 = reinterpret_cast<const uint4*>(src + 8 * i);
+        const uint4 a = s4[0], b = s4[1];
+        dst[i] = nibble_of(a.x) | nibble_of(a.y) << 4 | nibble_of(a.z) << 8 | nibble_of(a.w) << 12 |
+                 nibble_of(b.x) << 16 | nibble_of(b.y) << 20 | nibble_of(b.z) << 24 | nibble_of(b.w) << 28;
+    }
+}
+
+template <int WORDS, int G>
+__device__ __forceinline__ void unpack_bytes(uint32_t* __restrict__ dst, const uint32_t* __restrict__ src, int gl)
+{
+    for (int i = gl; i < WORDS; i += G) {
+        const uint32_t w = src[i];
+        uint4* d4 = reinterpret_cast<uint4*>(dst + 8 * i);
+        d4[0] = make_uint4(bytes_of(w), bytes_of(w >> 4), bytes_of(w >> 8), bytes_of(w >> 12));
+        d4[1] = make_uint4(bytes_of(w >> 16), bytes_of(w >> 20), bytes_of(w >> 24), bytes_of(w >> 28));
+    }
+}
+
+// a replica of the population in pop[] (bit-packed, or bytes when kBytes)
+// into the packed shared-memory image, and back
+template <int L, int G, int D, bool kBytes>
+__device__ __forceinline__ void load_replica(uint32_t* sp, const uint32_t* pop, long long slot, int gl)
+{
+    using Gm = Lat<L, D>;
+    if constexpr (kBytes) pack_bytes<Gm::WORDS, G>(sp, pop + (size_t)slot * (Gm::N / 4), gl);
+    else copy_words<Gm::WORDS, G>(sp, pop + (size_t)slot * Gm::WORDS, gl);
+}
+
+template <int L, int G, int D, bool kBytes>
+__device__ __forceinline__ void store_replica(uint32_t* pop, long long slot, const uint32_t* sp, int gl)
+{
+    using Gm = Lat<L, D>;
+    if constexpr (kBytes) unpack_bytes<Gm::WORDS, G>(pop + (size_t)slot * (Gm::N / 4), sp, gl);
+    else copy_words<Gm::WORDS, G>(pop + (size_t)slot * Gm::WORDS, sp, gl);
+}
+
 // anti-parallel bonds and up spins of the replica in shared memory
 // +-J model: a neighbour word seen through the couplings (bit flipped where
 // J < 0), so "disagree" means an unsatisfied bond in every formula below
@@ -421,7 +475,9 @@ __host__ __device__ constexpr bool bits_group_ok(int G)
     return D == 2 && G <= 32 && G % WP == 0 && G / WP <= 8;
 }
 
-template <int L, int G, int D = 2>
+// kBytes: the population is stored one byte per site (PA_SPIN_INT8) and
+// packed into the same shared-memory words on load, unpacked on store.
+template <int L, int G, int D = 2, bool kBytes = false>
 __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long long k, bool active,
                                                 uint32_t* sp, int gl, unsigned* red, unsigned& families)
 {
@@ -445,7 +501,7 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
     uint32_t p = 0;
     if (active) {
         p = r.parent[k];
-        copy_words<Gm::WORDS, G>(sp, r.pop[cur] + (size_t)p * Gm::WORDS, gl);
+        load_replica<L, G, D, kBytes>(sp, r.pop[cur], p, gl);
     }
     Gr::sync();
     for (int sw = 0; sw < theta; sw++) {
@@ -496,7 +552,7 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
     anti = Gr::sum(anti, red);
     ups = Gr::sum(ups, red);
     if (active) {
-        copy_words<Gm::WORDS, G>(r.pop[nxt] + (size_t)k * Gm::WORDS, sp, gl);
+        store_replica<L, G, D, kBytes>(r.pop[nxt], k, sp, gl);
         if (gl == 0) {
             const uint32_t f = r.fam[cur][p];
             record_replica(r, nxt, k, anti, ups, f);
@@ -508,7 +564,7 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
 
 // Initial spins of replica k (INIT stream: site g = c*N/2 + b, counter
 // (0, g>>2, 0, k), spin up iff x < 2^31), measured and written to pop[0].
-template <int L, int G, int D = 2>
+template <int L, int G, int D = 2, bool kBytes = false>
 __device__ __forceinline__ void bits_group_init(const RunDev& r, long long k, bool active, uint32_t* sp, int gl,
                                                 unsigned* red)
 {
@@ -535,7 +591,7 @@ __device__ __forceinline__ void bits_group_init(const RunDev& r, long long k, bo
     anti = Gr::sum(anti, red);
     ups = Gr::sum(ups, red);
     if (active) {
-        copy_words<Gm::WORDS, G>(r.pop[0] + (size_t)k * Gm::WORDS, sp, gl);
+        store_replica<L, G, D, kBytes>(r.pop[0], k, sp, gl);
         if (gl == 0) record_replica(r, 0, k, anti, ups, (uint32_t)k);
     }
     Gr::sync();
@@ -544,7 +600,7 @@ __device__ __forceinline__ void bits_group_init(const RunDev& r, long long k, bo
 // ======================================================== bit-packed kernels
 // Persistent: each group repeatedly takes the next replica of the run's
 // work counter, so the tail of a step is at most one replica's work.
-template <int L, int G, int D = 2>
+template <int L, int G, int D = 2, bool kBytes = false>
 __global__ void __launch_bounds__(256) k_init_bits(const __grid_constant__ RunDev r)
 {
     using Gm = Lat<L, D>;
@@ -559,11 +615,11 @@ __global__ void __launch_bounds__(256) k_init_bits(const __grid_constant__ RunDe
         const unsigned first = Gr::grab(r.work, red + 32);
         const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
         if (base >= R0) break;
-        bits_group_init<L, G, D>(r, (long long)first, first < R0, sp, gl, red);
+        bits_group_init<L, G, D, kBytes>(r, (long long)first, first < R0, sp, gl, red);
     }
 }
 
-template <int L, int G, int D = 2>
+template <int L, int G, int D = 2, bool kBytes = false>
 __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunDev r, int step)
 {
     using Gm = Lat<L, D>;
@@ -579,7 +635,7 @@ __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunD
         const unsigned first = Gr::grab(r.work, red + 32);
         const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
         if (base >= Ri) break;
-        bits_group_step<L, G, D>(r, step, (long long)first, first < Ri, sp, gl, red, families);
+        bits_group_step<L, G, D, kBytes>(r, step, (long long)first, first < Ri, sp, gl, red, families);
     }
     families = group_sum<32>(families);
     if ((threadIdx.x & 31) == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
@@ -1367,15 +1423,28 @@ __device__ __forceinline__ void tables_body(const RunDev& r, int step)
             v = stk[0];
         }
     }
-    s[t] = v;
-    __syncthreads();
-    for (int n = nthr; n > 1; n >>= 1) {
-        double x = 0.0;
-        if (t < n / 2) x = __dadd_rn(s[2 * t], s[2 * t + 1]);
-        __syncthreads();
-        if (t < n / 2) s[t] = x;
-        __syncthreads();
+    // The same pairwise tree over the nthr leaves, level by level: within a
+    // warp the lane holding the left subtree adds its right neighbour's
+    // (offsets 1, 2, 4, 8, 16), then warp 0 joins the warps' subtrees the
+    // same way. Each sum is (left subtree) + (right subtree), as above.
+    const int lane = t & 31, warp = t >> 5;
+    const int wl = nthr < 32 ? nthr : 32;  // leaves per warp
+    for (int off = 1; off < wl; off <<= 1) {
+        const double y = __shfl_down_sync(0xffffffffu, v, off);
+        if ((lane & (2 * off - 1)) == 0) v = __dadd_rn(v, y);
     }
+    if (lane == 0 && t < nthr) s[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        const int nw = nthr / wl;  // warp subtrees (power of two <= 32)
+        double x = lane < nw ? s[lane] : 0.0;
+        for (int off = 1; off < nw; off <<= 1) {
+            const double y = __shfl_down_sync(0xffffffffu, x, off);
+            if ((lane & (2 * off - 1)) == 0) x = __dadd_rn(x, y);
+        }
+        if (lane == 0) s[0] = x;
+    }
+    __syncthreads();
     const double S = s[0];
     const double Rd = (double)r.R;
     for (int kk = kmin + t; kk <= kmax; kk += kOneCta) {
@@ -2006,10 +2075,10 @@ __global__ void __launch_bounds__(256) k_rng_peak(long long blocks, PhiloxKey ke
 // ======================================================== launch wrappers
 namespace {
 
-template <int L, int G, int D = 2>
+template <int L, int G, int D = 2, bool kBytes = false>
 const void* bits_ptr(bool init)
 {
-    return init ? (const void*)k_init_bits<L, G, D> : (const void*)k_sweep_bits<L, G, D>;
+    return init ? (const void*)k_init_bits<L, G, D, kBytes> : (const void*)k_sweep_bits<L, G, D, kBytes>;
 }
 
 // simple cubic lattice: the warp groups and CTA groups the default choice
@@ -2028,18 +2097,18 @@ const void* bits3_ptr_L(int gt, bool init)
     return nullptr;
 }
 
-template <int L>
+template <int L, bool kBytes = false>
 const void* bits_ptr_L(int gt, bool init)
 {
     constexpr int WP = L * L / 64;
     switch (gt) {
-    case 1: return bits_ptr<L, 1>(init);
-    case 2: if constexpr (bits_group_ok<L, 2>(2)) return bits_ptr<L, 2>(init); break;
-    case 4: if constexpr (bits_group_ok<L, 2>(4)) return bits_ptr<L, 4>(init); break;
-    case 8: if constexpr (bits_group_ok<L, 2>(8)) return bits_ptr<L, 8>(init); break;
-    case 16: if constexpr (bits_group_ok<L, 2>(16)) return bits_ptr<L, 16>(init); break;
-    case 32: if constexpr (bits_group_ok<L, 2>(32)) return bits_ptr<L, 32>(init); break;
-    case 256: if constexpr (WP % 256 == 0) return bits_ptr<L, 256>(init); break;
+    case 1: return bits_ptr<L, 1, 2, kBytes>(init);
+    case 2: if constexpr (bits_group_ok<L, 2>(2)) return bits_ptr<L, 2, 2, kBytes>(init); break;
+    case 4: if constexpr (bits_group_ok<L, 2>(4)) return bits_ptr<L, 4, 2, kBytes>(init); break;
+    case 8: if constexpr (bits_group_ok<L, 2>(8)) return bits_ptr<L, 8, 2, kBytes>(init); break;
+    case 16: if constexpr (bits_group_ok<L, 2>(16)) return bits_ptr<L, 16, 2, kBytes>(init); break;
+    case 32: if constexpr (bits_group_ok<L, 2>(32)) return bits_ptr<L, 32, 2, kBytes>(init); break;
+    case 256: if constexpr (WP % 256 == 0) return bits_ptr<L, 256, 2, kBytes>(init); break;
     default: break;
     }
     return nullptr;
@@ -2078,6 +2147,19 @@ const void* sweep_kernel(const RunDev& h, bool init)
         case 16: return bits3_ptr_L<16>(h.gt, init);
         case 32: return bits3_ptr_L<32>(h.gt, init);
         case 64: return bits3_ptr_L<64>(h.gt, init);
+        default: return nullptr;
+        }
+    }
+    if (h.fmt == 0 && h.packed) {
+        // byte-stored spins swept in the bit-packed kernel (packed on load)
+        switch (h.L) {
+        case 8: return bits_ptr_L<8, true>(h.gt, init);
+        case 16: return bits_ptr_L<16, true>(h.gt, init);
+        case 32: return bits_ptr_L<32, true>(h.gt, init);
+        case 64: return bits_ptr_L<64, true>(h.gt, init);
+        case 128: return bits_ptr_L<128, true>(h.gt, init);
+        case 256: return bits_ptr_L<256, true>(h.gt, init);
+        case 512: return bits_ptr_L<512, true>(h.gt, init);
         default: return nullptr;
         }
     }
@@ -2156,11 +2238,12 @@ cudaError_t plan_sweep(const RunDev& h, Launch* ln)
     } else if (h.gt > 32) {
         // one replica per CTA of gt threads, plus reduction/broadcast words
         threads = h.gt;
-        smem = ((size_t)h.words + 33) * 4u;
+        smem = ((size_t)(h.packed ? h.N / 32 : h.words) + 33) * 4u;
     } else {
         // CTA of up to 8 warps; fewer when one warp's replicas need much shared memory
-        const size_t per_warp = (size_t)(32 / h.gt) * (size_t)h.words * 4u;
-        int warps = 8;
+        const size_t rep_words = h.packed ? (size_t)h.N / 32 : (size_t)h.words;  // packed image of a byte replica
+        const size_t per_warp = (size_t)(32 / h.gt) * rep_words * 4u;
+        int warps = h.bw > 0 && h.bw <= 8 ? h.bw : 8;
         while (warps > 1 && per_warp * warps > (size_t)max_optin) warps >>= 1;
         smem = per_warp * warps;
         threads = 32 * warps;
