@@ -2026,7 +2026,16 @@ __global__ void __launch_bounds__(256) k_gather(const uint4* __restrict__ src, c
         }
         const uint4* s = src + (size_t)p * (size_t)w4;
         uint4* d = dst + (size_t)o * (size_t)w4;
-        for (int i = l; i < w4; i += LPR) __stcs(d + i, __ldcs(s + i));
+        int i = l;
+        for (; i + 3 * LPR < w4; i += 4 * LPR) {  // four loads in flight per lane
+            const uint4 a = __ldcs(s + i), b = __ldcs(s + i + LPR), c = __ldcs(s + i + 2 * LPR),
+                        e = __ldcs(s + i + 3 * LPR);
+            __stcs(d + i, a);
+            __stcs(d + i + LPR, b);
+            __stcs(d + i + 2 * LPR, c);
+            __stcs(d + i + 3 * LPR, e);
+        }
+        for (; i < w4; i += LPR) __stcs(d + i, __ldcs(s + i));
     }
 }
 
