@@ -356,12 +356,15 @@ pa_status pa_tune_cache_lookup(const char *path, const pa_tune_key *key, pa_tune
 /* ---- batches of independent runs ---------------------------------------
  * Many independent fixed-schedule runs (batched runs; Sec. 2.2 notes
  * that independent runs combine by free-energy weights) stepped together:
- * every phase of a temperature step is one launch for all runs. The sweep
- * is two persistent kernels over one queue of work items: one replica per
- * CTA of the runs with group_threads 256 (L = 128, 256, 512), then
- * (run, replica batch) items of the warp-group runs, each part ordered by
- * descending work per replica. The whole schedule is one
- * CUDA graph, captured on the first launch and reused after pa_batch_reset.
+ * every bookkeeping phase of a temperature step is one launch for all runs.
+ * The sweep's work queue (one item per replica of the runs with
+ * group_threads 256 at L = 128, 256, 512; (run, replica batch) items of the
+ * warp-group runs) is cut into segments of runs sharing (L, group_threads),
+ * each ordered by descending work per replica and swept by a persistent
+ * kernel compiled for that shape; the segments' kernels run on parallel
+ * branches of the graph, so they overlap at their tails. The whole schedule
+ * is one CUDA graph, captured on the first launch and reused after
+ * pa_batch_reset.
  * Each run's results are those of the same pa_config run alone, bit for
  * bit. Runs must use fixed steps (dbeta > 0), bit-packed spins on the
  * square lattice and L <= 512 (L = 512: group_threads 256 only); group_threads == 0 picks the

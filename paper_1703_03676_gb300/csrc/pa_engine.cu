@@ -1667,10 +1667,11 @@ pa_status pa_measure_pipe_peak(int pipe, int64_t iters, uint32_t* sink, void* st
 
 // ================================================================== batches
 // Independent fixed-schedule runs stepped together (batched runs):
-// each phase of a temperature step is one launch over all runs, and the
-// sweep is one persistent kernel whose warps pull (run, replica batch)
-// items from a single queue ordered by descending work per replica. The
-// whole schedule is captured once as one CUDA graph.
+// each bookkeeping phase of a temperature step is one launch over all runs,
+// and the sweep is one persistent kernel per segment of runs sharing a
+// shape (L, threads per replica), pulling items from the segment's queue
+// (descending work per replica); the segments run on parallel graph
+// branches. The whole schedule is captured once as one CUDA graph.
 struct pa_batch {
     std::vector<pa_ctx*> runs;
     cudaStream_t stream = nullptr;
@@ -1686,6 +1687,7 @@ struct pa_batch {
     bool ev_pending = false;
     double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};
     long long phase_n[7] = {0, 0, 0, 0, 0, 0, 0};
+    std::vector<int> order;       // queue position -> run
 };
 
 namespace {
@@ -1713,6 +1715,11 @@ void batch_free(pa_batch* b)
         pa_destroy(c);
     }
     for (void* p : b->allocs) cudaFree(p);
+    for (int i = 0; i < pa::kMaxBatchSegs; i++) {
+        if (b->ln.side[i]) cudaStreamDestroy(b->ln.side[i]);
+        if (b->ln.join[i]) cudaEventDestroy(b->ln.join[i]);
+    }
+    if (b->ln.fork) cudaEventDestroy(b->ln.fork);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
 }
 
@@ -1803,7 +1810,6 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
     }
     b->profile = false;
     std::vector<RunDev> hr((size_t)n);
-    int warp_words = 0, cta_words = 0, n_cta = 0;
     for (int i = 0; i < n; i++) {
         pa_config c = cfgs[i];
         if (c.profile) b->profile = true;
@@ -1822,22 +1828,44 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
         b->runs.push_back(m);
         hr[(size_t)i] = m->h;
         b->max_steps = std::max(b->max_steps, (int)m->n_fixed);
-        if (m->h.gt > 32) {
-            cta_words = std::max(cta_words, m->h.words);
-            n_cta++;
-        } else {
-            warp_words = std::max(warp_words, (32 / m->h.gt) * m->h.words);
-        }
     }
-    // queue order: runs with CTA-wide groups first (the sweep's CTA phase),
-    // then descending work per replica (theta * N)
+    // queue order: runs grouped by shape (larger lattices first), each group
+    // by descending work per replica (theta * N); each group is one segment
     std::vector<int> order((size_t)n), tile_run, tile_first((size_t)n);
     for (int i = 0; i < n; i++) order[(size_t)i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-        const bool cx = hr[(size_t)x].gt > 32, cy = hr[(size_t)y].gt > 32;
-        if (cx != cy) return cx;
-        return (long long)hr[(size_t)x].theta * hr[(size_t)x].N > (long long)hr[(size_t)y].theta * hr[(size_t)y].N;
+        const RunDev &a = hr[(size_t)x], &c = hr[(size_t)y];
+        if (a.L != c.L) return a.L > c.L;
+        if (a.gt != c.gt) return a.gt > c.gt;
+        return (long long)a.theta * a.N > (long long)c.theta * c.N;
     });
+    b->ln.nseg = 0;
+    for (int q = 0; q < n; q++) {
+        const RunDev& a = hr[(size_t)order[(size_t)q]];
+        pa::BatchSeg* last = b->ln.nseg ? &b->ln.seg[b->ln.nseg - 1] : nullptr;
+        if (last && last->L == a.L && last->G == a.gt) {
+            last->q1 = q + 1;
+            continue;
+        }
+        if (b->ln.nseg == pa::kMaxBatchSegs) return fail(PA_EINVAL);
+        b->ln.seg[b->ln.nseg++] = pa::BatchSeg{q, q + 1, a.L, a.gt, 0, 0};
+    }
+    for (int i = 0; i < b->ln.nseg; i++) {
+        pa::BatchSeg& sg = b->ln.seg[i];
+        long long units = 0;
+        for (int q = sg.q0; q < sg.q1; q++) units += hr[(size_t)order[(size_t)q]].cap;
+        if (pa::plan_batch_segment(&sg, units) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(PA_EINVAL);
+        }
+    }
+    if (b->ln.nseg > 1) {
+        if (cudaEventCreateWithFlags(&b->ln.fork, cudaEventDisableTiming) != cudaSuccess) return fail(PA_ECUDA);
+        for (int i = 0; i < b->ln.nseg; i++)
+            if (cudaStreamCreateWithFlags(&b->ln.side[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->ln.join[i], cudaEventDisableTiming) != cudaSuccess)
+                return fail(PA_ECUDA);
+    }
     for (int i = 0; i < n; i++) {
         tile_first[(size_t)i] = (int)tile_run.size();
         for (int t = 0; t < hr[(size_t)i].ntiles; t++) tile_run.push_back(i);
@@ -1856,7 +1884,7 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
     unsigned* d_work = nullptr;
     if (!dalloc((void**)&d_runs, sizeof(RunDev) * (size_t)n) || !dalloc((void**)&d_order, 4 * (size_t)n) ||
         !dalloc((void**)&d_tile_run, 4 * tile_run.size()) || !dalloc((void**)&d_tile_first, 4 * (size_t)n) ||
-        !dalloc((void**)&d_off, 8 * (size_t)(n + 1)) || !dalloc((void**)&d_work, 16))
+        !dalloc((void**)&d_off, 8 * (size_t)(n + 1)) || !dalloc((void**)&d_work, 4 * pa::kMaxBatchSegs))
         return fail(PA_ENOMEM);
     if (cudaMemcpy(d_runs, hr.data(), sizeof(RunDev) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d_order, order.data(), 4 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1870,14 +1898,9 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
     b->bd.item_off = d_off;
     b->bd.work = d_work;
     b->bd.nruns = n;
-    b->bd.n_cta = n_cta;
-    b->bd.warp_words = warp_words;
-    b->bd.cta_words = cta_words;
+    b->bd.nseg = b->ln.nseg;
     b->ln.tiles = (int)tile_run.size();
-    if (pa::plan_batch(b->bd, &b->ln) != cudaSuccess) {
-        cudaGetLastError();
-        return fail(PA_EINVAL);
-    }
+    b->order = order;
     *out = b;
     return PA_OK;
 }
@@ -1945,7 +1968,13 @@ pa_status pa_batch_shape(pa_batch* b, int32_t i, int32_t* group_threads, int32_t
 {
     if (!b || i < 0 || i >= (int32_t)b->runs.size()) return PA_EINVAL;
     if (group_threads) *group_threads = b->runs[(size_t)i]->h.gt;
-    if (sweep_blocks) *sweep_blocks = b->runs[(size_t)i]->h.gt > 32 ? b->ln.cta_blocks : b->ln.sweep_blocks;
+    if (sweep_blocks) {
+        *sweep_blocks = 0;
+        for (int q = 0; q < (int)b->order.size(); q++)
+            if (b->order[(size_t)q] == i)
+                for (int s = 0; s < b->ln.nseg; s++)
+                    if (q >= b->ln.seg[s].q0 && q < b->ln.seg[s].q1) *sweep_blocks = b->ln.seg[s].blocks;
+    }
     return PA_OK;
 }
 

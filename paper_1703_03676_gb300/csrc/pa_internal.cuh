@@ -152,17 +152,16 @@ struct ResampleArgs {
 // ---------------------------------------------------------------- batches
 // Many independent runs stepped together: one launch per phase for all runs.
 constexpr int kMaxBatchRuns = 1024;
+constexpr int kMaxBatchSegs = 16;     // (L, threads per replica) shapes of one batch
 struct BatchDev {
     const RunDev* runs;       // device array of the runs' descriptors
-    const int* order;         // runs in queue order (descending work per replica)
+    const int* order;         // runs in queue order (by shape, then descending work per replica)
     const int* tile_run;      // copy-count tile -> run
     const int* tile_first;    // first copy-count tile of each run
     long long* item_off;      // nruns + 1 offsets of each run's work items (queue order)
-    unsigned* work;           // queue counters of the sweep: [0] warp-group items, [1] CTA-group items
+    unsigned* work;           // queue counter of each segment of the sweep
     int nruns;
-    int n_cta;                // runs at the front of `order` whose replicas take a whole CTA
-    int warp_words;           // shared-memory words per warp in the sweep (warp-group runs)
-    int cta_words;            // shared-memory words of one replica of the CTA-group runs
+    int nseg;                 // queue segments (runs of one shape)
 };
 
 // ---------------------------------------------------------------- launches
@@ -191,14 +190,20 @@ cudaError_t launch_philox(const uint32_t* ctr, long long n, PhiloxKey key, uint3
 cudaError_t launch_gather(const uint32_t* src, const uint32_t* parent, long long n_new, long long n_src, int words,
                           uint32_t* dst, unsigned* bad, int grid, cudaStream_t s);
 
+// one segment of the batched sweep: queue positions [q0, q1), shape (L, G)
+struct BatchSeg {
+    int q0, q1, L, G;
+    int blocks;               // persistent CTAs (256 threads)
+    size_t smem;
+};
 struct BatchLaunch {
     int tiles;                // copy-count tiles over all runs
-    int sweep_blocks;         // persistent CTAs (256 threads) of the warp-group sweep
-    size_t sweep_smem;
-    int cta_blocks;           // persistent CTAs of the CTA-group sweep
-    size_t cta_smem;
+    int nseg;
+    BatchSeg seg[kMaxBatchSegs];
+    cudaStream_t side[kMaxBatchSegs];  // one stream per segment (branches of the graph)
+    cudaEvent_t fork, join[kMaxBatchSegs];
 };
-cudaError_t plan_batch(const BatchDev& b, BatchLaunch* ln);
+cudaError_t plan_batch_segment(BatchSeg* seg, long long units);
 cudaError_t launch_batch_step(const BatchDev& b, const BatchLaunch& ln, int step, cudaStream_t s, int phase,
                               int* phase_of_launch);
 bool batch_supports(int L, int gt);

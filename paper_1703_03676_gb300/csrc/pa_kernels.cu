@@ -433,6 +433,19 @@ struct Group {
             return group_sum<G>(v);
         }
     }
+    // Work items of a persistent loop: every group of the grid starts with
+    // a fixed replica (first_item; static_items of them in all), and takes
+    // further ones from the run's counter (grab() + static_items()), so the
+    // counter is touched only by groups that finish while work remains.
+    __device__ static __forceinline__ unsigned first_item()
+    {
+        if constexpr (kCta) return blockIdx.x;
+        else return (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kPerWarp + (threadIdx.x & 31) / G;
+    }
+    __device__ static __forceinline__ unsigned static_items()
+    {
+        return kCta ? gridDim.x : gridDim.x * (blockDim.x >> 5) * kPerWarp;
+    }
     // first replica index of this group's next work item (persistent loop)
     __device__ static __forceinline__ unsigned grab(unsigned* work, unsigned* bcast)
     {
@@ -611,8 +624,7 @@ __global__ void __launch_bounds__(256) k_init_bits(const __grid_constant__ RunDe
     unsigned* red = smem + Gm::WORDS;  // CTA groups only
     const int gl = Gr::thread_in_group();
     const long long R0 = r.R;
-    for (;;) {
-        const unsigned first = Gr::grab(r.work, red + 32);
+    for (unsigned first = Gr::first_item();; first = Gr::grab(r.work, red + 32) + Gr::static_items()) {
         const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
         if (base >= R0) break;
         bits_group_init<L, G, D, kBytes>(r, (long long)first, first < R0, sp, gl, red);
@@ -631,8 +643,7 @@ __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunD
     const int gl = Gr::thread_in_group();
     const long long Ri = r.rec[step].R;
     unsigned families = 0;
-    for (;;) {
-        const unsigned first = Gr::grab(r.work, red + 32);
+    for (unsigned first = Gr::first_item();; first = Gr::grab(r.work, red + 32) + Gr::static_items()) {
         const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
         if (base >= Ri) break;
         bits_group_step<L, G, D, kBytes>(r, step, (long long)first, first < Ri, sp, gl, red, families);
@@ -643,6 +654,14 @@ __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunD
 
 // ======================================================== byte-spin kernels
 // Same RNG streams and update rule with one byte per spin (any even L >= 4).
+
+// next work item of a warp from the run's counter (lane 0 takes n items)
+__device__ __forceinline__ unsigned warp_grab(unsigned* work, unsigned n)
+{
+    unsigned v = 0;
+    if ((threadIdx.x & 31) == 0) v = atomicAdd(work, n);
+    return __shfl_sync(0xffffffffu, v, 0);
+}
 // Thread handles the sites of one Philox block (4 consecutive b) at a time.
 __device__ __forceinline__ int nb_index_side(int b, int c, int L, int half)
 {
@@ -712,10 +731,10 @@ __global__ void __launch_bounds__(256) k_init_bytes(const __grid_constant__ RunD
     const PhiloxKey key{r.key[0], r.key[1]};
     const long long R0 = r.R;
     const int N = r.N, NP = N / 2;
-    for (;;) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
-        base = __shfl_sync(0xffffffffu, base, 0);
+    // first item fixed per warp, then from the counter (as Group::first_item)
+    const unsigned static_items = gridDim.x * (blockDim.x >> 5) * RPW;
+    for (unsigned base = (blockIdx.x * (blockDim.x >> 5) + warp) * RPW;;
+         base = warp_grab(r.work, (unsigned)RPW) + static_items) {
         if (base >= R0) break;
         const long long k = (long long)base + g;
         const bool active = k < R0;
@@ -763,10 +782,10 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
     const int L = r.L, half = r.half, NP = r.N / 2, QP = (NP + 3) / 4;
     const unsigned hm = row_magic(half);
     unsigned families = 0;
-    for (;;) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
-        base = __shfl_sync(0xffffffffu, base, 0);
+    // first item fixed per warp, then from the counter (as Group::first_item)
+    const unsigned static_items = gridDim.x * (blockDim.x >> 5) * RPW;
+    for (unsigned base = (blockIdx.x * (blockDim.x >> 5) + warp) * RPW;;
+         base = warp_grab(r.work, (unsigned)RPW) + static_items) {
         if (base >= Ri) break;
         const long long k = (long long)base + g;
         const bool active = k < Ri;
@@ -898,10 +917,10 @@ __global__ void __launch_bounds__(256) k_init_potts(const __grid_constant__ RunD
     const PhiloxKey key{r.key[0], r.key[1]};
     const long long R0 = r.R;
     const int N = r.N, q = r.potts_q;
-    for (;;) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
-        base = __shfl_sync(0xffffffffu, base, 0);
+    // first item fixed per warp, then from the counter (as Group::first_item)
+    const unsigned static_items = gridDim.x * (blockDim.x >> 5) * RPW;
+    for (unsigned base = (blockIdx.x * (blockDim.x >> 5) + warp) * RPW;;
+         base = warp_grab(r.work, (unsigned)RPW) + static_items) {
         if (base >= R0) break;
         const long long k = (long long)base + g;
         const bool active = k < R0;
@@ -947,10 +966,10 @@ __global__ void __launch_bounds__(256) k_sweep_potts(const __grid_constant__ Run
     const int L = r.L, half = r.half, NP = r.N / 2, QP = NP / 2, q = r.potts_q;
     const unsigned hm = row_magic(half);
     unsigned families = 0;
-    for (;;) {
-        unsigned base = 0;
-        if (lane == 0) base = atomicAdd(r.work, (unsigned)RPW);
-        base = __shfl_sync(0xffffffffu, base, 0);
+    // first item fixed per warp, then from the counter (as Group::first_item)
+    const unsigned static_items = gridDim.x * (blockDim.x >> 5) * RPW;
+    for (unsigned base = (blockIdx.x * (blockDim.x >> 5) + warp) * RPW;;
+         base = warp_grab(r.work, (unsigned)RPW) + static_items) {
         if (base >= Ri) break;
         const long long k = (long long)base + g;
         const bool active = k < Ri;
@@ -1268,9 +1287,11 @@ __global__ void __launch_bounds__(32 * msc_warps<L>()) k_init_msc(const __grid_c
     unsigned* red = smem + N;
     const PhiloxKey key{r.key[0], r.key[1]};
     const long long R0 = r.R, groups = (R0 + 31) / 32;
+    unsigned next_g = blockIdx.x;  // first group fixed per CTA, then from the counter
     for (;;) {
-        const unsigned G = msc_grab<L>(r.work, red + 2 * W * 32);
+        const unsigned G = next_g;
         if ((long long)G >= groups) break;
+        next_g = msc_grab<L>(r.work, red + 2 * W * 32) + gridDim.x;  // after this CTA's first group
         const long long k = 32ll * G + lane;
         const bool valid = k < R0;
         // INIT stream of replica k: site g = c*N/2 + b, counter (0, g>>2, 0, k)
@@ -1305,14 +1326,16 @@ __global__ void __launch_bounds__(32 * msc_warps<L>()) k_sweep_msc(const __grid_
     unsigned* red = smem + N;
     const int cur = (step - 1) & 1, nxt = step & 1;
     const long long Ri = r.rec[step].R, groups = (Ri + 31) / 32;
+    unsigned next_g = blockIdx.x;  // first group fixed per CTA, then from the counter
     const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
     const PhiloxKey key{r.key[0], r.key[1]};
     const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
     const int theta = r.theta;
     unsigned families = 0;
     for (;;) {
-        const unsigned G = msc_grab<L>(r.work, red + 2 * W * 32);
+        const unsigned G = next_g;
         if ((long long)G >= groups) break;
+        next_g = msc_grab<L>(r.work, red + 2 * W * 32) + gridDim.x;  // after this CTA's first group
         const long long k = 32ll * G + lane;
         const bool valid = k < Ri;
         // gather: bit `lane` of every site word comes from this lane's parent
@@ -1882,9 +1905,11 @@ __global__ void __launch_bounds__(kOneCta) k_resample_small(const __grid_constan
 
 // ======================================================== batched sweep
 // Work items of step `step`, laid out in queue order: one per replica of a
-// run with CTA-wide groups (those come first), ceil(R_i / (replicas per
-// warp)) per run with warp groups. Each of the two sweep kernels takes its
-// part of the items from its own counter.
+// run with CTA-wide groups, ceil(R_i / (replicas per warp)) per run with
+// warp groups. The queue is cut into segments of runs that share (L, threads
+// per replica); each segment is swept by its own instance of the kernel
+// below (compiled for that shape alone), all segments on parallel branches
+// of the captured graph, each with its own counter work[seg].
 __global__ void k_plan(const __grid_constant__ BatchDev b, int step)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -1898,31 +1923,7 @@ __global__ void k_plan(const __grid_constant__ BatchDev b, int step)
         }
     }
     b.item_off[b.nruns] = acc;
-    b.work[0] = 0u;  // warp-group items
-    b.work[1] = 0u;  // CTA-group items
-}
-
-template <int L, int G>
-__device__ __forceinline__ void batch_item(const RunDev& r, int step, long long item, uint32_t* wsm)
-{
-    using Gm = Geo<L>;
-    using Gr = Group<G>;
-    static_assert(!Gr::kCta, "batched sweeps use warp groups");
-    const int lane = threadIdx.x & 31, g = lane / G;
-    const long long k = item * Gr::kPerWarp + g;
-    unsigned fam = 0;
-    bits_group_step<L, G>(r, step, k, k < r.rec[step].R, wsm + g * Gm::WORDS, lane % G, nullptr, fam);
-    fam = group_sum<32>(fam);
-    if (lane == 0 && fam) atomicAdd(&r.rec[step].fam, (unsigned long long)fam);
-}
-
-// one replica of a run with CTA-wide groups, taken by the whole CTA
-template <int L>
-__device__ __forceinline__ void batch_item_cta(const RunDev& r, int step, long long k, uint32_t* sp, unsigned* red)
-{
-    unsigned fam = 0;
-    bits_group_step<L, 256>(r, step, k, k < r.rec[step].R, sp, (int)threadIdx.x, red, fam);
-    if (threadIdx.x == 0 && fam) atomicAdd(&r.rec[step].fam, (unsigned long long)fam);
+    for (int s = 0; s < b.nseg; s++) b.work[s] = 0u;
 }
 
 // (L, G) pairs a batched sweep can run: warp groups dividing the plane, and
@@ -1942,62 +1943,50 @@ __device__ __forceinline__ int batch_run_of(const long long* off, int n, long lo
     return lo;
 }
 
-// Persistent CTAs over the items of the CTA-group runs (the first n_cta
-// runs of the queue, items [0, item_off[n_cta])): one replica at a time,
-// colour phases separated by __syncthreads. Its own counter (work[1]).
-__global__ void __launch_bounds__(256) k_sweep_batch_cta(const __grid_constant__ BatchDev b, int step)
+// Persistent sweep of the segment q0..q1-1 of the queue (runs of one shape):
+// with G = 256 each CTA takes one replica at a time (colour phases separated
+// by __syncthreads), with G <= 32 each warp takes (run, replica batch)
+// items, from the segment's counter work[seg].
+template <int L, int G>
+__global__ void __launch_bounds__(256) k_sweep_batch_seg(const __grid_constant__ BatchDev b, int step, int q0, int q1,
+                                                         int seg)
 {
+    using Gm = Geo<L>;
     extern __shared__ uint32_t smem[];
     __shared__ long long s_off[kMaxBatchRuns + 1];
-    __shared__ unsigned s_red[256 / 32];
-    __shared__ unsigned s_item;
-    for (int i = threadIdx.x; i <= b.n_cta; i += blockDim.x) s_off[i] = b.item_off[i];
+    __shared__ unsigned s_red[256 / 32 + 1];
+    const int nq = q1 - q0;
+    for (int i = threadIdx.x; i <= nq; i += blockDim.x) s_off[i] = b.item_off[q0 + i];
     __syncthreads();
-    const long long end = s_off[b.n_cta];
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(b.work + 1, 1u);
-        __syncthreads();
-        const long long it = s_item;
-        __syncthreads();
-        if (it >= end) break;
-        const int q = batch_run_of(s_off, b.n_cta, it);
-        const RunDev& r = b.runs[b.order[q]];
-        const long long k = it - s_off[q];
-        switch (r.L) {
-#define PA_BATCH_CTA_CASE(LL) \
-    case LL: batch_item_cta<LL>(r, step, k, smem, s_red); break;
-            PA_BATCH_CTA_SIZES(PA_BATCH_CTA_CASE)
-#undef PA_BATCH_CTA_CASE
-        default: break;
+    const long long first = s_off[0], end = s_off[nq];
+    if constexpr (G > 32) {
+        for (;;) {
+            if (threadIdx.x == 0) s_red[256 / 32] = atomicAdd(b.work + seg, 1u);
+            __syncthreads();
+            const long long it = first + (long long)s_red[256 / 32];
+            __syncthreads();
+            if (it >= end) break;
+            const int q = batch_run_of(s_off, nq, it);
+            const RunDev& r = b.runs[b.order[q0 + q]];
+            const long long k = it - s_off[q];
+            unsigned fam = 0;
+            bits_group_step<L, 256>(r, step, k, k < r.rec[step].R, smem, (int)threadIdx.x, s_red, fam);
+            if (threadIdx.x == 0 && fam) atomicAdd(&r.rec[step].fam, (unsigned long long)fam);
         }
-    }
-}
-
-// Persistent warps over the items of the warp-group runs (items
-// [item_off[n_cta], item_off[nruns])), taken one per warp from work[0].
-__global__ void __launch_bounds__(256) k_sweep_batch(const __grid_constant__ BatchDev b, int step)
-{
-    extern __shared__ uint32_t smem[];
-    __shared__ long long s_off[kMaxBatchRuns + 1];
-    for (int i = threadIdx.x; i <= b.nruns; i += blockDim.x) s_off[i] = b.item_off[i];
-    __syncthreads();
-    const long long total = s_off[b.nruns], first = s_off[b.n_cta];
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    uint32_t* wsm = smem + warp * b.warp_words;
-    for (;;) {
-        unsigned v = 0;
-        if (lane == 0) v = atomicAdd(b.work, 1u);
-        const long long it = first + (long long)__shfl_sync(0xffffffffu, v, 0);
-        if (it >= total) break;
-        const int q = batch_run_of(s_off, b.nruns, it);
-        const RunDev& r = b.runs[b.order[q]];
-        const long long item = it - s_off[q];
-        switch (r.L * 64 + r.gt) {
-#define PA_BATCH_CASE(LL, GG) \
-    case LL * 64 + GG: batch_item<LL, GG>(r, step, item, wsm); break;
-            PA_BATCH_SHAPES(PA_BATCH_CASE)
-#undef PA_BATCH_CASE
-        default: break;
+    } else {
+        using Gr = Group<G>;
+        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane / G;
+        uint32_t* wsm = smem + warp * (Gr::kPerWarp * Gm::WORDS);
+        for (;;) {
+            const long long it = first + (long long)warp_grab(b.work + seg, 1u);
+            if (it >= end) break;
+            const int q = batch_run_of(s_off, nq, it);
+            const RunDev& r = b.runs[b.order[q0 + q]];
+            const long long k = (it - s_off[q]) * Gr::kPerWarp + g;
+            unsigned fam = 0;
+            bits_group_step<L, G>(r, step, k, k < r.rec[step].R, wsm + g * Gm::WORDS, lane % G, nullptr, fam);
+            fam = group_sum<32>(fam);
+            if (lane == 0 && fam) atomicAdd(&r.rec[step].fam, (unsigned long long)fam);
         }
     }
 }
@@ -2265,9 +2254,24 @@ cudaError_t plan_sweep(const RunDev& h, Launch* ln)
     int per_sm = 0;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, ksw, threads, smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    // persistent grid: enough CTAs to hold every replica of a full population
+    // at once, at most what the device keeps resident
+    long long units;  // work items of a full population, and their number per CTA
+    long long per_cta;
+    if (h.fmt == 2) {
+        units = (h.cap + 31) / 32;
+        per_cta = 1;
+    } else if (h.gt > 32) {
+        units = h.cap;
+        per_cta = 1;
+    } else {
+        units = h.cap;
+        per_cta = (long long)(threads / 32) * (32 / h.gt);
+    }
+    const long long need = (units + per_cta - 1) / per_cta;
     ln->sweep_threads = threads;
     ln->sweep_smem = smem;
-    ln->sweep_blocks = sms * per_sm;
+    ln->sweep_blocks = (int)std::max(1ll, std::min((long long)sms * per_sm, need));
     ln->count_blocks = h.ntiles;
     return cudaSuccess;
 }
@@ -2370,35 +2374,51 @@ bool batch_supports(int L, int gt)
     }
 }
 
-cudaError_t plan_batch(const BatchDev& b, BatchLaunch* ln)
+namespace {
+// the segment kernel of shape (L, G), or null
+const void* batch_seg_kernel(int L, int G)
+{
+    if (G == 256) {
+        switch (L) {
+#define PA_BATCH_CTA_PTR(LL) \
+    case LL: return (const void*)k_sweep_batch_seg<LL, 256>;
+            PA_BATCH_CTA_SIZES(PA_BATCH_CTA_PTR)
+#undef PA_BATCH_CTA_PTR
+        default: return nullptr;
+        }
+    }
+    switch (L * 64 + G) {
+#define PA_BATCH_PTR(LL, GG) \
+    case LL * 64 + GG: return (const void*)k_sweep_batch_seg<LL, GG>;
+        PA_BATCH_SHAPES(PA_BATCH_PTR)
+#undef PA_BATCH_PTR
+    default: return nullptr;
+    }
+}
+}  // namespace
+
+// Grid and shared memory of a segment's kernel: enough persistent CTAs for
+// `units` replicas (the capacities of its runs), at most the resident ones.
+cudaError_t plan_batch_segment(BatchSeg* sg, long long units)
 {
     int dev = 0, sms = 0, max_optin = 0, per_sm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev)) != cudaSuccess) return e;
-    const size_t fixed = (kMaxBatchRuns + 1) * 8 + 64;  // static shared memory of both kernels
-    // warp-group kernel
-    const size_t smem = (size_t)std::max(8 * b.warp_words, 1) * 4;
+    const void* k = batch_seg_kernel(sg->L, sg->G);
+    if (!k) return cudaErrorInvalidConfiguration;
+    const size_t words = (size_t)sg->L * sg->L / 32;
+    const size_t smem = sg->G > 32 ? words * 4 : (size_t)8 * (32 / sg->G) * words * 4;
+    const size_t fixed = (kMaxBatchRuns + 1) * 8 + 64;  // static shared memory of the kernel
     if (smem + fixed > (size_t)max_optin) return cudaErrorInvalidConfiguration;
-    if ((e = cudaFuncSetAttribute((const void*)k_sweep_batch, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-        cudaSuccess)
-        return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_batch, 256, smem)) != cudaSuccess) return e;
+    if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    ln->sweep_blocks = sms * per_sm;
-    ln->sweep_smem = smem;
-    // CTA-group kernel
-    const size_t csmem = (size_t)std::max(b.cta_words, 1) * 4;
-    if (csmem + fixed > (size_t)max_optin) return cudaErrorInvalidConfiguration;
-    if ((e = cudaFuncSetAttribute((const void*)k_sweep_batch_cta, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)csmem)) != cudaSuccess)
-        return e;
-    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_sweep_batch_cta, 256, csmem)) != cudaSuccess)
-        return e;
-    if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    ln->cta_blocks = sms * per_sm;
-    ln->cta_smem = csmem;
+    const long long per_cta = sg->G > 32 ? 1 : 8ll * (32 / sg->G);
+    const long long need = std::max(1ll, (units + per_cta - 1) / per_cta);
+    sg->blocks = (int)std::min((long long)sms * per_sm, need);
+    sg->smem = smem;
     return cudaSuccess;
 }
 
@@ -2412,15 +2432,29 @@ cudaError_t launch_batch_step(const BatchDev& b, const BatchLaunch& ln, int step
     case 1: k_counts_batch<<<ln.tiles, kTileThreads, 0, s>>>(b, step); break;
     case 2: k_scan_batch<<<b.nruns, kOneCta, 0, s>>>(b, step); break;
     case 3: k_parent_batch<<<ln.tiles, kTile, 0, s>>>(b, step); break;
-    case 4:
+    case 4: {
         k_plan<<<1, 32, 0, s>>>(b, step);
-        if (cudaPeekAtLastError() != cudaSuccess) break;
-        if (b.n_cta > 0) {
-            k_sweep_batch_cta<<<ln.cta_blocks, 256, ln.cta_smem, s>>>(b, step);
-            if (cudaPeekAtLastError() != cudaSuccess) break;
+        cudaError_t e = cudaPeekAtLastError();
+        if (e != cudaSuccess) return e;
+        // every segment on its own branch: the kernels overlap at their tails
+        if (ln.nseg > 1 && (e = cudaEventRecord(ln.fork, s)) != cudaSuccess) return e;
+        for (int i = 0; i < ln.nseg; i++) {
+            const BatchSeg& sg = ln.seg[i];
+            cudaStream_t t = ln.nseg > 1 ? ln.side[i] : s;
+            if (ln.nseg > 1 && (e = cudaStreamWaitEvent(t, ln.fork, 0)) != cudaSuccess) return e;
+            BatchDev arg = b;
+            int st = step, q0 = sg.q0, q1 = sg.q1, si = i;
+            void* args[] = {&arg, &st, &q0, &q1, &si};
+            if ((e = cudaLaunchKernel(batch_seg_kernel(sg.L, sg.G), dim3(sg.blocks), dim3(256), args, sg.smem, t)) !=
+                cudaSuccess)
+                return e;
+            if (ln.nseg > 1) {
+                if ((e = cudaEventRecord(ln.join[i], t)) != cudaSuccess) return e;
+                if ((e = cudaStreamWaitEvent(s, ln.join[i], 0)) != cudaSuccess) return e;
+            }
         }
-        if (b.n_cta < b.nruns) k_sweep_batch<<<ln.sweep_blocks, 256, ln.sweep_smem, s>>>(b, step);
         break;
+    }
     case 5: k_stats_batch<<<b.nruns, kOneCta, 0, s>>>(b, step); break;
     default: return cudaErrorInvalidValue;
     }
