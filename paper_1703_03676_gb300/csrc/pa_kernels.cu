@@ -643,10 +643,16 @@ __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunD
     const int gl = Gr::thread_in_group();
     const long long Ri = r.rec[step].R;
     unsigned families = 0;
-    for (unsigned first = Gr::first_item();; first = Gr::grab(r.work, red + 32) + Gr::static_items()) {
+    // A grid that holds the whole population (small runs) gives every group
+    // one fixed replica and no counter traffic; otherwise groups take
+    // replicas from the run's counter.
+    const bool covers = (long long)Gr::static_items() >= Ri;
+    for (unsigned first = covers ? Gr::first_item() : Gr::grab(r.work, red + 32);;) {
         const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
         if (base >= Ri) break;
         bits_group_step<L, G, D, kBytes>(r, step, (long long)first, first < Ri, sp, gl, red, families);
+        if (covers) break;
+        first = Gr::grab(r.work, red + 32);
     }
     families = group_sum<32>(families);
     if ((threadIdx.x & 31) == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
