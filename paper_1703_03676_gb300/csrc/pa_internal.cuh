@@ -169,6 +169,8 @@ struct Launch {
     int sweep_blocks, sweep_threads;  // persistent sweep grid
     int count_blocks;                 // tiles over cap
     size_t sweep_smem;
+    const void* sweep_cover;          // sweep instance with one fixed replica per group (grid holds the
+                                      // whole capacity), or null
 };
 
 cudaError_t launch_init(const RunDev* d_run, const RunDev& h, const Launch& ln, cudaStream_t s);

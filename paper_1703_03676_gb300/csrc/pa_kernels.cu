@@ -631,7 +631,10 @@ __global__ void __launch_bounds__(256) k_init_bits(const __grid_constant__ RunDe
     }
 }
 
-template <int L, int G, int D = 2, bool kBytes = false>
+// kCover: the grid holds every replica of the population (small runs):
+// each group sweeps one fixed replica and never touches the counter.
+// Otherwise the groups take replicas from the run's counter.
+template <int L, int G, int D = 2, bool kBytes = false, bool kCover = false>
 __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunDev r, int step)
 {
     using Gm = Lat<L, D>;
@@ -643,16 +646,17 @@ __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunD
     const int gl = Gr::thread_in_group();
     const long long Ri = r.rec[step].R;
     unsigned families = 0;
-    // A grid that holds the whole population (small runs) gives every group
-    // one fixed replica and no counter traffic; otherwise groups take
-    // replicas from the run's counter.
-    const bool covers = (long long)Gr::static_items() >= Ri;
-    for (unsigned first = covers ? Gr::first_item() : Gr::grab(r.work, red + 32);;) {
+    if constexpr (kCover) {
+        const unsigned first = Gr::first_item();
         const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
-        if (base >= Ri) break;
-        bits_group_step<L, G, D, kBytes>(r, step, (long long)first, first < Ri, sp, gl, red, families);
-        if (covers) break;
-        first = Gr::grab(r.work, red + 32);
+        if (base < Ri) bits_group_step<L, G, D, kBytes>(r, step, (long long)first, first < Ri, sp, gl, red, families);
+    } else {
+        for (;;) {
+            const unsigned first = Gr::grab(r.work, red + 32);
+            const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
+            if (base >= Ri) break;
+            bits_group_step<L, G, D, kBytes>(r, step, (long long)first, first < Ri, sp, gl, red, families);
+        }
     }
     families = group_sum<32>(families);
     if ((threadIdx.x & 31) == 0 && families) atomicAdd(&r.rec[step].fam, (unsigned long long)families);
@@ -737,10 +741,8 @@ __global__ void __launch_bounds__(256) k_init_bytes(const __grid_constant__ RunD
     const PhiloxKey key{r.key[0], r.key[1]};
     const long long R0 = r.R;
     const int N = r.N, NP = N / 2;
-    // first item fixed per warp, then from the counter (as Group::first_item)
-    const unsigned static_items = gridDim.x * (blockDim.x >> 5) * RPW;
-    for (unsigned base = (blockIdx.x * (blockDim.x >> 5) + warp) * RPW;;
-         base = warp_grab(r.work, (unsigned)RPW) + static_items) {
+    for (;;) {
+        const unsigned base = warp_grab(r.work, (unsigned)RPW);
         if (base >= R0) break;
         const long long k = (long long)base + g;
         const bool active = k < R0;
@@ -788,10 +790,8 @@ __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ Run
     const int L = r.L, half = r.half, NP = r.N / 2, QP = (NP + 3) / 4;
     const unsigned hm = row_magic(half);
     unsigned families = 0;
-    // first item fixed per warp, then from the counter (as Group::first_item)
-    const unsigned static_items = gridDim.x * (blockDim.x >> 5) * RPW;
-    for (unsigned base = (blockIdx.x * (blockDim.x >> 5) + warp) * RPW;;
-         base = warp_grab(r.work, (unsigned)RPW) + static_items) {
+    for (;;) {
+        const unsigned base = warp_grab(r.work, (unsigned)RPW);
         if (base >= Ri) break;
         const long long k = (long long)base + g;
         const bool active = k < Ri;
@@ -923,10 +923,8 @@ __global__ void __launch_bounds__(256) k_init_potts(const __grid_constant__ RunD
     const PhiloxKey key{r.key[0], r.key[1]};
     const long long R0 = r.R;
     const int N = r.N, q = r.potts_q;
-    // first item fixed per warp, then from the counter (as Group::first_item)
-    const unsigned static_items = gridDim.x * (blockDim.x >> 5) * RPW;
-    for (unsigned base = (blockIdx.x * (blockDim.x >> 5) + warp) * RPW;;
-         base = warp_grab(r.work, (unsigned)RPW) + static_items) {
+    for (;;) {
+        const unsigned base = warp_grab(r.work, (unsigned)RPW);
         if (base >= R0) break;
         const long long k = (long long)base + g;
         const bool active = k < R0;
@@ -972,10 +970,8 @@ __global__ void __launch_bounds__(256) k_sweep_potts(const __grid_constant__ Run
     const int L = r.L, half = r.half, NP = r.N / 2, QP = NP / 2, q = r.potts_q;
     const unsigned hm = row_magic(half);
     unsigned families = 0;
-    // first item fixed per warp, then from the counter (as Group::first_item)
-    const unsigned static_items = gridDim.x * (blockDim.x >> 5) * RPW;
-    for (unsigned base = (blockIdx.x * (blockDim.x >> 5) + warp) * RPW;;
-         base = warp_grab(r.work, (unsigned)RPW) + static_items) {
+    for (;;) {
+        const unsigned base = warp_grab(r.work, (unsigned)RPW);
         if (base >= Ri) break;
         const long long k = (long long)base + g;
         const bool active = k < Ri;
@@ -1293,11 +1289,9 @@ __global__ void __launch_bounds__(32 * msc_warps<L>()) k_init_msc(const __grid_c
     unsigned* red = smem + N;
     const PhiloxKey key{r.key[0], r.key[1]};
     const long long R0 = r.R, groups = (R0 + 31) / 32;
-    unsigned next_g = blockIdx.x;  // first group fixed per CTA, then from the counter
     for (;;) {
-        const unsigned G = next_g;
+        const unsigned G = msc_grab<L>(r.work, red + 2 * W * 32);
         if ((long long)G >= groups) break;
-        next_g = msc_grab<L>(r.work, red + 2 * W * 32) + gridDim.x;  // after this CTA's first group
         const long long k = 32ll * G + lane;
         const bool valid = k < R0;
         // INIT stream of replica k: site g = c*N/2 + b, counter (0, g>>2, 0, k)
@@ -1332,16 +1326,14 @@ __global__ void __launch_bounds__(32 * msc_warps<L>()) k_sweep_msc(const __grid_
     unsigned* red = smem + N;
     const int cur = (step - 1) & 1, nxt = step & 1;
     const long long Ri = r.rec[step].R, groups = (Ri + 31) / 32;
-    unsigned next_g = blockIdx.x;  // first group fixed per CTA, then from the counter
     const uint32_t t4m1 = r.thr[2 * step], t8m1 = r.thr[2 * step + 1];
     const PhiloxKey key{r.key[0], r.key[1]};
     const unsigned u0 = (unsigned)(step - 1) * (unsigned)r.theta;
     const int theta = r.theta;
     unsigned families = 0;
     for (;;) {
-        const unsigned G = next_g;
+        const unsigned G = msc_grab<L>(r.work, red + 2 * W * 32);
         if ((long long)G >= groups) break;
-        next_g = msc_grab<L>(r.work, red + 2 * W * 32) + gridDim.x;  // after this CTA's first group
         const long long k = 32ll * G + lane;
         const bool valid = k < Ri;
         // gather: bit `lane` of every site word comes from this lane's parent
@@ -1426,12 +1418,14 @@ __device__ __forceinline__ int pad_pow2(int n)
 // elsewhere) padded to a power of two, then the copy tables over [kmin, kmax].
 // Thread t sums the aligned block [t*chunk, (t+1)*chunk) with a carry stack
 // (the block's subtree), then a shared-memory tree joins neighbours.
-__device__ __forceinline__ void tables_body(const RunDev& r, int step)
+// kmin, kmax: occupied range of population i-1 (from its record, or handed
+// over in shared memory by the same CTA); sF, sU: optional shared-memory
+// copies of the copy tables over [kmin, kmax] (null: global only).
+__device__ __forceinline__ void tables_body(const RunDev& r, int step, int kmin, int kmax, uint32_t* sF = nullptr,
+                                            unsigned long long* sU = nullptr)
 {
     __shared__ double s[kOneCta];
     const int t = threadIdx.x;
-    const StepDev& prev = r.rec[step - 1];
-    const int kmin = prev.kmin, kmax = prev.kmax;
     const uint32_t* H = r.H[(step - 1) & 1];
     const double* tw = r.tw;
     const int P = pad_pow2(r.nlev);
@@ -1480,8 +1474,15 @@ __device__ __forceinline__ void tables_body(const RunDev& r, int step)
         const double tau = __ddiv_rn(__dmul_rn(Rd, tw[kk - kmin]), S);
         const double F = floor(tau);
         const double frac = __dsub_rn(tau, F);
-        r.F[kk] = (uint32_t)F;
-        r.U[kk] = (unsigned long long)ceil(__dmul_rn(frac, 4294967296.0));
+        const uint32_t f32 = (uint32_t)F;
+        const unsigned long long u64 = (unsigned long long)ceil(__dmul_rn(frac, 4294967296.0));
+        if (sF) {
+            sF[kk - kmin] = f32;
+            sU[kk - kmin] = u64;
+        } else {
+            r.F[kk] = f32;
+            r.U[kk] = u64;
+        }
     }
     uint32_t* Hn = r.H[step & 1];
     for (int i = t; i < 2 * r.nlev; i += kOneCta) Hn[i] = 0u;
@@ -1496,14 +1497,14 @@ __device__ __forceinline__ void tables_body(const RunDev& r, int step)
 __global__ void __launch_bounds__(kOneCta) k_tables(const __grid_constant__ RunDev r, int step)
 {
     if (*r.status) return;
-    tables_body(r, step);
+    tables_body(r, step, r.rec[step - 1].kmin, r.rec[step - 1].kmax);
 }
 
 __global__ void __launch_bounds__(kOneCta) k_tables_batch(const __grid_constant__ BatchDev b, int step)
 {
     const RunDev& r = b.runs[blockIdx.x];
     if (*r.status || step > r.nsteps) return;
-    tables_body(r, step);
+    tables_body(r, step, r.rec[step - 1].kmin, r.rec[step - 1].kmax);
 }
 
 // Copy numbers of the old population (Eq. resampling-factors): one Philox
@@ -1712,7 +1713,9 @@ __device__ __forceinline__ __int128 warp_sum128(__int128 v)
 
 // Integer moments of population i from its histograms (exact: every sum is
 // an integer, so no order matters), occupied range, running sum for MHR.
-__device__ __forceinline__ void stats_body(const RunDev& r, int step)
+// range (optional): shared-memory pair that receives (kmin, kmax) for the
+// rest of the CTA (valid after the next __syncthreads)
+__device__ __forceinline__ void stats_body(const RunDev& r, int step, int* range = nullptr)
 {
     __shared__ __int128 ws[5][kOneCta / 32];
     __shared__ int wmin[kOneCta / 32], wmax[kOneCta / 32];
@@ -1787,6 +1790,10 @@ __device__ __forceinline__ void stats_body(const RunDev& r, int step)
         if (lane == 0) {
             rec.kmin = mn;
             rec.kmax = mx;
+            if (range) {
+                range[0] = mn;
+                range[1] = mx;
+            }
         }
     }
     if (t == 0) {
@@ -1823,12 +1830,15 @@ __global__ void __launch_bounds__(kOneCta) k_stats_batch(const __grid_constant__
 // the chunks before it, so parent[] gets exactly the same old-slot order.
 // A chunk that would take R_i past the capacity sets the capacity status
 // before any of its parents is written.
-__device__ __forceinline__ void resample_small_body(const RunDev& r, int step)
+// Rp: R_{i-1}; lv0: this thread's first four old-slot levels (loaded by
+// the caller before the tables, -1 beyond Rp); sF, sU: the copy tables in
+// shared memory over [kmin, ...] (null: read the global tables).
+__device__ __forceinline__ void resample_small_body(const RunDev& r, int step, long long Rp, const int lv0[4],
+                                                    const uint32_t* sF, const unsigned long long* sU, int kmin)
 {
     __shared__ unsigned long long s_wsum[kOneCta / 32];
     __shared__ unsigned long long s_chunk;
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    const long long Rp = r.rec[step - 1].R;
     const int32_t* __restrict__ lev = r.elev[(step - 1) & 1];
     const PhiloxKey key{r.key[0], r.key[1]};
     const unsigned long long cap = (unsigned long long)r.cap;
@@ -1844,8 +1854,10 @@ __device__ __forceinline__ void resample_small_body(const RunDev& r, int step)
             for (int l = 0; l < 4; l++) {
                 const long long j = j0 + l;
                 if (j < Rp) {
-                    const int lv = lev[j];
-                    cnt[l] = (unsigned long long)r.F[lv] + (((unsigned long long)xs[l] < r.U[lv]) ? 1ull : 0ull);
+                    const int lv = c0 == 0 ? lv0[l] : lev[j];
+                    const uint32_t F = sF ? sF[lv - kmin] : r.F[lv];
+                    const unsigned long long U = sF ? sU[lv - kmin] : r.U[lv];
+                    cnt[l] = (unsigned long long)F + (((unsigned long long)xs[l] < U) ? 1ull : 0ull);
                 }
             }
         }
@@ -1896,17 +1908,36 @@ __device__ __forceinline__ void resample_small_body(const RunDev& r, int step)
     }
 }
 
+constexpr int kSmallLevels = 2048;  // copy tables kept in shared memory up to this range
+
 template <bool kStats>
 __global__ void __launch_bounds__(kOneCta) k_resample_small(const __grid_constant__ RunDev r, int step)
 {
+    __shared__ int s_range[2];
+    __shared__ uint32_t s_F[kSmallLevels];
+    __shared__ unsigned long long s_U[kSmallLevels];
     if (*r.status) return;
+    // loads that depend on nothing computed here, issued first: R_{i-1} and
+    // this thread's first four old-slot levels (written by the previous step)
+    const long long Rp = r.rec[step - 1].R;
+    const int32_t* __restrict__ lev = r.elev[(step - 1) & 1];
+    int lv0[4];
+#pragma unroll
+    for (int l = 0; l < 4; l++) lv0[l] = 4ll * threadIdx.x + l < Rp ? lev[4 * threadIdx.x + l] : -1;
+    int kmin, kmax;
     if constexpr (kStats) {
-        stats_body(r, step - 1);  // population i-1, deferred from its own step
+        stats_body(r, step - 1, s_range);  // population i-1, deferred from its own step
         __syncthreads();
+        kmin = s_range[0];
+        kmax = s_range[1];
+    } else {
+        kmin = r.rec[step - 1].kmin;
+        kmax = r.rec[step - 1].kmax;
     }
-    tables_body(r, step);
-    __syncthreads();  // F, U and rec[step] are read by the whole CTA below
-    resample_small_body(r, step);
+    const bool in_smem = kmax - kmin + 1 <= kSmallLevels;
+    tables_body(r, step, kmin, kmax, in_smem ? s_F : nullptr, in_smem ? s_U : nullptr);
+    __syncthreads();  // the copy tables and rec[step] are read by the whole CTA below
+    resample_small_body(r, step, Rp, lv0, in_smem ? s_F : nullptr, in_smem ? s_U : nullptr, kmin);
 }
 
 // ======================================================== batched sweep
@@ -2132,6 +2163,27 @@ const void* potts_ptr(bool init)
 
 }  // namespace
 
+// Square-lattice shapes with a sweep instance for grids that hold the whole
+// population (the default shapes of small runs: several threads per word)
+#define PA_COVER_SHAPES(X) X(8, 8) X(16, 32) X(32, 32)
+
+namespace {
+const void* cover_kernel(const RunDev& h)
+{
+    if (h.dim == 3 || !(h.fmt == 1 || (h.fmt == 0 && h.packed))) return nullptr;
+    const bool bytes = h.fmt == 0;
+    switch (h.L * 64 + h.gt) {
+#define PA_COVER_PTR(LL, GG)                                                                  \
+    case LL * 64 + GG:                                                                        \
+        return bytes ? (const void*)k_sweep_bits<LL, GG, 2, true, true>                     \
+                     : (const void*)k_sweep_bits<LL, GG, 2, false, true>;
+        PA_COVER_SHAPES(PA_COVER_PTR)
+#undef PA_COVER_PTR
+    default: return nullptr;
+    }
+}
+}  // namespace
+
 // The init / sweep kernel of a run's (format, L, threads per replica).
 const void* sweep_kernel(const RunDev& h, bool init)
 {
@@ -2278,6 +2330,18 @@ cudaError_t plan_sweep(const RunDev& h, Launch* ln)
     ln->sweep_threads = threads;
     ln->sweep_smem = smem;
     ln->sweep_blocks = (int)std::max(1ll, std::min((long long)sms * per_sm, need));
+    // a grid that holds the whole capacity can sweep with one fixed replica
+    // per group (no counter), where that instance exists
+    ln->sweep_cover = nullptr;
+    if (need <= (long long)sms * per_sm) {
+        const void* kc = cover_kernel(h);
+        int per_sm_c = 0;
+        if (kc && cudaFuncSetAttribute(kc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) == cudaSuccess &&
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm_c, kc, threads, smem) == cudaSuccess &&
+            per_sm_c >= 1 && (long long)sms * per_sm_c >= need)
+            ln->sweep_cover = kc;
+        cudaGetLastError();
+    }
     ln->count_blocks = h.ntiles;
     return cudaSuccess;
 }
@@ -2293,7 +2357,7 @@ cudaError_t launch_init(const RunDev* /*d_run*/, const RunDev& h, const Launch& 
 
 cudaError_t launch_sweep(const RunDev* /*d_run*/, const RunDev& h, const Launch& ln, int step, cudaStream_t s)
 {
-    const void* k = sweep_kernel(h, false);
+    const void* k = ln.sweep_cover ? ln.sweep_cover : sweep_kernel(h, false);
     if (!k) return cudaErrorInvalidConfiguration;
     RunDev arg = h;
     int st = step;
