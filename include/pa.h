@@ -399,15 +399,20 @@ void pa_batch_destroy(pa_batch *b);
 
 /* ---- serving ------------------------------------------------------------
  * A request loop with continuous batching (serving): requests
- * arrive at given times; each is admitted, in arrival order, once it has
- * arrived, fewer than max_active runs are resident and the sum of the
+ * arrive at given times; arrived requests are admitted in arrival order
+ * while fewer than max_active runs are resident and the sum of the
  * resident runs' pa_footprint_bytes stays within hbm_budget (a request
- * larger than the whole budget is admitted alone). Every admitted run gets
- * its own stream and stays resident on the device until it finishes; the
- * loop advances each run with pa_step_async, so the kernels of different
- * runs overlap on the GPU while others wait for their host-side step
- * decision, and a finished run frees its memory for the next request.
- * Results are those of each request run alone. */
+ * larger than the whole budget is admitted alone, once nothing else is
+ * resident). A request that does not fit may be passed by up to max_bypass
+ * later requests that do (0: strict arrival order); after that nothing more
+ * is admitted before it, so a large request is never starved. Every
+ * admitted run gets its own stream and stays resident on the device until
+ * it finishes; the loop advances each run with pa_step_async, so the
+ * kernels of different runs overlap on the GPU while others wait for their
+ * host-side step decision, and a finished run frees its memory for the next
+ * request. Runs allocate and free their device memory stream-ordered and
+ * reuse pinned host buffers, so admitting or retiring a run does not
+ * synchronise the device. Results are those of each request run alone. */
 typedef struct {
     double arrival_s;       /* seconds after the loop starts                     */
     pa_config cfg;
@@ -430,6 +435,9 @@ typedef struct {
                                (their memory stays allocated; the caller
                                destroys them) instead of destroying them        */
     double time_scale;      /* multiplies every arrival time (> 0)               */
+    int32_t max_bypass;     /* later requests that may pass one that does not fit
+                               (>= 0; 0: strict arrival order)                  */
+    int32_t pad;
 } pa_serve_options;
 
 /* Serve n requests sorted by arrival time; returns when all are finished.

@@ -429,14 +429,17 @@ class _RequestResult(ctypes.Structure):
 
 class _ServeOptions(ctypes.Structure):
     _fields_ = [("hbm_budget", ctypes.c_uint64), ("max_active", ctypes.c_int32), ("keep", ctypes.c_int32),
-                ("time_scale", ctypes.c_double)]
+                ("time_scale", ctypes.c_double), ("max_bypass", ctypes.c_int32), ("pad", ctypes.c_int32)]
 
 
-def serve(requests, hbm_budget: int = 0, max_active: int = 8, time_scale: float = 1.0, keep: bool = False):
+def serve(requests, hbm_budget: int = 0, max_active: int = 8, time_scale: float = 1.0, keep: bool = False,
+          max_bypass: int = 8):
     """Run the native request loop (pa_serve) on [(arrival_s, PAConfig)]
-    sorted by arrival. Returns (results, runs): results is a list of dicts
-    (admit_s, finish_s, attempts, steps, footprint, status); runs holds the
-    finished runs as PARun objects when keep is set."""
+    sorted by arrival. A request that does not fit the budget may be passed
+    by up to max_bypass later ones (0: strict arrival order). Returns
+    (results, runs): results is a list of dicts (admit_s, finish_s,
+    attempts, steps, footprint, status); runs holds the finished runs as
+    PARun objects when keep is set."""
     n = len(requests)
     reqs = (_Request * max(n, 1))()
     for i, (t, c) in enumerate(requests):
@@ -444,7 +447,7 @@ def serve(requests, hbm_budget: int = 0, max_active: int = 8, time_scale: float 
         reqs[i].cfg = c._c()
     res = (_RequestResult * max(n, 1))()
     ctxs = (_P * max(n, 1))()
-    opt = _ServeOptions(int(hbm_budget), int(max_active), int(bool(keep)), float(time_scale))
+    opt = _ServeOptions(int(hbm_budget), int(max_active), int(bool(keep)), float(time_scale), int(max_bypass), 0)
     _check(lib().pa_serve(reqs, n, ctypes.byref(opt), res, ctxs if keep else None), "pa_serve")
     out = [{f: getattr(res[i], f) for f, _ in _RequestResult._fields_ if f != "pad"} for i in range(n)]
     runs = []

@@ -103,6 +103,7 @@ struct pa_ctx {
     // adaptive runs: record, status and energy histogram of the last enqueued
     // step stream into pinned memory; ev_ready marks their arrival
     void* h_down = nullptr;
+    size_t h_down_bytes = 0;
     cudaEvent_t ev_ready = nullptr;
     unsigned* d_key = nullptr;    // Philox key in device memory
     cudaGraphExec_t graph = nullptr;  // steps 1..n of the fixed schedule
@@ -299,12 +300,17 @@ size_t footprint(const pa_config& c)
     return b;
 }
 
+// Device buffers of a run are stream-ordered allocations on the run's
+// stream (cudaMallocAsync / cudaFreeAsync): creating or destroying a run
+// does not synchronise the device, so runs resident beside it (serving,
+// batches) keep running. pa_create synchronises its own stream once after
+// allocating, before the host uploads its tables.
 template <class T>
 pa_status dev_alloc(pa_ctx* c, T** p, size_t count)
 {
     void* q = nullptr;
     const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-    cudaError_t e = cudaMalloc(&q, bytes);
+    cudaError_t e = cudaMallocAsync(&q, bytes, c->stream);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return e == cudaErrorMemoryAllocation ? PA_ENOMEM : PA_ECUDA;
@@ -319,6 +325,45 @@ pa_status dev_alloc(pa_ctx* c, T** p, size_t count)
         pa_status s_ = (x);              \
         if (s_ != PA_OK) return s_;      \
     } while (0)
+
+// Pinned host staging buffers, kept for reuse by later runs of the process
+// (size classes of powers of two): freeing pinned memory synchronises the
+// device, which would stall every other run's stream.
+std::mutex g_pinned_mu;
+std::multimap<size_t, void*> g_pinned_free;
+
+size_t pinned_class(size_t bytes)
+{
+    size_t c = 4096;
+    while (c < bytes) c <<= 1;
+    return c;
+}
+
+void* pinned_alloc(size_t bytes)
+{
+    const size_t cls = pinned_class(bytes);
+    {
+        std::lock_guard<std::mutex> g(g_pinned_mu);
+        auto it = g_pinned_free.find(cls);
+        if (it != g_pinned_free.end()) {
+            void* p = it->second;
+            g_pinned_free.erase(it);
+            return p;
+        }
+    }
+    void* p = nullptr;
+    if (cudaMallocHost(&p, cls) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return p;
+}
+
+void pinned_release(void* p, size_t bytes)
+{
+    std::lock_guard<std::mutex> g(g_pinned_mu);
+    g_pinned_free.emplace(pinned_class(bytes), p);
+}
 
 // ---------------------------------------------------------------- profiling
 pa_status prof_record(pa_ctx* c, int phase)
@@ -713,9 +758,9 @@ pa_status free_all(pa_ctx* c)
     if (c->graph) cudaGraphExecDestroy(c->graph);
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     for (cudaEvent_t e : c->gev) cudaEventDestroy(e);
-    for (void* p : c->allocs) cudaFree(p);
-    if (c->h_stage) cudaFreeHost(c->h_stage);
-    if (c->h_down) cudaFreeHost(c->h_down);
+    for (void* p : c->allocs) cudaFreeAsync(p, c->stream);
+    if (c->h_stage) pinned_release(c->h_stage, c->h_stage_bytes);
+    if (c->h_down) pinned_release(c->h_down, c->h_down_bytes);
     if (c->ev_ready) cudaEventDestroy(c->ev_ready);
     if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
     return PA_OK;
@@ -963,6 +1008,7 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     PA_ALLOC(h.work, 4);
     PA_ALLOC(c->d_key, 4);
     h.key = c->d_key;
+    if (cudaStreamSynchronize(c->stream) != cudaSuccess) return fail(PA_ECUDA);  // allocations ready
     if (Jr) {
         std::vector<uint32_t> masks;
         std::vector<uint8_t> bytes;
@@ -970,13 +1016,15 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
         if (cfg->spin_format == PA_SPIN_BITS32) {
             uint32_t* d = nullptr;
             PA_ALLOC(d, masks.size());
-            if (cudaMemcpy(d, masks.data(), masks.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+                cudaMemcpy(d, masks.data(), masks.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
                 return fail(PA_ECUDA);
             h.bonds = d;
         } else {
             uint8_t* d = nullptr;
             PA_ALLOC(d, bytes.size());
-            if (cudaMemcpy(d, bytes.data(), bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+            if (cudaStreamSynchronize(c->stream) != cudaSuccess ||
+                cudaMemcpy(d, bytes.data(), bytes.size(), cudaMemcpyHostToDevice) != cudaSuccess)
                 return fail(PA_ECUDA);
             h.bonds8 = d;
         }
@@ -984,9 +1032,10 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
 #undef PA_ALLOC
     // staging for adaptive uploads (level weights + thresholds)
     c->h_stage_bytes = N1 * sizeof(double) + 64;
-    if (cudaMallocHost(&c->h_stage, c->h_stage_bytes) != cudaSuccess) return fail(PA_ENOMEM);
+    if (!(c->h_stage = pinned_alloc(c->h_stage_bytes))) return fail(PA_ENOMEM);
     if (c->adaptive) {
-        if (cudaMallocHost(&c->h_down, sizeof(StepDev) + 16 + 4 * N1) != cudaSuccess) return fail(PA_ENOMEM);
+        c->h_down_bytes = sizeof(StepDev) + 16 + 4 * N1;
+        if (!(c->h_down = pinned_alloc(c->h_down_bytes))) return fail(PA_ENOMEM);
         if (cudaEventCreateWithFlags(&c->ev_ready, cudaEventDisableTiming) != cudaSuccess) return fail(PA_ECUDA);
     }
     c->T4.push_back(1ull << 32);
@@ -1714,7 +1763,7 @@ void batch_free(pa_batch* b)
         c->own_stream = false;
         pa_destroy(c);
     }
-    for (void* p : b->allocs) cudaFree(p);
+    for (void* p : b->allocs) cudaFreeAsync(p, b->stream);
     for (int i = 0; i < pa::kMaxBatchSegs; i++) {
         if (b->ln.side[i]) cudaStreamDestroy(b->ln.side[i]);
         if (b->ln.join[i]) cudaEventDestroy(b->ln.join[i]);
@@ -1871,7 +1920,7 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
         for (int t = 0; t < hr[(size_t)i].ntiles; t++) tile_run.push_back(i);
     }
     auto dalloc = [&](void** p, size_t bytes) -> bool {
-        if (cudaMalloc(p, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+        if (cudaMallocAsync(p, std::max<size_t>(bytes, 16), b->stream) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
@@ -1886,6 +1935,7 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
         !dalloc((void**)&d_tile_run, 4 * tile_run.size()) || !dalloc((void**)&d_tile_first, 4 * (size_t)n) ||
         !dalloc((void**)&d_off, 8 * (size_t)(n + 1)) || !dalloc((void**)&d_work, 4 * pa::kMaxBatchSegs))
         return fail(PA_ENOMEM);
+    if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fail(PA_ECUDA);  // allocations ready
     if (cudaMemcpy(d_runs, hr.data(), sizeof(RunDev) * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d_order, order.data(), 4 * (size_t)n, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(d_tile_run, tile_run.data(), 4 * tile_run.size(), cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1992,7 +2042,8 @@ void pa_batch_destroy(pa_batch* b)
 extern "C" pa_status pa_serve(const pa_request* reqs, int32_t n, const pa_serve_options* opt,
                               pa_request_result* out, pa_ctx** out_ctx)
 {
-    if (!reqs || !opt || !out || n < 0 || opt->max_active < 1 || !(opt->time_scale > 0.0)) return PA_EINVAL;
+    if (!reqs || !opt || !out || n < 0 || opt->max_active < 1 || !(opt->time_scale > 0.0) || opt->max_bypass < 0)
+        return PA_EINVAL;
     if (opt->keep && !out_ctx) return PA_EINVAL;
     for (int32_t i = 0; i < n; i++) {
         if (i > 0 && reqs[i].arrival_s < reqs[i - 1].arrival_s) return PA_EINVAL;
@@ -2010,29 +2061,44 @@ extern "C" pa_status pa_serve(const pa_request* reqs, int32_t n, const pa_serve_
         bool enq_done;
     };
     std::vector<Active> active;
+    std::vector<char> admitted((size_t)n, 0);
     size_t used = 0;
-    int32_t next = 0, finished = 0;
+    int32_t head = 0, finished = 0;  // head: oldest request not admitted yet
+    int32_t head_passed = 0;          // later requests admitted while the head waits
     while (finished < n) {
         bool progress = false;
-        // admission: arrival order, concurrency limit, HBM budget
-        while (next < n && reqs[next].arrival_s * opt->time_scale <= now_s() &&
-               (int32_t)active.size() < opt->max_active) {
-            const size_t fp = pa_footprint_bytes(&reqs[next].cfg);
-            if (opt->hbm_budget && !active.empty() && used + fp > opt->hbm_budget) break;
-            pa_request_result& r = out[next];
+        // admission: arrived requests in arrival order, within the concurrency
+        // limit and the HBM budget; a request that does not fit may be passed
+        // by up to max_bypass later ones, after which admission waits for it
+        for (int32_t q = head; q < n && reqs[q].arrival_s * opt->time_scale <= now_s() &&
+                               (int32_t)active.size() < opt->max_active;
+             q++) {
+            if (admitted[(size_t)q]) continue;
+            const size_t fp = pa_footprint_bytes(&reqs[q].cfg);
+            const bool fits = !opt->hbm_budget || active.empty() || used + fp <= opt->hbm_budget;
+            if (!fits) {
+                if (q == head && head_passed >= opt->max_bypass) break;
+                continue;
+            }
+            pa_request_result& r = out[q];
             r.admit_s = now_s();
             r.footprint = (int64_t)fp;
             pa_ctx* c = nullptr;
-            const pa_status st = pa_create(&reqs[next].cfg, nullptr, &c);
+            const pa_status st = pa_create(&reqs[q].cfg, nullptr, &c);
             if (st != PA_OK) {
                 r.status = st;
                 r.finish_s = now_s();
                 finished++;
             } else {
-                active.push_back({next, c, fp, false});
+                active.push_back({q, c, fp, false});
                 used += fp;
             }
-            next++;
+            admitted[(size_t)q] = 1;
+            if (q != head) head_passed++;
+            while (head < n && admitted[(size_t)head]) {
+                head++;
+                head_passed = 0;
+            }
             progress = true;
         }
         // advance every resident run

@@ -41,9 +41,9 @@ def test_served_equals_alone_and_budget_holds():
     reqs = requests()
     fps = [eng.footprint_bytes(c) for _, c in reqs]
     budget = int(2.5 * max(fps))  # at most a few resident at once
-    res, runs = eng.serve(reqs, hbm_budget=budget, max_active=4, keep=True)
+    res, runs = eng.serve(reqs, hbm_budget=budget, max_active=4, keep=True, max_bypass=0)
     assert all(r["status"] == 0 for r in res), res
-    # admission: in arrival order, within budget and concurrency at all times
+    # admission: in arrival order (no bypass), within budget and concurrency at all times
     admits = [r["admit_s"] for r in res]
     assert admits == sorted(admits)
     for i, (t, _) in enumerate(reqs):
@@ -111,6 +111,34 @@ def test_served_other_models_equal_alone():
     reqs = [(0.001 * q, c) for q, c in enumerate(cfgs)]
     res, runs = eng.serve(reqs, hbm_budget=1 << 34, max_active=3, keep=True)
     assert all(r["status"] == 0 for r in res), res
+    for (_, c), r in zip(reqs, runs):
+        alone = eng.PARun(eng.PAConfig(**c.__dict__))
+        alone.run()
+        np.testing.assert_array_equal(r.rows(), alone.rows())
+        np.testing.assert_array_equal(r.population(), alone.population())
+        alone.close()
+        r.close()
+
+
+def test_large_request_passed_by_small_ones_then_admitted_alone():
+    """A request larger than the whole budget is passed by at most max_bypass
+    later small requests, then admitted once nothing else is resident and runs
+    alone; every result equals its run alone."""
+    def small(q):
+        return eng.PAConfig(L=16, R=800, theta=3, beta_f=0.3, dbeta=0.05, seed=2000 + q, spin_format=B32)
+    big = eng.PAConfig(L=128, R=3000, theta=2, beta_f=0.2, dbeta=0.05, seed=2100, spin_format=B32)
+    reqs = [(0.0, small(0)), (0.0005, big)] + [(0.001 + 0.0005 * q, small(q + 1)) for q in range(8)]
+    fp_small, fp_big = eng.footprint_bytes(small(0)), eng.footprint_bytes(big)
+    budget = 3 * fp_small
+    assert fp_big > budget
+    res, runs = eng.serve(reqs, hbm_budget=budget, max_active=3, keep=True, max_bypass=3)
+    assert all(r["status"] == 0 for r in res), res
+    big_admit, big_finish = res[1]["admit_s"], res[1]["finish_s"]
+    passed = [q for q in range(2, len(reqs)) if res[q]["admit_s"] < big_admit]
+    assert 1 <= len(passed) <= 3, passed
+    for q, r in enumerate(res):
+        if q != 1:  # nothing else resident while the big run is
+            assert r["finish_s"] <= big_admit + 1e-6 or r["admit_s"] >= big_finish - 1e-6, (q, r, res[1])
     for (_, c), r in zip(reqs, runs):
         alone = eng.PARun(eng.PAConfig(**c.__dict__))
         alone.run()
