@@ -357,12 +357,15 @@ pa_status pa_tune_cache_lookup(const char *path, const pa_tune_key *key, pa_tune
  * Many independent fixed-schedule runs (batched runs; Sec. 2.2 notes
  * that independent runs combine by free-energy weights) stepped together:
  * every bookkeeping phase of a temperature step is one launch for all runs.
- * The sweep's work queue (one item per replica of the runs with
- * group_threads 256 at L = 128, 256, 512; (run, replica batch) items of the
- * warp-group runs) is cut into segments of runs sharing (L, group_threads),
- * each ordered by descending work per replica and swept by a persistent
- * kernel compiled for that shape; the segments' kernels run on parallel
- * branches of the graph, so they overlap at their tails. The whole schedule
+ * A run that fills the device alone (group_threads 256, one replica per
+ * CTA at L = 128, 256, 512; or a warp-group run whose capacity needs at
+ * least as many CTAs as the device keeps resident) is swept by its own sweep
+ * kernel, the one it runs alone with. The other runs' sweep work queue
+ * ((run, replica batch) items) is cut into segments of runs sharing (L,
+ * group_threads), each ordered by descending work per replica and swept by
+ * a persistent kernel compiled for that shape. The segments' kernels and
+ * the own kernels (in turn on four streams) run on parallel branches of
+ * the graph, so they overlap at their tails. The whole schedule
  * is one CUDA graph, captured on the first launch and reused after
  * pa_batch_reset.
  * Each run's results are those of the same pa_config run alone, bit for
@@ -393,7 +396,7 @@ pa_status pa_batch_get(pa_batch *b, int32_t i, pa_ctx **out);
  * [4] plan + sweep, [5] stats. */
 pa_status pa_batch_phase_times(pa_batch *b, double ms[7], int64_t launches[7]);
 /* Threads per replica used for run i and the persistent grid size of the
- * sweep kernel that runs it (CTA-group or warp-group kernel). */
+ * sweep kernel that runs it (its own kernel, or its segment's kernel). */
 pa_status pa_batch_shape(pa_batch *b, int32_t i, int32_t *group_threads, int32_t *sweep_blocks);
 void pa_batch_destroy(pa_batch *b);
 
@@ -535,6 +538,20 @@ pa_status pa_measure_rng_peak(int64_t blocks_per_thread, uint32_t *dev_sink, voi
  * or iteration count. */
 pa_status pa_measure_pipe_peak(int pipe, int64_t iters, uint32_t *dev_sink, void *cuda_stream,
                                double *lane_ops_per_ns);
+
+/* Self-test of the bounded wait behind the sweep's bulk prefetch (the
+ * one-replica-per-CTA sweep at L = 128 loads the next replica with a bulk
+ * copy completed on a shared-memory barrier, and gives up with PA_ETIMEOUT
+ * after a bounded number of polls instead of spinning on). One 32-thread
+ * CTA arms the same barrier for `bytes` bytes (16..4096, a multiple of 16)
+ * of a device pattern; with copy != 0 it issues the copy, with copy == 0
+ * nothing ever delivers them. Every thread polls at most `tries` times
+ * (>= 1). Returns PA_OK when the bytes landed and equal the pattern,
+ * PA_ETIMEOUT when the wait ran out (nothing is left in flight and the
+ * context stays usable), PA_ECUDA if they landed but differ, PA_EINVAL for
+ * bad arguments. Allocates and frees its buffers; synchronous on
+ * `cuda_stream`. */
+pa_status pa_selftest_bulk_wait(int32_t bytes, int32_t copy, int32_t tries, void *cuda_stream);
 
 #ifdef __cplusplus
 }

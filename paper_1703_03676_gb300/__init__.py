@@ -132,6 +132,7 @@ SIGNATURES = [
                                  ctypes.POINTER(ctypes.c_double)]),
     ("pa_measure_rng_peak", ctypes.c_int, [ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
     ("pa_measure_pipe_peak", ctypes.c_int, [ctypes.c_int, ctypes.c_int64, _P, _P, ctypes.POINTER(ctypes.c_double)]),
+    ("pa_selftest_bulk_wait", ctypes.c_int, [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, _P]),
     ("pa_resample", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int64, _P,
                                    ctypes.c_int64, _I64P, _P]),
     ("pa_resample_noalloc", ctypes.c_int, [_P, ctypes.c_int64, _P, _P, ctypes.c_int64, ctypes.c_uint64,
@@ -580,6 +581,13 @@ def measure_rng_peak(blocks_per_thread: int = 4096, stream=None) -> float:
     _check(lib().pa_measure_rng_peak(blocks_per_thread, ctypes.c_void_p(sink.data_ptr()), _stream_handle(stream),
                                      ctypes.byref(out)), "pa_measure_rng_peak")
     return out.value
+
+
+def selftest_bulk_wait(nbytes: int, copy: bool, tries: int, stream=None) -> str:
+    """Outcome of the bounded bulk-copy wait self-test (pa_selftest_bulk_wait):
+    "ok" when the bytes landed and match, "timeout" when the wait ran out."""
+    return _STATUS.get(lib().pa_selftest_bulk_wait(nbytes, 1 if copy else 0, tries, _stream_handle(stream)),
+                       "unknown")
 
 
 PIPE_WIDE_MUL, PIPE_LOP3, PIPE_IMAD = 0, 1, 2

@@ -1661,6 +1661,25 @@ pa_status pa_gather(const uint32_t* src, int64_t n_src, const uint32_t* parent, 
     return hbad ? PA_EINVAL : PA_OK;
 }
 
+pa_status pa_selftest_bulk_wait(int32_t bytes, int32_t copy, int32_t tries, void* stream)
+{
+    if (bytes < 16 || bytes > 4096 || bytes % 16 || tries < 1) return PA_EINVAL;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t* src = nullptr;  // pattern, then the kernel's result word
+    PA_CUDA(cudaMalloc(&src, (size_t)bytes + 16));
+    std::vector<uint32_t> pat((size_t)bytes / 4 + 4);
+    for (size_t i = 0; i < pat.size(); i++) pat[i] = 0x9E3779B9u * (uint32_t)(i + 1);
+    int res = 2;
+    cudaError_t e = cudaMemcpyAsync(src, pat.data(), (size_t)bytes + 16, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = pa::launch_bulk_selftest(src, bytes, copy != 0, tries, (int*)(src + bytes / 4), s);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&res, src + bytes / 4, 4, cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    cudaFree(src);
+    if (e != cudaSuccess) return from_cuda(e, __LINE__);
+    if (res == pa::kStatusTimeout) return PA_ETIMEOUT;
+    return res == 0 ? PA_OK : PA_ECUDA;
+}
+
 pa_status pa_measure_rng_peak(int64_t blocks_per_thread, uint32_t* sink, void* stream, double* words_per_ns)
 {
     if (blocks_per_thread < 8 || !sink || !words_per_ns) return PA_EINVAL;
@@ -1737,6 +1756,11 @@ struct pa_batch {
     double phase_ms[7] = {0, 0, 0, 0, 0, 0, 0};
     long long phase_n[7] = {0, 0, 0, 0, 0, 0, 0};
     std::vector<int> order;       // queue position -> run
+    // runs of one replica per CTA: descriptors, sweep plans and last steps
+    // (BatchLaunch points at these), and their index among the runs
+    std::vector<pa::RunDev> own_h;
+    std::vector<pa::Launch> own_ln;
+    std::vector<int> own_last, own_run;
 };
 
 namespace {
@@ -1767,6 +1791,10 @@ void batch_free(pa_batch* b)
     for (int i = 0; i < pa::kMaxBatchSegs; i++) {
         if (b->ln.side[i]) cudaStreamDestroy(b->ln.side[i]);
         if (b->ln.join[i]) cudaEventDestroy(b->ln.join[i]);
+    }
+    for (int i = 0; i < pa::kBatchOwnStreams; i++) {
+        if (b->ln.own_side[i]) cudaStreamDestroy(b->ln.own_side[i]);
+        if (b->ln.own_join[i]) cudaEventDestroy(b->ln.own_join[i]);
     }
     if (b->ln.fork) cudaEventDestroy(b->ln.fork);
     if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
@@ -1879,18 +1907,32 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
         b->max_steps = std::max(b->max_steps, (int)m->n_fixed);
     }
     // queue order: runs grouped by shape (larger lattices first), each group
-    // by descending work per replica (theta * N); each group is one segment
+    // by descending work per replica (theta * N). A run that fills the device
+    // alone (one replica per CTA, or a warp-group run whose sweep grid is all
+    // the device keeps resident) is swept by its own sweep kernel, the one it
+    // runs alone with; beside the others, its tail overlaps theirs. The other
+    // runs of one shape form a segment, swept by one kernel.
+    auto own = [&](int i) { return hr[(size_t)i].gt > 32 || b->runs[(size_t)i]->ln.sweep_full; };
     std::vector<int> order((size_t)n), tile_run, tile_first((size_t)n);
     for (int i = 0; i < n; i++) order[(size_t)i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         const RunDev &a = hr[(size_t)x], &c = hr[(size_t)y];
+        if (own(x) != own(y)) return own(x);  // own-kernel runs first: segments stay contiguous
         if (a.L != c.L) return a.L > c.L;
         if (a.gt != c.gt) return a.gt > c.gt;
         return (long long)a.theta * a.N > (long long)c.theta * c.N;
     });
     b->ln.nseg = 0;
     for (int q = 0; q < n; q++) {
-        const RunDev& a = hr[(size_t)order[(size_t)q]];
+        const int i = order[(size_t)q];
+        const RunDev& a = hr[(size_t)i];
+        if (own(i)) {
+            b->own_h.push_back(a);
+            b->own_ln.push_back(b->runs[(size_t)i]->ln);
+            b->own_last.push_back((int)b->runs[(size_t)i]->n_fixed);
+            b->own_run.push_back(i);
+            continue;
+        }
         pa::BatchSeg* last = b->ln.nseg ? &b->ln.seg[b->ln.nseg - 1] : nullptr;
         if (last && last->L == a.L && last->G == a.gt) {
             last->q1 = q + 1;
@@ -1908,11 +1950,20 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
             return fail(PA_EINVAL);
         }
     }
-    if (b->ln.nseg > 1) {
+    b->ln.nown = (int)b->own_h.size();
+    b->ln.own_h = b->own_h.data();
+    b->ln.own_ln = b->own_ln.data();
+    b->ln.own_last = b->own_last.data();
+    const int ncs = std::min(b->ln.nown, pa::kBatchOwnStreams);
+    if (b->ln.nseg + ncs > 1) {
         if (cudaEventCreateWithFlags(&b->ln.fork, cudaEventDisableTiming) != cudaSuccess) return fail(PA_ECUDA);
         for (int i = 0; i < b->ln.nseg; i++)
             if (cudaStreamCreateWithFlags(&b->ln.side[i], cudaStreamNonBlocking) != cudaSuccess ||
                 cudaEventCreateWithFlags(&b->ln.join[i], cudaEventDisableTiming) != cudaSuccess)
+                return fail(PA_ECUDA);
+        for (int i = 0; i < ncs; i++)
+            if (cudaStreamCreateWithFlags(&b->ln.own_side[i], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b->ln.own_join[i], cudaEventDisableTiming) != cudaSuccess)
                 return fail(PA_ECUDA);
     }
     for (int i = 0; i < n; i++) {
@@ -2020,6 +2071,8 @@ pa_status pa_batch_shape(pa_batch* b, int32_t i, int32_t* group_threads, int32_t
     if (group_threads) *group_threads = b->runs[(size_t)i]->h.gt;
     if (sweep_blocks) {
         *sweep_blocks = 0;
+        for (size_t j = 0; j < b->own_run.size(); j++)
+            if (b->own_run[j] == i) *sweep_blocks = b->own_ln[j].sweep_blocks;
         for (int q = 0; q < (int)b->order.size(); q++)
             if (b->order[(size_t)q] == i)
                 for (int s = 0; s < b->ln.nseg; s++)

@@ -250,6 +250,60 @@ __device__ __forceinline__ uint32_t metropolis_word3(uint32_t s, uint32_t n1, ui
     return s ^ (ge3 | (acc4 & eq2) | (acc8 & eq1) | (acc12 & eq0));
 }
 
+// ======================================================== bulk copies
+// One-dimensional bulk copy global -> shared memory through the tensor-memory
+// accelerator (cp.async.bulk), completion tracked by an mbarrier in shared
+// memory (expect-tx bytes; the barrier's phase flips when they have landed).
+// Every wait is bounded: after kBulkWaitTries failed polls the caller gets
+// false and reports a timeout instead of spinning on.
+constexpr int kBulkWaitTries = 1 << 20;
+
+__device__ __forceinline__ unsigned smem_u32(const void* p)
+{
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long* m)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(m)) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+// issued by one thread: the barrier expects `bytes`, the copy delivers them
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, unsigned bytes, unsigned long long* m)
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // order earlier generic accesses of dst
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes) : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                     smem_u32(dst)),
+                 "l"(src), "r"(bytes), "r"(smem_u32(m))
+                 : "memory");
+}
+
+// wait until the barrier has completed the phase with this parity
+__device__ __forceinline__ bool mbar_wait(unsigned long long* m, unsigned parity, int tries = kBulkWaitTries)
+{
+    for (int i = 0; i < tries; i++) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(smem_u32(m)), "r"(parity)
+            : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// the next replica's load, issued by thread 0 once the current replica's
+// first colour phase is done (src null: no next replica)
+struct Prefetch {
+    const uint32_t* src;
+    uint32_t* dst;
+    unsigned long long* mbar;
+    unsigned bytes;
+};
+
 // ======================================================== shared epilogue
 // 128-bit unsigned accumulation (lo, hi) with an explicit carry: integer
 // addition is associative, so the total does not depend on the order.
@@ -490,9 +544,13 @@ __host__ __device__ constexpr bool bits_group_ok(int G)
 
 // kBytes: the population is stored one byte per site (PA_SPIN_INT8) and
 // packed into the same shared-memory words on load, unpacked on store.
+// pf (CTA groups): the replica is already in sp (loaded by a bulk copy),
+// and pf describes the next replica's bulk copy, issued after the first
+// colour phase; null: load the replica here.
 template <int L, int G, int D = 2, bool kBytes = false>
 __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long long k, bool active,
-                                                uint32_t* sp, int gl, unsigned* red, unsigned& families)
+                                                uint32_t* sp, int gl, unsigned* red, unsigned& families,
+                                                const Prefetch* pf = nullptr)
 {
     using Gm = Lat<L, D>;
     using Gr = Group<G>;
@@ -514,7 +572,7 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
     uint32_t p = 0;
     if (active) {
         p = r.parent[k];
-        load_replica<L, G, D, kBytes>(sp, r.pop[cur], p, gl);
+        if (!pf) load_replica<L, G, D, kBytes>(sp, r.pop[cur], p, gl);
     }
     Gr::sync();
     for (int sw = 0; sw < theta; sw++) {
@@ -558,6 +616,9 @@ __device__ __forceinline__ void bits_group_step(const RunDev& r, int step, long 
                 }
             }
             Gr::sync();
+            if constexpr (Gr::kCta) {
+                if (pf && sw == 0 && c == 0 && threadIdx.x == 0 && pf->src) bulk_load(pf->dst, pf->src, pf->bytes, pf->mbar);
+            }
         }
     }
     unsigned anti = 0, ups = 0;
@@ -650,6 +711,46 @@ __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunD
         const unsigned first = Gr::first_item();
         const unsigned base = Gr::kCta ? first : first - (threadIdx.x & 31) / G;
         if (base < Ri) bits_group_step<L, G, D, kBytes>(r, step, (long long)first, first < Ri, sp, gl, red, families);
+    } else if constexpr (Gr::kCta && !kBytes && Gm::WORDS <= kPrefetchMaxWords) {
+        static_assert(Gm::WORDS % 4 == 0, "bulk copies move multiples of 16 bytes");
+        // One replica per CTA, two replica buffers: while the CTA sweeps
+        // replica `cur` in buf[b], a bulk copy brings the next one's parent
+        // into buf[b ^ 1] (shared memory: buf0, buf1, then the reduction words).
+        __shared__ __align__(8) unsigned long long s_mbar[2];
+        uint32_t* const buf0 = smem;
+        uint32_t* const buf1 = smem + Gm::WORDS;
+        unsigned* red2 = smem + 2 * Gm::WORDS;
+        const int cur_pop = (step - 1) & 1;
+        const unsigned bytes = Gm::WORDS * 4u;
+        if (threadIdx.x == 0) {
+            mbar_init(&s_mbar[0]);
+            mbar_init(&s_mbar[1]);
+        }
+        unsigned cur = Gr::grab(r.work, red2 + 32);  // (synchronises: the barriers are initialised)
+        if (threadIdx.x == 0 && cur < Ri)
+            bulk_load(buf0, r.pop[cur_pop] + (size_t)r.parent[cur] * Gm::WORDS, bytes, &s_mbar[0]);
+        // buffer b (0/1) alternates; each barrier's phase parity flips once
+        // per use of its buffer, i.e. every second replica
+        unsigned b = 0, phases = 0;  // bit i: parity to wait for on barrier i
+        for (;;) {
+            if (cur >= Ri) break;
+            const unsigned nxt = Gr::grab(r.work, red2 + 32);
+            Prefetch pf{nullptr, b ? buf0 : buf1, &s_mbar[b ^ 1u], bytes};
+            if (threadIdx.x == 0 && nxt < Ri) pf.src = r.pop[cur_pop] + (size_t)r.parent[nxt] * Gm::WORDS;
+            const unsigned par = (phases >> b) & 1u;
+            if (!mbar_wait(&s_mbar[b], par)) {
+                // the copy did not land in time: report it and leave no copy
+                // in flight (a second bounded wait), then stop
+                if (threadIdx.x == 0) *r.status = kStatusTimeout;
+                mbar_wait(&s_mbar[b], par);
+                break;
+            }
+            phases ^= 1u << b;
+            bits_group_step<L, G, D, kBytes>(r, step, (long long)cur, true, b ? buf1 : buf0, gl, red2, families,
+                                              &pf);
+            cur = nxt;
+            b ^= 1u;
+        }
     } else {
         for (;;) {
             const unsigned first = Gr::grab(r.work, red + 32);
@@ -1980,52 +2081,74 @@ __device__ __forceinline__ int batch_run_of(const long long* off, int n, long lo
     return lo;
 }
 
-// Persistent sweep of the segment q0..q1-1 of the queue (runs of one shape):
-// with G = 256 each CTA takes one replica at a time (colour phases separated
-// by __syncthreads), with G <= 32 each warp takes (run, replica batch)
-// items, from the segment's counter work[seg].
+// Persistent sweep of the segment q0..q1-1 of the queue (warp-group runs of
+// one shape): each warp takes (run, replica batch) items from the segment's
+// counter work[seg]. (Runs of one replica per CTA are swept by their own
+// sweep kernel, launched beside the segments.)
 template <int L, int G>
 __global__ void __launch_bounds__(256) k_sweep_batch_seg(const __grid_constant__ BatchDev b, int step, int q0, int q1,
                                                          int seg)
 {
+    static_assert(G <= 32, "warp groups only");
     using Gm = Geo<L>;
+    using Gr = Group<G>;
     extern __shared__ uint32_t smem[];
     __shared__ long long s_off[kMaxBatchRuns + 1];
-    __shared__ unsigned s_red[256 / 32 + 1];
     const int nq = q1 - q0;
     for (int i = threadIdx.x; i <= nq; i += blockDim.x) s_off[i] = b.item_off[q0 + i];
     __syncthreads();
     const long long first = s_off[0], end = s_off[nq];
-    if constexpr (G > 32) {
-        for (;;) {
-            if (threadIdx.x == 0) s_red[256 / 32] = atomicAdd(b.work + seg, 1u);
-            __syncthreads();
-            const long long it = first + (long long)s_red[256 / 32];
-            __syncthreads();
-            if (it >= end) break;
-            const int q = batch_run_of(s_off, nq, it);
-            const RunDev& r = b.runs[b.order[q0 + q]];
-            const long long k = it - s_off[q];
-            unsigned fam = 0;
-            bits_group_step<L, 256>(r, step, k, k < r.rec[step].R, smem, (int)threadIdx.x, s_red, fam);
-            if (threadIdx.x == 0 && fam) atomicAdd(&r.rec[step].fam, (unsigned long long)fam);
-        }
-    } else {
-        using Gr = Group<G>;
-        const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane / G;
-        uint32_t* wsm = smem + warp * (Gr::kPerWarp * Gm::WORDS);
-        for (;;) {
-            const long long it = first + (long long)warp_grab(b.work + seg, 1u);
-            if (it >= end) break;
-            const int q = batch_run_of(s_off, nq, it);
-            const RunDev& r = b.runs[b.order[q0 + q]];
-            const long long k = (it - s_off[q]) * Gr::kPerWarp + g;
-            unsigned fam = 0;
-            bits_group_step<L, G>(r, step, k, k < r.rec[step].R, wsm + g * Gm::WORDS, lane % G, nullptr, fam);
-            fam = group_sum<32>(fam);
-            if (lane == 0 && fam) atomicAdd(&r.rec[step].fam, (unsigned long long)fam);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, g = lane / G;
+    uint32_t* wsm = smem + warp * (Gr::kPerWarp * Gm::WORDS);
+    for (;;) {
+        const long long it = first + (long long)warp_grab(b.work + seg, 1u);
+        if (it >= end) break;
+        const int q = batch_run_of(s_off, nq, it);
+        const RunDev& r = b.runs[b.order[q0 + q]];
+        const long long k = (it - s_off[q]) * Gr::kPerWarp + g;
+        unsigned fam = 0;
+        bits_group_step<L, G>(r, step, k, k < r.rec[step].R, wsm + g * Gm::WORDS, lane % G, nullptr, fam);
+        fam = group_sum<32>(fam);
+        if (lane == 0 && fam) atomicAdd(&r.rec[step].fam, (unsigned long long)fam);
+    }
+}
+
+// ======================================================== bounded-wait self-test
+// One CTA of 32 threads runs the sweep's bulk-copy path on `bytes` bytes of
+// src: thread 0 arms the barrier for them and, if `copy`, issues the copy;
+// every thread waits at most `tries` polls. out[0] = 0 when the bytes landed
+// and equal src, kStatusTimeout when the wait ran out (the barrier armed
+// without a copy: nothing is in flight when the CTA exits), 1 when the
+// bytes landed but differ.
+__global__ void __launch_bounds__(32) k_bulk_selftest(const uint32_t* __restrict__ src, int bytes, int copy, int tries,
+                                                     int* out)
+{
+    __shared__ __align__(16) uint32_t buf[1024];
+    __shared__ __align__(8) unsigned long long mbar;
+    if (threadIdx.x == 0) mbar_init(&mbar);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (copy) {
+            bulk_load(buf, src, (unsigned)bytes, &mbar);
+        } else {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&mbar)),
+                         "r"((unsigned)bytes)
+                         : "memory");
         }
     }
+    const bool landed = mbar_wait(&mbar, 0u, tries);
+    unsigned diff = 0;
+    if (landed)
+        for (int i = threadIdx.x; i < bytes / 4; i += 32) diff |= buf[i] ^ src[i];
+    diff = __reduce_or_sync(0xffffffffu, diff);
+    if (threadIdx.x == 0) out[0] = !landed ? kStatusTimeout : (diff ? 1 : 0);
+}
+
+cudaError_t launch_bulk_selftest(const uint32_t* src, int bytes, bool copy, int tries, int* out, cudaStream_t s)
+{
+    if (bytes < 16 || bytes > 4096 || bytes % 16 || ((uintptr_t)src & 15) || tries < 1) return cudaErrorInvalidValue;
+    k_bulk_selftest<<<1, 32, 0, s>>>(src, bytes, copy ? 1 : 0, tries, out);
+    return cudaGetLastError();
 }
 
 // ======================================================== standalone gather
@@ -2283,6 +2406,7 @@ cudaError_t plan_sweep(const RunDev& h, Launch* ln)
         ln->sweep_threads = 256;
         ln->sweep_smem = 0;
         ln->sweep_blocks = (int)((h.cap + 255) / 256);
+        ln->sweep_full = false;
         ln->count_blocks = h.ntiles;
         return cudaSuccess;
     }
@@ -2292,9 +2416,11 @@ cudaError_t plan_sweep(const RunDev& h, Launch* ln)
         if (threads <= 0) return cudaErrorInvalidConfiguration;
         smem = ((size_t)h.N + 2 * (size_t)threads + 1) * 4u;
     } else if (h.gt > 32) {
-        // one replica per CTA of gt threads, plus reduction/broadcast words
+        // one replica per CTA of gt threads, plus reduction/broadcast words;
+        // bit-packed sweeps keep a second replica buffer for the bulk prefetch
         threads = h.gt;
-        smem = ((size_t)(h.packed ? h.N / 32 : h.words) + 33) * 4u;
+        const size_t rep = h.packed ? (size_t)h.N / 32 : (size_t)h.words;
+        smem = ((h.fmt == 1 && rep <= (size_t)kPrefetchMaxWords ? 2 : 1) * rep + 33) * 4u;
     } else {
         // CTA of up to 8 warps; fewer when one warp's replicas need much shared memory
         const size_t rep_words = h.packed ? (size_t)h.N / 32 : (size_t)h.words;  // packed image of a byte replica
@@ -2330,6 +2456,7 @@ cudaError_t plan_sweep(const RunDev& h, Launch* ln)
     ln->sweep_threads = threads;
     ln->sweep_smem = smem;
     ln->sweep_blocks = (int)std::max(1ll, std::min((long long)sms * per_sm, need));
+    ln->sweep_full = need >= (long long)sms * per_sm;
     // a grid that holds the whole capacity can sweep with one fixed replica
     // per group (no counter), where that instance exists
     ln->sweep_cover = nullptr;
@@ -2448,15 +2575,7 @@ namespace {
 // the segment kernel of shape (L, G), or null
 const void* batch_seg_kernel(int L, int G)
 {
-    if (G == 256) {
-        switch (L) {
-#define PA_BATCH_CTA_PTR(LL) \
-    case LL: return (const void*)k_sweep_batch_seg<LL, 256>;
-            PA_BATCH_CTA_SIZES(PA_BATCH_CTA_PTR)
-#undef PA_BATCH_CTA_PTR
-        default: return nullptr;
-        }
-    }
+    if (G > 32) return nullptr;  // CTA groups: swept by each run's own kernel
     switch (L * 64 + G) {
 #define PA_BATCH_PTR(LL, GG) \
     case LL * 64 + GG: return (const void*)k_sweep_batch_seg<LL, GG>;
@@ -2479,13 +2598,13 @@ cudaError_t plan_batch_segment(BatchSeg* sg, long long units)
     const void* k = batch_seg_kernel(sg->L, sg->G);
     if (!k) return cudaErrorInvalidConfiguration;
     const size_t words = (size_t)sg->L * sg->L / 32;
-    const size_t smem = sg->G > 32 ? words * 4 : (size_t)8 * (32 / sg->G) * words * 4;
+    const size_t smem = (size_t)8 * (32 / sg->G) * words * 4;  // 8 warps of 32/G replicas
     const size_t fixed = (kMaxBatchRuns + 1) * 8 + 64;  // static shared memory of the kernel
     if (smem + fixed > (size_t)max_optin) return cudaErrorInvalidConfiguration;
     if ((e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k, 256, smem)) != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const long long per_cta = sg->G > 32 ? 1 : 8ll * (32 / sg->G);
+    const long long per_cta = 8ll * (32 / sg->G);
     const long long need = std::max(1ll, (units + per_cta - 1) / per_cta);
     sg->blocks = (int)std::min((long long)sms * per_sm, need);
     sg->smem = smem;
@@ -2506,22 +2625,38 @@ cudaError_t launch_batch_step(const BatchDev& b, const BatchLaunch& ln, int step
         k_plan<<<1, 32, 0, s>>>(b, step);
         cudaError_t e = cudaPeekAtLastError();
         if (e != cudaSuccess) return e;
-        // every segment on its own branch: the kernels overlap at their tails
-        if (ln.nseg > 1 && (e = cudaEventRecord(ln.fork, s)) != cudaSuccess) return e;
+        // every segment on its own branch, the own-kernel runs in turn on
+        // kBatchOwnStreams more: the kernels overlap at their tails
+        int live = 0;  // own-kernel runs still stepping
+        for (int j = 0; j < ln.nown; j++) live += step <= ln.own_last[j];
+        const int ncs = std::min(live, kBatchOwnStreams);
+        const bool fork = ln.nseg + ncs > 1;
+        if (fork && (e = cudaEventRecord(ln.fork, s)) != cudaSuccess) return e;
         for (int i = 0; i < ln.nseg; i++) {
             const BatchSeg& sg = ln.seg[i];
-            cudaStream_t t = ln.nseg > 1 ? ln.side[i] : s;
-            if (ln.nseg > 1 && (e = cudaStreamWaitEvent(t, ln.fork, 0)) != cudaSuccess) return e;
+            cudaStream_t t = fork ? ln.side[i] : s;
+            if (fork && (e = cudaStreamWaitEvent(t, ln.fork, 0)) != cudaSuccess) return e;
             BatchDev arg = b;
             int st = step, q0 = sg.q0, q1 = sg.q1, si = i;
             void* args[] = {&arg, &st, &q0, &q1, &si};
             if ((e = cudaLaunchKernel(batch_seg_kernel(sg.L, sg.G), dim3(sg.blocks), dim3(256), args, sg.smem, t)) !=
                 cudaSuccess)
                 return e;
-            if (ln.nseg > 1) {
+            if (fork) {
                 if ((e = cudaEventRecord(ln.join[i], t)) != cudaSuccess) return e;
                 if ((e = cudaStreamWaitEvent(s, ln.join[i], 0)) != cudaSuccess) return e;
             }
+        }
+        for (int i = 0; i < ncs; i++)
+            if (fork && (e = cudaStreamWaitEvent(ln.own_side[i], ln.fork, 0)) != cudaSuccess) return e;
+        for (int j = 0, n = 0; j < ln.nown; j++) {
+            if (step > ln.own_last[j]) continue;
+            cudaStream_t t = fork ? ln.own_side[n++ % kBatchOwnStreams] : s;
+            if ((e = launch_sweep(nullptr, ln.own_h[j], ln.own_ln[j], step, t)) != cudaSuccess) return e;
+        }
+        for (int i = 0; fork && i < ncs; i++) {
+            if ((e = cudaEventRecord(ln.own_join[i], ln.own_side[i])) != cudaSuccess) return e;
+            if ((e = cudaStreamWaitEvent(s, ln.own_join[i], 0)) != cudaSuccess) return e;
         }
         break;
     }

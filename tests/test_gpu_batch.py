@@ -136,6 +136,22 @@ def test_one_failing_run_leaves_the_others():
     b.close()
 
 
+def test_failing_cta_group_run_leaves_the_others():
+    """A run of one replica per CTA (swept by its own kernel inside the
+    batch) that exceeds its capacity stops there; the warp-group and
+    CTA-group runs beside it equal their runs alone."""
+    good = [cfg(128, 200, 2, 0.3, 0.1, 131), cfg(32, 600, 2, 0.3, 0.1, 132), cfg(256, 40, 1, 0.3, 0.1, 133)]
+    bad = cfg(128, 64, 1, 1.0, 0.25, 134, capacity=64, group_threads=256)
+    refs = [alone(c) for c in good]
+    b = eng.PABatch(good + [bad])
+    assert b.shape(3)["group_threads"] == 256
+    with pytest.raises(eng.PAError) as ei:
+        b.run()
+    assert ei.value.kind == "capacity"
+    check_same(b, refs)
+    b.close()
+
+
 def test_config4_draw_matches_oracle_philox():
     from oracle.pa_oracle import philox_many
     got = eng.batch_config4_draw(64)
