@@ -89,6 +89,7 @@ MUL_OPS_PER_ATTEMPT = 4.0       # issued by the kernel (lane-varying products)
 MUL_OPS_ALGORITHMIC = 5.0       # a quarter of Philox4x32-10's 20 wide products
 ALU_OPS_PER_ATTEMPT = 4.5 + 1.0 + 0.5
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_sweep_bits_L64_R20000_theta100.md")
+GATHER_SUMMARY = os.path.join(ROOT, "profiles", "k_gather_L128_R50000.md")
 
 
 def kernel_source_hash() -> str:
@@ -97,11 +98,11 @@ def kernel_source_hash() -> str:
         return hashlib.sha256(f.read()).hexdigest()[:16]
 
 
-def profiled_traffic():
-    """DRAM bytes per sweep launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+def profiled_traffic(summary=PROFILE_SUMMARY):
+    """DRAM bytes per launch from a committed ncu summary (the sweep's by
+    default), if it was taken on the current kernel source (else None)."""
     try:
-        text = open(PROFILE_SUMMARY).read()
+        text = open(summary).read()
     except OSError:
         return None
     vals = {}
@@ -353,7 +354,7 @@ def measured_peaks():
         return 6800.0, "of fallback"
 
 
-def gather_roofline(eng, stream, reps=5, warm=3):
+def gather_roofline(eng, stream, reps=20, warm=3):
     """The resampling copy alone (pa_gather) on the sizes of the adaptive
     L = 128, R = 50000 workload, where the two populations (2 x 102 MB)
     exceed L2: algorithmic bytes = read + write of every new replica
@@ -384,7 +385,7 @@ def gather_roofline(eng, stream, reps=5, warm=3):
     return {"bound": "hbm", "kernel": "k_gather<32> (pa_gather)", "achieved": gbs, "peak": peak, "unit": "GB/s",
             "frac": gbs / peak, "peak_note": lab + " (MEASURED_PEAKS.json hbm_gbs)" if lab == "of measured"
             else lab, "algorithmic_bytes_per_launch": byts, "launch_ms": ms, "reps": reps,
-            "traffic": None,
+            "traffic": profiled_traffic(GATHER_SUMMARY),
             "workload": f"resampling copy of L={L} bit-packed replicas ({words * 4} B each), R_(i-1)={R}, "
                         f"R_i={n_new}, sorted parents with copy numbers 0..3; L2 flushed before each launch"}
 
