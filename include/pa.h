@@ -356,7 +356,9 @@ pa_status pa_tune_cache_lookup(const char *path, const pa_tune_key *key, pa_tune
 /* ---- batches of independent runs ---------------------------------------
  * Many independent fixed-schedule runs (batched runs; Sec. 2.2 notes
  * that independent runs combine by free-energy weights) stepped together:
- * every bookkeeping phase of a temperature step is one launch for all runs.
+ * every bookkeeping phase of a temperature step is one launch for all runs
+ * (when every run's capacity is at most 16384, one launch of one CTA per run
+ * for all of them, as a run alone takes one such CTA).
  * A run that fills the device alone (group_threads 256, one replica per
  * CTA at L = 128, 256, 512; or a warp-group run whose capacity needs at
  * least as many CTAs as the device keeps resident) is swept by its own sweep

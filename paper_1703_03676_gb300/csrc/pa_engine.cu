@@ -1835,6 +1835,7 @@ pa_status batch_capture(pa_batch* b)
     if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal) != cudaSuccess) st = PA_ECUDA;
     for (int step = 1; st == PA_OK && step <= b->max_steps; step++) {
         for (int phase = 0; phase < 6 && st == PA_OK; phase++) {
+            if (!pa::batch_phase_launches(b->ln, step, phase)) continue;
             st = batch_record(b, phase);
             if (st == PA_OK && pa::launch_batch_step(b->bd, b->ln, step, cap, phase, nullptr) != cudaSuccess)
                 st = PA_ECUDA;
@@ -1950,6 +1951,9 @@ pa_status pa_batch_create(const pa_config* cfgs, int32_t n, void* cuda_stream, p
             return fail(PA_EINVAL);
         }
     }
+    b->ln.small = true;
+    for (pa_ctx* m : b->runs) b->ln.small = b->ln.small && m->small_rs;
+    b->ln.last = b->max_steps;
     b->ln.nown = (int)b->own_h.size();
     b->ln.own_h = b->own_h.data();
     b->ln.own_ln = b->own_ln.data();

@@ -211,6 +211,8 @@ struct BatchSeg {
 constexpr int kBatchOwnStreams = 4;  // side streams taking the own-kernel runs' sweeps in turn
 struct BatchLaunch {
     int tiles;                // copy-count tiles over all runs
+    bool small;               // every run's capacity <= kSmallCap: one-CTA resampling per run
+    int last;                 // the batch's last step
     int nseg;
     BatchSeg seg[kMaxBatchSegs];
     cudaStream_t side[kMaxBatchSegs];  // one stream per segment (branches of the graph)
@@ -229,6 +231,7 @@ struct BatchLaunch {
 cudaError_t plan_batch_segment(BatchSeg* seg, long long units);
 cudaError_t launch_batch_step(const BatchDev& b, const BatchLaunch& ln, int step, cudaStream_t s, int phase,
                               int* phase_of_launch);
+bool batch_phase_launches(const BatchLaunch& ln, int step, int phase);
 bool batch_supports(int L, int gt);
 
 #ifdef PA_GB300_H

@@ -2011,13 +2011,11 @@ __device__ __forceinline__ void resample_small_body(const RunDev& r, int step, l
 
 constexpr int kSmallLevels = 2048;  // copy tables kept in shared memory up to this range
 
+// The whole one-CTA step of run r (shared memory from the calling kernel)
 template <bool kStats>
-__global__ void __launch_bounds__(kOneCta) k_resample_small(const __grid_constant__ RunDev r, int step)
+__device__ __forceinline__ void resample_small_step(const RunDev& r, int step, int* s_range, uint32_t* s_F,
+                                                    unsigned long long* s_U)
 {
-    __shared__ int s_range[2];
-    __shared__ uint32_t s_F[kSmallLevels];
-    __shared__ unsigned long long s_U[kSmallLevels];
-    if (*r.status) return;
     // loads that depend on nothing computed here, issued first: R_{i-1} and
     // this thread's first four old-slot levels (written by the previous step)
     const long long Rp = r.rec[step - 1].R;
@@ -2041,13 +2039,43 @@ __global__ void __launch_bounds__(kOneCta) k_resample_small(const __grid_constan
     resample_small_body(r, step, Rp, lv0, in_smem ? s_F : nullptr, in_smem ? s_U : nullptr, kmin);
 }
 
+template <bool kStats>
+__global__ void __launch_bounds__(kOneCta) k_resample_small(const __grid_constant__ RunDev r, int step)
+{
+    __shared__ int s_range[2];
+    __shared__ uint32_t s_F[kSmallLevels];
+    __shared__ unsigned long long s_U[kSmallLevels];
+    if (*r.status) return;
+    resample_small_step<kStats>(r, step, s_range, s_F, s_U);
+}
+
+// The same for every run of a batch whose runs all have capacity <=
+// kSmallCap: one CTA per run (blockIdx.x = run index). A run past its last
+// step only does the statistics of that step (deferred to the step after
+// it), then idles; the batch's last step is followed by k_stats_batch.
+template <bool kStats>
+__global__ void __launch_bounds__(kOneCta) k_resample_small_batch(const __grid_constant__ BatchDev b, int step)
+{
+    __shared__ int s_range[2];
+    __shared__ uint32_t s_F[kSmallLevels];
+    __shared__ unsigned long long s_U[kSmallLevels];
+    const RunDev& r = b.runs[blockIdx.x];
+    if (*r.status) return;
+    if (step > r.nsteps) {
+        if (kStats && step == r.nsteps + 1) stats_body(r, step - 1);
+        return;
+    }
+    resample_small_step<kStats>(r, step, s_range, s_F, s_U);
+}
+
 // ======================================================== batched sweep
-// Work items of step `step`, laid out in queue order: one per replica of a
-// run with CTA-wide groups, ceil(R_i / (replicas per warp)) per run with
-// warp groups. The queue is cut into segments of runs that share (L, threads
+// Work items of step `step`, laid out in queue order: ceil(R_i / (replicas
+// per warp)) per warp-group run (one per replica for CTA-wide groups, whose
+// runs are swept by their own kernels and never read theirs). The runs that
+// do not fill the device alone are cut into segments that share (L, threads
 // per replica); each segment is swept by its own instance of the kernel
-// below (compiled for that shape alone), all segments on parallel branches
-// of the captured graph, each with its own counter work[seg].
+// below (compiled for that shape alone), on parallel branches of the
+// captured graph, each with its own counter work[seg].
 __global__ void k_plan(const __grid_constant__ BatchDev b, int step)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
@@ -2064,8 +2092,9 @@ __global__ void k_plan(const __grid_constant__ BatchDev b, int step)
     for (int s = 0; s < b.nseg; s++) b.work[s] = 0u;
 }
 
-// (L, G) pairs a batched sweep can run: warp groups dividing the plane, and
-// one replica per 256-thread CTA for L >= 128
+// (L, G) pairs a batched sweep can run: warp groups dividing the plane (a
+// segment kernel, or the run's own sweep kernel when it fills the device), and
+// one replica per 256-thread CTA for L >= 128 (always the run's own kernel)
 #define PA_BATCH_SHAPES(X) X(8, 1) X(16, 2) X(16, 4) X(32, 8) X(32, 16) X(64, 16) X(64, 32) X(128, 32) X(256, 32)
 #define PA_BATCH_CTA_SIZES(X) X(128) X(256) X(512)
 
@@ -2611,13 +2640,30 @@ cudaError_t plan_batch_segment(BatchSeg* sg, long long units)
     return cudaSuccess;
 }
 
+// Whether phase `phase` of step `step` launches anything: batches of small
+// runs do phases 0-3 (and the statistics, deferred) in one launch, and
+// their statistics phase only after the last step.
+bool batch_phase_launches(const BatchLaunch& ln, int step, int phase)
+{
+    if (!ln.small) return true;
+    if (phase >= 1 && phase <= 3) return false;
+    return phase != 5 || step == ln.last;
+}
+
 // One phase of a batched step: 0 tables, 1 counts, 2 scan, 3 parent, 4 plan +
-// sweep, 5 stats (the phase numbers of pa_phase_times).
+// sweep, 5 stats (the phase numbers of pa_phase_times); in batches of small
+// runs, phase 0 is the one-CTA resampling (with the previous step's
+// statistics) and phase 5 only follows the last step.
 cudaError_t launch_batch_step(const BatchDev& b, const BatchLaunch& ln, int step, cudaStream_t s, int phase,
                               int* /*unused*/)
 {
+    if (!batch_phase_launches(ln, step, phase)) return cudaSuccess;
     switch (phase) {
-    case 0: k_tables_batch<<<b.nruns, kOneCta, 0, s>>>(b, step); break;
+    case 0:
+        if (!ln.small) k_tables_batch<<<b.nruns, kOneCta, 0, s>>>(b, step);
+        else if (step > 1) k_resample_small_batch<true><<<b.nruns, kOneCta, 0, s>>>(b, step);
+        else k_resample_small_batch<false><<<b.nruns, kOneCta, 0, s>>>(b, step);
+        break;
     case 1: k_counts_batch<<<ln.tiles, kTileThreads, 0, s>>>(b, step); break;
     case 2: k_scan_batch<<<b.nruns, kOneCta, 0, s>>>(b, step); break;
     case 3: k_parent_batch<<<ln.tiles, kTile, 0, s>>>(b, step); break;

@@ -67,6 +67,21 @@ def test_batch_equals_alone_and_oracle():
     b.close()
 
 
+def test_batch_with_a_large_population():
+    """A run whose capacity is above the one-CTA resampling limit (16384)
+    takes the batch through the multi-kernel bookkeeping (tables, counts,
+    scan, parents, statistics: one launch each for all runs); the small-run
+    batches above take the one-CTA-per-run form. Both equal the runs alone."""
+    mix = [(16, 16000, 1, 0.15, 0.05, 141), (32, 900, 2, 0.2, 0.05, 142), (128, 120, 1, 0.1, 0.05, 143),
+           (8, 500, 3, 0.3, 0.05, 144)]
+    cfgs = [cfg(*m) for m in mix]
+    refs = [alone(c) for c in cfgs]
+    b = eng.PABatch(cfgs)
+    b.run()
+    check_same(b, refs)
+    b.close()
+
+
 def test_batch_group_shapes_do_not_change_results():
     base = [cfg(*m) for m in MIX[:5]]
     refs = [alone(c) for c in base]
