@@ -395,7 +395,10 @@ pa_status pa_batch_reset(pa_batch *b, const uint64_t *seeds);
 pa_status pa_batch_get(pa_batch *b, int32_t i, pa_ctx **out);
 /* Accumulated device time per phase of the batched steps (needs profile in
  * any of the configs): [0] tables, [1] counts, [2] scan, [3] parent,
- * [4] plan + sweep, [5] stats. */
+ * [4] plan + sweep, [5] stats. In a batch whose runs all have capacity
+ * <= 16384, [0] is the one-CTA resampling of every run (with the previous
+ * step's statistics), [1]-[3] stay empty and [5] is the last step's
+ * statistics only. launches[p] counts the phase's launches. */
 pa_status pa_batch_phase_times(pa_batch *b, double ms[7], int64_t launches[7]);
 /* Threads per replica used for run i and the persistent grid size of the
  * sweep kernel that runs it (its own kernel, or its segment's kernel). */
