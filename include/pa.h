@@ -145,6 +145,11 @@ typedef struct {
 
 /* Create a run and generate its beta0 population (row 0). `cuda_stream` is
  * a cudaStream_t borrowed for the context's lifetime, or NULL.
+ * A population of at most 16384 slots of capacity takes two launches per
+ * temperature step (resampling, sweep), each launched with programmatic
+ * dependent launch so that it is scheduled while the one before it runs and
+ * starts work when that one completes; the environment variable PA_PDL=0,
+ * read here, launches them one after the other instead (same results).
  * Errors: PA_EINVAL (bad config), PA_ENOMEM, PA_ECUDA. */
 pa_status pa_create(const pa_config *cfg, void *cuda_stream, pa_ctx **out);
 

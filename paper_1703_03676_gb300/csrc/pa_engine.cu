@@ -119,6 +119,9 @@ struct pa_ctx {
     long long n_kern = 0;         // kernels of this library launched for the run
     long long graph_kern = 0;     // kernels in one launch of `graph`
     bool small_rs = false;        // capacity <= kSmallCap: one-CTA resampling launch per step
+    bool pdl = false;             // small_rs steps: each launch may be scheduled while the one before
+                                  // it runs (programmatic dependent launch; off with PA_PDL=0 and
+                                  // when profiling events sit between the launches)
     bool stats_pending = false;   // statistics of the last enqueued step not yet launched
 };
 
@@ -437,7 +440,7 @@ pa_status enqueue_kernels(pa_ctx* c, int step, bool stats_now)
 {
     const RunDev& h = c->h;
     if (c->small_rs) {
-        PA_PHASE(c, 0, pa::launch_resample_small(h, step, c->stats_pending, c->stream));
+        PA_PHASE(c, 0, pa::launch_resample_small(h, step, c->stats_pending, c->stream, c->pdl));
     } else {
         if (c->stats_pending) PA_PHASE(c, 5, pa::launch_stats(nullptr, h, step - 1, c->stream));
         PA_PHASE(c, 0, pa::launch_tables(nullptr, h, step, c->stream));
@@ -446,7 +449,7 @@ pa_status enqueue_kernels(pa_ctx* c, int step, bool stats_now)
         PA_PHASE(c, 3, pa::launch_parent(nullptr, h, c->ln, step, c->stream));
     }
     c->stats_pending = false;
-    PA_PHASE(c, 4, pa::launch_sweep(nullptr, h, c->ln, step, c->stream));
+    PA_PHASE(c, 4, pa::launch_sweep(nullptr, h, c->ln, step, c->stream, c->pdl));
     if (stats_now) PA_PHASE(c, 5, pa::launch_stats(nullptr, h, step, c->stream));
     else c->stats_pending = true;
     return PA_OK;
@@ -971,6 +974,10 @@ pa_status create_impl(const pa_config* cfg, void* cuda_stream, const int8_t* Jr,
     h.estep = cfg->potts_q ? 1 : 4;
     h.eoff = (long long)h.dim * s.N;  // Ising dim N; Potts (square lattice) 2N
     c->small_rs = s.cap <= pa::kSmallCap;
+    {
+        const char* e = std::getenv("PA_PDL");
+        c->pdl = c->small_rs && !cfg->profile && !(e && e[0] == '0');
+    }
     const size_t N1 = (size_t)s.nlev;
     pa_status st = PA_OK;
 #define PA_ALLOC(p, n)                            \

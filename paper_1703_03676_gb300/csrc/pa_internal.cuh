@@ -188,11 +188,15 @@ cudaError_t launch_parent(const RunDev* d_run, const RunDev& h, const Launch& ln
 // the same three kernels on plain arguments; tiles = blocks covering the
 // largest old population the launch may see
 cudaError_t launch_resample(const ResampleArgs& a, int tiles, cudaStream_t s);
-cudaError_t launch_sweep(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s);
+// pdl: launch with programmatic serialization (the kernel may be scheduled
+// while the previous kernel of the stream runs; it waits for that kernel's
+// completion before touching memory)
+cudaError_t launch_sweep(const RunDev* d_run, const RunDev& h, const Launch& ln, int step, cudaStream_t s,
+                         bool pdl = false);
 cudaError_t launch_stats(const RunDev* d_run, const RunDev& h, int step, cudaStream_t s);
 // statistics of step-1 (optional), tables, copy numbers, offsets and parents
 // of step `step` in one single-CTA launch (capacity <= kSmallCap)
-cudaError_t launch_resample_small(const RunDev& h, int step, bool with_stats, cudaStream_t s);
+cudaError_t launch_resample_small(const RunDev& h, int step, bool with_stats, cudaStream_t s, bool pdl = false);
 cudaError_t launch_rng_peak(long long blocks, uint32_t* sink, int grid, int threads, cudaStream_t s);
 // the bulk-copy path with a bounded wait, with or without the copy (out[0]:
 // 0 landed and equal, kStatusTimeout wait ran out, 1 landed but different)

@@ -23,6 +23,24 @@
 
 namespace pa {
 
+// ======================================================== programmatic dependent launch
+// A kernel launched with the programmatic-serialization attribute may be
+// scheduled while the kernel before it in the stream is still running.
+// pdl_wait() returns once that kernel has completed and its writes are
+// visible (for a kernel launched without the attribute there is nothing to
+// wait for and it returns at once); every kernel that can be launched so
+// calls it before touching memory. pdl_trigger() lets the next kernel of the
+// stream be scheduled early: it is issued right after the wait, so at most
+// one kernel waits ahead of the one that runs.
+__device__ __forceinline__ void pdl_wait()
+{
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+__device__ __forceinline__ void pdl_trigger()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 // ======================================================== bit-packed geometry
 constexpr uint32_t row_first_mask(int hb)
 {
@@ -698,6 +716,8 @@ __global__ void __launch_bounds__(256) k_init_bits(const __grid_constant__ RunDe
 template <int L, int G, int D = 2, bool kBytes = false, bool kCover = false>
 __global__ void __launch_bounds__(256) k_sweep_bits(const __grid_constant__ RunDev r, int step)
 {
+    pdl_wait();
+    pdl_trigger();
     using Gm = Lat<L, D>;
     using Gr = Group<G>;
     extern __shared__ uint32_t smem[];
@@ -877,6 +897,8 @@ __global__ void __launch_bounds__(256) k_init_bytes(const __grid_constant__ RunD
 template <int G>
 __global__ void __launch_bounds__(256) k_sweep_bytes(const __grid_constant__ RunDev r, int step)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int RPW = 32 / G;
     extern __shared__ uint32_t smem[];
     if (*r.status) return;
@@ -1056,6 +1078,8 @@ __global__ void __launch_bounds__(256) k_init_potts(const __grid_constant__ RunD
 template <int G>
 __global__ void __launch_bounds__(256) k_sweep_potts(const __grid_constant__ RunDev r, int step)
 {
+    pdl_wait();
+    pdl_trigger();
     constexpr int RPW = 32 / G;
     extern __shared__ uint32_t smem[];
     if (*r.status) return;
@@ -1184,6 +1208,8 @@ __global__ void __launch_bounds__(256) k_init_rp(const __grid_constant__ RunDev 
 
 __global__ void __launch_bounds__(256) k_sweep_rp(const __grid_constant__ RunDev r, int step)
 {
+    pdl_wait();
+    pdl_trigger();
     if (*r.status) return;
     const long long Ri = r.rec[step].R;
     const long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1418,6 +1444,8 @@ __global__ void __launch_bounds__(32 * msc_warps<L>()) k_init_msc(const __grid_c
 template <int L>
 __global__ void __launch_bounds__(32 * msc_warps<L>()) k_sweep_msc(const __grid_constant__ RunDev r, int step)
 {
+    pdl_wait();
+    pdl_trigger();
     using Gm = MscGeo<L>;
     constexpr int W = msc_warps<L>(), N = Gm::N, HALF = Gm::HALF, NP = Gm::NP, QP = Gm::QP;
     extern __shared__ uint32_t smem[];
@@ -2042,6 +2070,8 @@ __device__ __forceinline__ void resample_small_step(const RunDev& r, int step, i
 template <bool kStats>
 __global__ void __launch_bounds__(kOneCta) k_resample_small(const __grid_constant__ RunDev r, int step)
 {
+    pdl_wait();
+    pdl_trigger();
     __shared__ int s_range[2];
     __shared__ uint32_t s_F[kSmallLevels];
     __shared__ unsigned long long s_U[kSmallLevels];
@@ -2511,13 +2541,32 @@ cudaError_t launch_init(const RunDev* /*d_run*/, const RunDev& h, const Launch& 
     return cudaLaunchKernel(k, dim3(ln.sweep_blocks), dim3(ln.sweep_threads), args, ln.sweep_smem, s);
 }
 
-cudaError_t launch_sweep(const RunDev* /*d_run*/, const RunDev& h, const Launch& ln, int step, cudaStream_t s)
+// A launch of kernel k that may overlap the previous kernel of stream s
+// (programmatic serialization; the kernel starts with pdl_wait)
+static cudaError_t launch_pdl(const void* k, dim3 grid, dim3 block, void** args, size_t smem, cudaStream_t s)
+{
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, k, args);
+}
+
+cudaError_t launch_sweep(const RunDev* /*d_run*/, const RunDev& h, const Launch& ln, int step, cudaStream_t s,
+                         bool pdl)
 {
     const void* k = ln.sweep_cover ? ln.sweep_cover : sweep_kernel(h, false);
     if (!k) return cudaErrorInvalidConfiguration;
     RunDev arg = h;
     int st = step;
     void* args[] = {&arg, &st};
+    if (pdl) return launch_pdl(k, dim3(ln.sweep_blocks), dim3(ln.sweep_threads), args, ln.sweep_smem, s);
     return cudaLaunchKernel(k, dim3(ln.sweep_blocks), dim3(ln.sweep_threads), args, ln.sweep_smem, s);
 }
 
@@ -2557,9 +2606,16 @@ cudaError_t launch_resample(const ResampleArgs& a, int tiles, cudaStream_t s)
     return cudaGetLastError();
 }
 
-cudaError_t launch_resample_small(const RunDev& h, int step, bool with_stats, cudaStream_t s)
+cudaError_t launch_resample_small(const RunDev& h, int step, bool with_stats, cudaStream_t s, bool pdl)
 {
     if (h.cap > kSmallCap) return cudaErrorInvalidValue;
+    if (pdl) {
+        RunDev arg = h;
+        int st = step;
+        void* args[] = {&arg, &st};
+        const void* k = with_stats ? (const void*)k_resample_small<true> : (const void*)k_resample_small<false>;
+        return launch_pdl(k, dim3(1), dim3(kOneCta), args, 0, s);
+    }
     if (with_stats) k_resample_small<true><<<1, kOneCta, 0, s>>>(h, step);
     else k_resample_small<false><<<1, kOneCta, 0, s>>>(h, step);
     return cudaGetLastError();
