@@ -163,21 +163,33 @@ def clocks_sampler_stop(h, path, gpu_index):
 def _oracle_sample(args):
     """One worker: the oracle on R_s replicas of the workload `wl`, for
     n_steps temperature steps (None: the whole anneal to beta_f); returns
-    (attempts, seconds). (Workers are spawned, so the workload comes in the
-    arguments, not from this module's globals.)"""
+    (attempts, seconds, restarts). A population this small can die out (all
+    copy numbers 0 when R_{i-1} > R); the sample then starts a new anneal
+    from beta0 with the next seed, counting the steps already done, until
+    n_steps steps (or one whole anneal) are complete; `restarts` counts
+    these. (Workers are spawned, so the workload comes in the arguments, not
+    from this module's globals.)"""
     R_s, n_steps, seed, wl = args
     sys.path.insert(0, ROOT)
-    from oracle.pa_oracle import PopulationAnnealing
+    from oracle.pa_oracle import OracleError, PopulationAnnealing
     t0 = time.perf_counter()
-    pa = PopulationAnnealing(wl["L"], R_s, wl["theta"], beta_f=wl["beta_f"], dbeta=wl["dbeta"], seed=seed,
-                             dim=wl["dim"], potts_q=wl["potts_q"])
     att = 0
     k = 0
-    while not pa.done and (n_steps is None or k < n_steps):
-        rec = pa.step()
-        att += wl["L"] ** wl["dim"] * wl["theta"] * rec.R
-        k += 1
-    return att, time.perf_counter() - t0
+    restarts = 0
+    while True:
+        pa = PopulationAnnealing(wl["L"], R_s, wl["theta"], beta_f=wl["beta_f"], dbeta=wl["dbeta"],
+                                 seed=seed + 1000003 * restarts, dim=wl["dim"], potts_q=wl["potts_q"])
+        try:
+            while not pa.done and (n_steps is None or k < n_steps):
+                rec = pa.step()
+                att += wl["L"] ** wl["dim"] * wl["theta"] * rec.R
+                k += 1
+        except OracleError as e:
+            if e.kind != "extinct" or restarts >= 100:
+                raise
+            restarts += 1
+            continue
+        return att, time.perf_counter() - t0, restarts
 
 
 def cpu_oracle(workers: int, R_s: int, n_steps, seed0: int):
@@ -188,8 +200,14 @@ def cpu_oracle(workers: int, R_s: int, n_steps, seed0: int):
     with ctx.Pool(workers) as pool:
         res = pool.map(_oracle_sample, [(R_s, n_steps, seed0 + w, dict(WL)) for w in range(workers)])
     wall = time.perf_counter() - t0
-    att = sum(a for a, _ in res)
-    return att / wall / 1e9, att, wall
+    att = sum(r[0] for r in res)
+    restarts = sum(r[2] for r in res)
+    return att / wall / 1e9, att, wall, restarts
+
+
+def restart_note(restarts: int) -> str:
+    return (f"; {restarts} population(s) died out and restarted from beta0 with the next seed, their steps "
+            f"counted" if restarts else "")
 
 
 def anneal_label():
@@ -198,10 +216,11 @@ def anneal_label():
 
 
 def cpu_baseline_obj(workers, R_s):
-    v, att, wall = cpu_oracle(workers, R_s, None, 9000)
+    v, att, wall, restarts = cpu_oracle(workers, R_s, None, 9000)
     return {"value": v, "unit": UNIT, "cores": workers, "kind": "oracle",
             "sample": f"{workers} independent oracle processes, each {anneal_label()} of the workload with "
-                      f"R={R_s} (not R={WL['R']}): {att:.3e} attempts in {wall:.1f} s wall"}
+                      f"R={R_s} (not R={WL['R']}): {att:.3e} attempts in {wall:.1f} s wall"
+                      f"{restart_note(restarts)}"}
 
 
 # ------------------------------------------------------------------ helpers
@@ -254,14 +273,15 @@ def run_reference(args):
     R_s = args.ref_replicas
     for _ in range(args.warmup):
         cpu_oracle(workers, 1, 10, 500)  # untimed: spawn, build and page in
-    tot_att, tot_wall = 0, 0.0
+    tot_att, tot_wall, tot_restarts = 0, 0.0, 0
     for k in range(args.steps):
-        _, att, wall = cpu_oracle(workers, R_s, None, 1000 + 100 * k)
+        _, att, wall, restarts = cpu_oracle(workers, R_s, None, 1000 + 100 * k)
         tot_att += att
         tot_wall += wall
+        tot_restarts += restarts
     v = tot_att / tot_wall / 1e9
     sample = (f"each step: {workers} independent oracle processes, each {anneal_label()} of the workload "
-              f"with R={R_s} (not R={WL['R']})")
+              f"with R={R_s} (not R={WL['R']}){restart_note(tot_restarts)}")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_wall / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int8",
@@ -719,7 +739,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-replicas", type=int, default=8,
                     help="replicas per process of the cpu_baseline sample (whole anneals)")
-    ap.add_argument("--ref-replicas", type=int, default=2,
+    ap.add_argument("--ref-replicas", type=int, default=4,
                     help="replicas per process of each --impl reference step (whole anneals)")
     args = ap.parse_args()
     if args.warmup < 3:

@@ -56,6 +56,11 @@ class OracleError(RuntimeError):
         super().__init__(msg)
         self.kind = kind
 
+    def __reduce__(self):
+        # rebuilt from (kind, message) when it crosses a process boundary
+        # (a worker of a multiprocessing pool raising it)
+        return (OracleError, (self.kind, str(self)))
+
 
 def _ptr(a: np.ndarray, ctype):
     import ctypes
