@@ -199,6 +199,29 @@ def test_capacity_failure_matches_oracle():
     run.close()
 
 
+def test_extinction_matches_oracle():
+    """A population of two replicas that grew to more than two, with every
+    expected copy number below one, dies out at the same step on both sides
+    (L = 8, R = 2, seed 113: step 3); the rows before it agree."""
+    from oracle.pa_oracle import OracleError
+    pa = oracle_run(8, 2, 1, 1.0, 0.05, 113)
+    with pytest.raises(OracleError) as oe:
+        pa.run()
+    assert oe.value.kind == "extinct"
+    bad = len(pa.records)  # steps completed before the failing one
+    for fmt in (B32, I8):
+        run = eng.PARun(eng.PAConfig(L=8, R=2, theta=1, beta_f=1.0, dbeta=0.05, seed=113, spin_format=fmt,
+                                     record_histograms=True))
+        with pytest.raises(eng.PAError) as ei:
+            run.run()
+        assert ei.value.kind == "extinct"
+        rows = run.rows()
+        assert len(rows) == bad
+        for i, ref in enumerate(pa.rows):
+            assert_row_close(rows[i], ref, f"row {i}")
+        run.close()
+
+
 def test_invalid_configs_rejected():
     for kw in [dict(L=7), dict(L=24, spin_format=B32), dict(theta=0), dict(R=0), dict(beta_f=-1.0),
                dict(dbeta=0.0, overlap=1.5), dict(group_threads=3)]:

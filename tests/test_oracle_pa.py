@@ -132,6 +132,30 @@ def test_capacity_error():
     assert ei.value.kind == "capacity"
 
 
+def test_extinction_only_when_every_copy_weight_is_below_one():
+    """Sec. 2.1, Eq. resampling-factors: replica j expects
+    tau_j = R exp(-dbeta E_j) / sum_l exp(-dbeta E_l) copies, at least one of
+    which is at least 1 when R_{i-1} <= R; so a population can die out only
+    after it has grown past R and every tau_j is below 1. With L = 8, R = 2,
+    theta = 1, dbeta = 0.05 and seed 113 it dies out at step 3; the expected
+    copy numbers of the population it resampled are written out here from the
+    equation (numpy exp and sum, not the oracle's tables)."""
+    pa = PopulationAnnealing(8, 2, 1, beta_f=1.0, dbeta=0.05, seed=113)
+    with pytest.raises(OracleError) as ei:
+        pa.run()
+    assert ei.value.kind == "extinct"
+    assert len(pa.records) == 3 and len(pa.rows) == 3  # steps 0, 1, 2 completed
+    E = pa.E.astype(np.float64)  # energies of population 2, the one step 3 resampled
+    assert E.size > 2 and E.size == pa.records[-1].R
+    w = np.exp(-0.05 * (E - E.min()))
+    tau = 2.0 * w / w.sum()
+    assert tau.max() < 1.0
+    # the same run with more replicas does not die out
+    big = PopulationAnnealing(8, 8, 1, beta_f=1.0, dbeta=0.05, seed=113)
+    big.run()
+    assert big.done
+
+
 def _runs(L, R, theta, dbeta, seeds):
     out = []
     for s in seeds:
