@@ -60,3 +60,11 @@ def test_spawned_pool_finishes_when_a_population_dies_out(monkeypatch):
     v, att, wall, restarts = bench.cpu_oracle(2, 2, None, DYING_SEED)
     assert restarts >= 1 and att > 0 and v > 0
     assert "died out" in bench.restart_note(restarts) and bench.restart_note(0) == ""
+
+
+def test_cpu_baseline_object(monkeypatch):
+    for k, v in SMALL.items():
+        monkeypatch.setitem(bench.WL, k, v)
+    obj = bench.cpu_baseline_obj(2, 2)
+    assert obj["kind"] == "oracle" and obj["cores"] == 2 and obj["value"] > 0 and obj["unit"] == bench.UNIT
+    assert "whole anneal" in obj["sample"]
